@@ -1,0 +1,211 @@
+/*
+ * mecuco.h - C ABI of the GB300 (sm_103a) MeCuCo local mean-curvature library.
+ *
+ * The library computes, for every point x_i of a dataset X (N x m), the
+ * paper's Fast-mode mean-curvature score K_i (arXiv 2606.06329, Sec. 4,
+ * Algorithm 1, Fast branch):
+ *   1. the k nearest other points of x_i under squared Euclidean distance
+ *      (Sec. 3 Step 1, eq. knn; Alg. 1 kNN-Graph),
+ *   2. the centred k x m patch X_c (Sec. 3 Step 2; Alg. 1 Fast branch),
+ *   3. its truncated SVD with p = k-1 through the k x k Gram X_c X_c^T
+ *      (eq. svd_cov; Alg. 1 SVD_p),
+ *   4. tau, t_range, t_A, t_B, t_null and K_i = |(t_range + t_null)/2 + tau/2|
+ *      (eqs. tnull, tA, tB, fast_curv; Alg. 1 Fast branch).
+ *
+ * Conventions shared by every entry point
+ *   - X is row-major with leading dimension ld >= m (elements, not bytes);
+ *     element type F32 or BF16.  Unless an entry point says "host", every
+ *     pointer is a DEVICE pointer on the context's device, owned by the
+ *     caller; the library never frees or retains it past the call.
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Device-pointer entry points are asynchronous on that stream: they
+ *     enqueue work and return; results are valid once the stream reaches
+ *     that point.  Host entry points synchronise the stream before return.
+ *   - Neighbour lists idx are int32, N x k row-major, each row sorted by
+ *     (distance, index) ascending; a point is not its own neighbour unless
+ *     include_self = 1.  Requirements: 2 <= k <= 64, k <= N - 1 (k <= N with
+ *     include_self), 1 <= m, N < 2^31.
+ *   - The truncation rank is p = min(k - 1, m, numerical rank of X_c), the
+ *     numerical rank counting eigenvalues of X_c X_c^T above 8 sqrt(m) 2^-24
+ *     times the largest (the FP32 Gram's rounding scale); q = m - p and
+ *     t_null = 0 when q = 0.
+ *   - Return value: MECUCO_OK, or an error code; on an argument error nothing
+ *     is enqueued.  Errors detected on the device (an eigensolver sweep cap,
+ *     a bounded wait that ran out) never trap: they are OR-ed into a device
+ *     status word read back by mecuco_get_last_status() after the stream has
+ *     been synchronised.  No entry point throws across the ABI.
+ *   - A context may be used from one host thread at a time.
+ */
+#ifndef MECUCO_H
+#define MECUCO_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MECUCO_API __attribute__((visibility("default")))
+#else
+#define MECUCO_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mecuco_ctx *mecuco_t;
+
+typedef enum {
+    MECUCO_OK = 0,
+    MECUCO_ERR_INVALID_ARG = 1,   /* a size, pointer, alignment or enum is out of range */
+    MECUCO_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement */
+    MECUCO_ERR_OOM = 3,           /* device or pinned-host allocation failed */
+    MECUCO_ERR_CUDA = 4,          /* a CUDA runtime call failed (message: mecuco_last_error_message) */
+    MECUCO_ERR_NOT_CONVERGED = 5, /* device: an eigensolve hit its sweep cap (result still written) */
+    MECUCO_ERR_TIMEOUT = 6        /* device: a bounded wait ran out (result of that launch invalid) */
+} mecuco_status;
+
+typedef enum { MECUCO_F32 = 0, MECUCO_BF16 = 1 } mecuco_dtype;
+
+/* Fast-mode null-space term.
+ *   LITERAL: t_B = tau - 2 |X_c V_r|_F^2/(k-1) + |G_tens|_F^2/(k-1) and
+ *            t_null = (t_A + 2 t_B)/(m - p), exactly as Alg. 1 prints them.
+ *   HAAR:    the Haar expectation of eq. gnull_exp written out:
+ *            t_B = tau - 2 sum_{j,a} X_c[j,a]^2 (1 - d_P[a])/(k-1)
+ *                  + |G_tens|_F^2/(k-1), t_null = (t_A + 2 t_B)/(m - p + 2). */
+typedef enum { MECUCO_FAST_LITERAL = 0, MECUCO_FAST_HAAR = 1 } mecuco_variant;
+
+/* Arithmetic of the hot path.
+ *   FP32:       distances, Gram, third moments and the k-space estimator in
+ *               FP32 on the CUDA cores; FP32 Jacobi.  (the plain form)
+ *   BF16_MIXED: distance GEMM in BF16 on the tensor cores with FP32
+ *               accumulation and an FP32 exact re-rank of the candidates;
+ *               patch moments from BF16 operands with FP32 accumulation;
+ *               FP64 Jacobi eigensolve and rotation accumulation.  (the
+ *               chosen form) */
+typedef enum { MECUCO_PREC_FP32 = 0, MECUCO_PREC_BF16_MIXED = 1 } mecuco_precision;
+
+/* Tunable options (mecuco_set_option).  Values are int64. */
+typedef enum {
+    MECUCO_OPT_KNN_MARGIN = 0,       /* extra candidates kept per row before the exact re-rank (default 32) */
+    MECUCO_OPT_JACOBI_FP64 = 1,      /* -1: by precision (default), 0: FP32 sweeps, 1: FP64 sweeps */
+    MECUCO_OPT_JACOBI_MAX_SWEEPS = 2,/* sweep cap of the eigensolver (default 40) */
+    MECUCO_OPT_CHUNK_POINTS = 3,     /* points per estimator chunk (0 = automatic) */
+    MECUCO_OPT_KNN_QUERY_CHUNK = 4,  /* query rows per kNN launch (0 = automatic) */
+    MECUCO_OPT_PROFILE = 5           /* 1: bracket every kernel with CUDA events (mecuco_get_stage_times) */
+} mecuco_option;
+
+/* Kernel stages, for mecuco_get_stage_times. */
+typedef enum {
+    MECUCO_STAGE_ROWNORM = 0,    /* squared row norms (kNN) */
+    MECUCO_STAGE_KNN_SEARCH = 1, /* distance tiles + per-row candidate lists */
+    MECUCO_STAGE_KNN_RERANK = 2, /* exact re-rank + certification */
+    MECUCO_STAGE_KNN_FALLBACK = 3,/* exact full scan of uncertified rows */
+    MECUCO_STAGE_GRAM = 4,       /* gather, centre, G = X_c X_c^T, R, Q */
+    MECUCO_STAGE_MOMENTS = 5,    /* gather, centre, third moments M */
+    MECUCO_STAGE_JACOBI = 6,     /* k x k eigensolve */
+    MECUCO_STAGE_ESTIMATOR = 7,  /* k-space Fast estimator */
+    MECUCO_STAGE_COUNT = 8
+} mecuco_stage;
+
+/* Counters of the last completed call (valid after the stream is synchronised). */
+typedef struct {
+    int64_t knn_rows;            /* query rows searched */
+    int64_t knn_uncertified;     /* rows whose candidate margin could not be certified */
+    int64_t knn_fallback_rows;   /* rows re-solved by the exact full-scan path */
+    int64_t jacobi_max_sweeps;   /* largest sweep count used by any patch */
+    int64_t jacobi_not_converged;/* patches that hit the sweep cap */
+    int64_t rank_deficient;      /* patches with numerical rank < min(k-1, m) */
+    int64_t kernel_launches;     /* kernels launched by the call */
+} mecuco_stats;
+
+/* Create a context on CUDA device `device`.  It owns a device workspace that
+ * grows on demand (cudaMalloc) and a device status word.  Returns
+ * MECUCO_ERR_INVALID_ARG for a bad device, MECUCO_ERR_UNSUPPORTED if the
+ * device is not compute capability 10.3, MECUCO_ERR_OOM on allocation
+ * failure. */
+MECUCO_API mecuco_status mecuco_create(mecuco_t *h, int device);
+
+/* Release everything the context owns.  Synchronises the device first.
+ * NULL is accepted and ignored. */
+MECUCO_API mecuco_status mecuco_destroy(mecuco_t h);
+
+/* Set a tuning option (see mecuco_option); out-of-range values are rejected. */
+MECUCO_API mecuco_status mecuco_set_option(mecuco_t h, mecuco_option opt, int64_t value);
+
+/* Step 1 (Sec. 3 Step 1, eq. knn): the k nearest neighbours of every point.
+ *   X        device, N x m (ld) of dtype dt
+ *   idx_out  device, N x k int32, overwritten; rows sorted by (d, index)
+ *   dist_out device, N x k float (nullable): squared distances of idx_out,
+ *            from the exact re-rank (FP32 rounding of a compensated sum)
+ * prec selects the candidate search (FP32 SIMT, or BF16 tensor-core GEMM);
+ * both finish with the same exact re-rank, so both return the same lists up
+ * to ties closer than the re-rank's rounding. */
+MECUCO_API mecuco_status mecuco_knn(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m,
+                         int64_t ld, int k, int include_self, mecuco_precision prec,
+                         int32_t *idx_out, float *dist_out, void *stream);
+
+/* Steps 2-4 (Sec. 3 Step 2; eq. svd_cov; eqs. tnull, tA, tB, fast_curv;
+ * Alg. 1 Fast branch): the Fast-mode curvature of every point.
+ *   X          device, N x m (ld) of dtype dt
+ *   idx        device, N x k int32 neighbour lists, or NULL to run
+ *              mecuco_knn first (with include_self and prec)
+ *   kappa_out  device, N floats, overwritten with K_i >= 0
+ *   lambda_out device, N x k floats (nullable): lambda_r = s_l^2/(k-1) in
+ *              descending order, zero past p
+ *   U_out      device, N x k x k floats (nullable): the k x k eigenvector
+ *              matrix U of X_c X_c^T (row r, column l), columns in the order
+ *              of lambda; the tangent basis is V_r = X_c^T U_p diag(s)^-1
+ *   s_out      device, N x k floats (nullable): singular values s_l of X_c */
+MECUCO_API mecuco_status mecuco_curvature(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m,
+                               int64_t ld, int k, const int32_t *idx, int include_self,
+                               mecuco_variant var, mecuco_precision prec, float *kappa_out,
+                               float *lambda_out, float *U_out, float *s_out, void *stream);
+
+/* Row-range forms (resumable chunked runs, sampled timing, per-rank shards):
+ * only query rows [row_begin, row_end) are processed; every point of X is still
+ * a candidate neighbour.  Outputs hold (row_end - row_begin) rows: row r of
+ * idx_out / kappa_out / ... belongs to point row_begin + r, and idx (if given)
+ * holds the neighbour lists of those rows only.  Same contracts otherwise. */
+MECUCO_API mecuco_status mecuco_knn_range(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N,
+                                          int64_t m, int64_t ld, int k, int include_self,
+                                          mecuco_precision prec, int64_t row_begin, int64_t row_end,
+                                          int32_t *idx_out, float *dist_out, void *stream);
+MECUCO_API mecuco_status mecuco_curvature_range(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N,
+                                                int64_t m, int64_t ld, int k, const int32_t *idx,
+                                                int include_self, mecuco_variant var,
+                                                mecuco_precision prec, int64_t row_begin,
+                                                int64_t row_end, float *kappa_out, float *lambda_out,
+                                                float *U_out, float *s_out, void *stream);
+
+/* The same computation with HOST buffers (pageable or pinned): X_host is
+ * copied to the device, the path runs, kappa (and idx if idx_host_out is not
+ * NULL) are copied back.  Synchronous.  Device buffers come from the
+ * context's workspace. */
+MECUCO_API mecuco_status mecuco_curvature_host(mecuco_t h, const void *X_host, mecuco_dtype dt, int64_t N,
+                                    int64_t m, int64_t ld, int k, int include_self,
+                                    mecuco_variant var, mecuco_precision prec,
+                                    float *kappa_host_out, int32_t *idx_host_out, void *stream);
+
+/* Status OR-ed on the device by the calls since the previous query, then
+ * cleared.  Synchronises `stream` first. */
+MECUCO_API mecuco_status mecuco_get_last_status(mecuco_t h, void *stream);
+
+/* Counters of the last call (synchronises `stream` first). */
+MECUCO_API mecuco_status mecuco_get_stats(mecuco_t h, mecuco_stats *out, void *stream);
+
+/* Per-stage device time (ms) and launch counts accumulated since the previous
+ * query while MECUCO_OPT_PROFILE is on; both arrays hold MECUCO_STAGE_COUNT
+ * entries.  Synchronises `stream`, then resets the totals. */
+MECUCO_API mecuco_status mecuco_get_stage_times(mecuco_t h, double *ms_out, int64_t *launches_out,
+                                                void *stream);
+
+/* Static description of a status code. */
+MECUCO_API const char *mecuco_status_string(mecuco_status st);
+
+/* Text of the last CUDA error seen by this thread ("" if none). */
+MECUCO_API const char *mecuco_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MECUCO_H */

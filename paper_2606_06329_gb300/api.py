@@ -1,0 +1,188 @@
+"""Python binding of the C ABI (argument marshalling only).
+
+Every function here forwards torch tensors' device pointers and the current
+CUDA stream to the same-named entry point of libmecuco.so; all arithmetic of
+the path runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _native as N
+
+_PREC = {"fp32": N.PREC_FP32, "bf16_mixed": N.PREC_BF16_MIXED}
+_VAR = {"literal": N.FAST_LITERAL, "haar": N.FAST_HAAR}
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return N.F32
+    if t.dtype == torch.bfloat16:
+        return N.BF16
+    raise TypeError(f"X must be float32 or bfloat16, got {t.dtype}")
+
+
+def _check_x(X: torch.Tensor, device: int):
+    if X.dim() != 2 or X.stride(1) != 1:
+        raise ValueError("X must be a 2-D tensor with unit column stride")
+    if not X.is_cuda or X.device.index != device:
+        raise ValueError(f"X must live on cuda:{device}")
+
+
+def _stream(device: int):
+    return C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """Owns one ``mecuco_t`` handle (device workspace, status word)."""
+
+    def __init__(self, device: int = 0):
+        self.lib = N.load()
+        self.device = int(device)
+        h = C.c_void_p()
+        N.check(self.lib.mecuco_create(C.byref(h), self.device), "mecuco_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.mecuco_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_option(self, opt: int, value: int):
+        N.check(self.lib.mecuco_set_option(self.handle, int(opt), int(value)), "mecuco_set_option")
+
+    # -- entry points -------------------------------------------------------
+    def mecuco_knn(self, X: torch.Tensor, k: int, include_self: bool = False, precision: str = "fp32",
+                   return_dist: bool = False):
+        _check_x(X, self.device)
+        n, m = X.shape
+        idx = torch.empty((n, k), dtype=torch.int32, device=X.device)
+        dist = torch.empty((n, k), dtype=torch.float32, device=X.device) if return_dist else None
+        st = self.lib.mecuco_knn(self.handle, _ptr(X), _dtype_code(X), n, m, X.stride(0), int(k),
+                                 int(bool(include_self)), _PREC[precision], _ptr(idx), _ptr(dist),
+                                 _stream(self.device))
+        N.check(st, "mecuco_knn")
+        return (idx, dist) if return_dist else idx
+
+    def mecuco_curvature(self, X: torch.Tensor, k: int, idx: torch.Tensor | None = None,
+                         include_self: bool = False, variant: str = "literal", precision: str = "fp32",
+                         return_lambda: bool = False, return_U: bool = False, return_s: bool = False):
+        _check_x(X, self.device)
+        n, m = X.shape
+        if idx is not None:
+            if idx.dtype != torch.int32 or tuple(idx.shape) != (n, k) or not idx.is_contiguous():
+                raise ValueError("idx must be a contiguous int32 (N, k) tensor")
+        dev = X.device
+        kappa = torch.empty(n, dtype=torch.float32, device=dev)
+        lam = torch.empty((n, k), dtype=torch.float32, device=dev) if return_lambda else None
+        U = torch.empty((n, k, k), dtype=torch.float32, device=dev) if return_U else None
+        s = torch.empty((n, k), dtype=torch.float32, device=dev) if return_s else None
+        st = self.lib.mecuco_curvature(self.handle, _ptr(X), _dtype_code(X), n, m, X.stride(0), int(k),
+                                       _ptr(idx), int(bool(include_self)), _VAR[variant], _PREC[precision],
+                                       _ptr(kappa), _ptr(lam), _ptr(U), _ptr(s), _stream(self.device))
+        N.check(st, "mecuco_curvature")
+        out = {"kappa": kappa}
+        if return_lambda:
+            out["lambda"] = lam
+        if return_U:
+            out["U"] = U
+        if return_s:
+            out["s"] = s
+        return out if (return_lambda or return_U or return_s) else kappa
+
+    def mecuco_knn_range(self, X: torch.Tensor, k: int, row_begin: int, row_end: int, include_self: bool = False,
+                         precision: str = "fp32", return_dist: bool = False):
+        _check_x(X, self.device)
+        n, m = X.shape
+        nr = row_end - row_begin
+        idx = torch.empty((nr, k), dtype=torch.int32, device=X.device)
+        dist = torch.empty((nr, k), dtype=torch.float32, device=X.device) if return_dist else None
+        st = self.lib.mecuco_knn_range(self.handle, _ptr(X), _dtype_code(X), n, m, X.stride(0), int(k),
+                                       int(bool(include_self)), _PREC[precision], int(row_begin), int(row_end),
+                                       _ptr(idx), _ptr(dist), _stream(self.device))
+        N.check(st, "mecuco_knn_range")
+        return (idx, dist) if return_dist else idx
+
+    def mecuco_curvature_range(self, X: torch.Tensor, k: int, row_begin: int, row_end: int,
+                               idx: torch.Tensor | None = None, include_self: bool = False,
+                               variant: str = "literal", precision: str = "fp32"):
+        _check_x(X, self.device)
+        n, m = X.shape
+        nr = row_end - row_begin
+        if idx is not None and (idx.dtype != torch.int32 or tuple(idx.shape) != (nr, k) or not idx.is_contiguous()):
+            raise ValueError("idx must be a contiguous int32 (row_end - row_begin, k) tensor")
+        kappa = torch.empty(nr, dtype=torch.float32, device=X.device)
+        st = self.lib.mecuco_curvature_range(self.handle, _ptr(X), _dtype_code(X), n, m, X.stride(0), int(k),
+                                             _ptr(idx), int(bool(include_self)), _VAR[variant], _PREC[precision],
+                                             int(row_begin), int(row_end), _ptr(kappa), None, None, None,
+                                             _stream(self.device))
+        N.check(st, "mecuco_curvature_range")
+        return kappa
+
+    def mecuco_get_stage_times(self) -> dict:
+        ms = (C.c_double * len(N.STAGES))()
+        cnt = (C.c_int64 * len(N.STAGES))()
+        N.check(self.lib.mecuco_get_stage_times(self.handle, ms, cnt, _stream(self.device)), "mecuco_get_stage_times")
+        return {name: (ms[i], cnt[i]) for i, name in enumerate(N.STAGES)}
+
+    def mecuco_curvature_host(self, X: torch.Tensor, k: int, include_self: bool = False,
+                              variant: str = "literal", precision: str = "fp32", return_idx: bool = False,
+                              kappa_out: torch.Tensor | None = None, idx_out: torch.Tensor | None = None):
+        """Host (CPU, ideally pinned) tensors in and out; copies happen inside the call."""
+        if X.is_cuda or X.dim() != 2 or X.stride(1) != 1:
+            raise ValueError("X must be a 2-D CPU tensor with unit column stride")
+        n, m = X.shape
+        kappa = kappa_out if kappa_out is not None else torch.empty(n, dtype=torch.float32)
+        idx = idx_out if idx_out is not None else (torch.empty((n, k), dtype=torch.int32) if return_idx else None)
+        st = self.lib.mecuco_curvature_host(self.handle, _ptr(X), _dtype_code(X), n, m, X.stride(0), int(k),
+                                            int(bool(include_self)), _VAR[variant], _PREC[precision],
+                                            _ptr(kappa), _ptr(idx), _stream(self.device))
+        N.check(st, "mecuco_curvature_host")
+        return (kappa, idx) if (return_idx or idx_out is not None) else kappa
+
+    def mecuco_get_last_status(self) -> int:
+        return int(self.lib.mecuco_get_last_status(self.handle, _stream(self.device)))
+
+    def mecuco_get_stats(self) -> dict:
+        st = N.mecuco_stats()
+        N.check(self.lib.mecuco_get_stats(self.handle, C.byref(st), _stream(self.device)), "mecuco_get_stats")
+        return {f: getattr(st, f) for f, _ in N.mecuco_stats._fields_}
+
+
+_default = {}
+
+
+def context(device: int = 0) -> Context:
+    if device not in _default:
+        _default[device] = Context(device)
+    return _default[device]
+
+
+def mecuco_knn(X, k, **kw):
+    return context(X.device.index or 0).mecuco_knn(X, k, **kw)
+
+
+def mecuco_curvature(X, k, **kw):
+    return context(X.device.index or 0).mecuco_curvature(X, k, **kw)
+
+
+def mecuco_curvature_host(X, k, device: int = 0, **kw):
+    return context(device).mecuco_curvature_host(X, k, **kw)

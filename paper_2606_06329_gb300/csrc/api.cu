@@ -1,0 +1,559 @@
+// api.cu - the C ABI declared in include/mecuco.h: context, workspace,
+// argument validation, stage profiling and the orchestration of the hot path
+// (kNN -> gather/centre/Gram/moments -> Jacobi -> estimator).
+#include <stdio.h>
+#include <string.h>
+
+#include <cstddef>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace mecuco;
+
+namespace {
+thread_local char g_errmsg[512] = "";
+
+void set_err(const char *where, cudaError_t e) {
+    snprintf(g_errmsg, sizeof(g_errmsg), "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Offsets into one device buffer, 256-byte aligned.  Sizing and carving use
+// the same sequence of take() calls, first with base == nullptr.
+struct Carver {
+    char *base;
+    size_t off;
+    explicit Carver(char *b, size_t start = 0) : base(b), off(start) {}
+    template <typename T>
+    T *take(size_t count) {
+        off = align_up(off, 256);
+        T *p = reinterpret_cast<T *>(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+struct EventPair {
+    cudaEvent_t a, b;
+    int stage;
+};
+}  // namespace
+
+struct mecuco_ctx {
+    int device = 0;
+    int num_sms = 0;
+    char *ws = nullptr;  // device workspace, grown on demand
+    size_t ws_bytes = 0;
+    char *io = nullptr;  // device copies of the host-buffer entry point
+    size_t io_bytes = 0;
+    DevCounters *ctr = nullptr;
+    int32_t *m3_items = nullptr;
+    int m3_items_k = -1;
+    // options
+    int64_t knn_margin = 32;
+    int jacobi_fp64 = -1;
+    int jacobi_max_sweeps = 40;
+    int64_t chunk_points = 0;
+    int64_t knn_qchunk = 0;
+    int profile = 0;
+    // per-call bookkeeping
+    int64_t launches = 0;
+    int64_t knn_rows = 0;
+    // profiler
+    std::vector<EventPair> events;
+    size_t events_used = 0;
+    double stage_ms[MECUCO_STAGE_COUNT] = {};
+    int64_t stage_n[MECUCO_STAGE_COUNT] = {};
+};
+
+namespace {
+
+#define CK(call)                                                                 \
+    do {                                                                         \
+        cudaError_t e_ = (call);                                                 \
+        if (e_ != cudaSuccess) { set_err(#call, e_); return MECUCO_ERR_CUDA; }   \
+    } while (0)
+
+mecuco_status flush_events(mecuco_t h) {
+    if (h->events_used == 0) return MECUCO_OK;
+    CK(cudaEventSynchronize(h->events[h->events_used - 1].b));
+    for (size_t i = 0; i < h->events_used; ++i) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, h->events[i].a, h->events[i].b));
+        h->stage_ms[h->events[i].stage] += ms;
+        h->stage_n[h->events[i].stage] += 1;
+    }
+    h->events_used = 0;
+    return MECUCO_OK;
+}
+
+mecuco_status prof_begin(mecuco_t h, int stage, cudaStream_t s, EventPair **out) {
+    *out = nullptr;
+    if (!h->profile) return MECUCO_OK;
+    if (h->events_used >= 4096) {
+        mecuco_status st = flush_events(h);
+        if (st != MECUCO_OK) return st;
+    }
+    if (h->events_used == h->events.size()) {
+        EventPair ep{};
+        CK(cudaEventCreate(&ep.a));
+        CK(cudaEventCreate(&ep.b));
+        h->events.push_back(ep);
+    }
+    EventPair *ep = &h->events[h->events_used++];
+    ep->stage = stage;
+    CK(cudaEventRecord(ep->a, s));
+    *out = ep;
+    return MECUCO_OK;
+}
+
+// Launch `call` (a launcher returning cudaError_t) as stage `stage` on stream s.
+#define LAUNCH(h, stage, s, call)                                                \
+    do {                                                                         \
+        EventPair *ep_ = nullptr;                                                \
+        mecuco_status ps_ = prof_begin((h), (stage), (s), &ep_);                 \
+        if (ps_ != MECUCO_OK) return ps_;                                        \
+        cudaError_t e_ = (call);                                                 \
+        if (e_ != cudaSuccess) { set_err(#call, e_); return MECUCO_ERR_CUDA; }   \
+        if (ep_) CK(cudaEventRecord(ep_->b, (s)));                               \
+        ++(h)->launches;                                                         \
+    } while (0)
+
+mecuco_status ensure(char *&buf, size_t &cur, size_t need) {
+    if (need <= cur) return MECUCO_OK;
+    if (buf) {
+        // earlier asynchronous work may still use the old buffer
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) { set_err("cudaDeviceSynchronize", e); return MECUCO_ERR_CUDA; }
+        cudaFree(buf);
+        buf = nullptr;
+        cur = 0;
+    }
+    size_t want = align_up(need + need / 8, 1 << 20);
+    cudaError_t e = cudaMalloc(&buf, want);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        e = cudaMalloc(&buf, need);
+        if (e != cudaSuccess) { (void)cudaGetLastError(); buf = nullptr; return MECUCO_ERR_OOM; }
+        want = need;
+    }
+    cur = want;
+    return MECUCO_OK;
+}
+
+mecuco_status check_common(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
+                           int k, int include_self) {
+    if (!h || !X) return MECUCO_ERR_INVALID_ARG;
+    if (dt != MECUCO_F32 && dt != MECUCO_BF16) return MECUCO_ERR_INVALID_ARG;
+    if (N < 2 || N >= (int64_t)1 << 31 || m < 1 || ld < m) return MECUCO_ERR_INVALID_ARG;
+    if (k < 2 || k > 64) return MECUCO_ERR_INVALID_ARG;
+    if (include_self != 0 && include_self != 1) return MECUCO_ERR_INVALID_ARG;
+    if ((int64_t)k > N - (include_self ? 0 : 1)) return MECUCO_ERR_INVALID_ARG;
+    return MECUCO_OK;
+}
+
+mecuco_status check_range(int64_t N, int64_t rb, int64_t re) {
+    if (rb < 0 || re > N || rb >= re) return MECUCO_ERR_INVALID_ARG;
+    return MECUCO_OK;
+}
+
+int candidate_capacity(mecuco_t h, int k) {
+    int64_t kc = k + h->knn_margin;
+    kc = (kc + 31) / 32 * 32;
+    if (kc > 128) kc = 128;
+    if (kc < k) kc = k;
+    return (int)kc;
+}
+
+struct KnnPlan {
+    int kc, nsplit;
+    int64_t qchunk;
+};
+
+KnnPlan plan_knn(mecuco_t h, int64_t N, int64_t nrows, int k) {
+    KnnPlan p;
+    p.kc = candidate_capacity(h, k);
+    p.qchunk = h->knn_qchunk > 0 ? h->knn_qchunk : (int64_t)1 << 18;
+    if (p.qchunk > nrows) p.qchunk = nrows;
+    // keep >= 2 CTAs per SM busy: split the candidate range when there are
+    // few query blocks (the re-rank then sees kc * nsplit candidates per row)
+    const int64_t qblocks = (p.qchunk + 127) / 128;
+    const int64_t want = 2LL * h->num_sms;
+    p.nsplit = 1;
+    if (qblocks < want) p.nsplit = (int)std::min<int64_t>((want + qblocks - 1) / qblocks, 1024 / p.kc);
+    while (p.nsplit > 1 && (N + p.nsplit - 1) / p.nsplit < p.kc) --p.nsplit;
+    return p;
+}
+
+// Scratch of run_knn, carved after `start`.
+void knn_scratch(Carver &c, const KnnPlan &p, int64_t N, float **norms, float **cd, int32_t **ci, int32_t **fl) {
+    *norms = c.take<float>((size_t)N);
+    *cd = c.take<float>((size_t)p.qchunk * p.nsplit * p.kc);
+    *ci = c.take<int32_t>((size_t)p.qchunk * p.nsplit * p.kc);
+    *fl = c.take<int32_t>((size_t)p.qchunk);
+}
+
+// kNN of query rows [rb, re) (outputs relative to rb); scratch at ws + start,
+// the workspace already sized by the caller.
+mecuco_status run_knn(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, int k,
+                      int include_self, mecuco_precision prec, int64_t rb, int64_t re, int32_t *idx_out,
+                      float *dist_out, cudaStream_t s, size_t start) {
+    if (prec != MECUCO_PREC_FP32) return MECUCO_ERR_UNSUPPORTED;
+    KnnPlan p = plan_knn(h, N, re - rb, k);
+    Carver c(h->ws, start);
+    float *norms, *cand_d;
+    int32_t *cand_i, *flags;
+    knn_scratch(c, p, N, &norms, &cand_d, &cand_i, &flags);
+    LAUNCH(h, MECUCO_STAGE_ROWNORM, s, launch_rownorm(X, dt, N, m, ld, norms, s));
+    for (int64_t q0 = rb; q0 < re; q0 += p.qchunk) {
+        int64_t nq = std::min(p.qchunk, re - q0);
+        int32_t *io = idx_out + (q0 - rb) * k;
+        float *dout = dist_out ? dist_out + (q0 - rb) * k : nullptr;
+        LAUNCH(h, MECUCO_STAGE_KNN_SEARCH, s,
+               launch_knn_simt(X, dt, N, m, ld, norms, q0, nq, p.kc, p.nsplit, include_self, cand_d, cand_i, s));
+        LAUNCH(h, MECUCO_STAGE_KNN_RERANK, s,
+               launch_knn_rerank(X, dt, N, m, ld, norms, q0, nq, p.kc, p.nsplit, k, cand_d, cand_i, io, dout, flags,
+                                 h->ctr, s));
+        LAUNCH(h, MECUCO_STAGE_KNN_FALLBACK, s,
+               launch_knn_fallback(X, dt, N, m, ld, q0, nq, k, include_self, flags, io, dout, h->ctr, s));
+    }
+    h->knn_rows += re - rb;
+    return MECUCO_OK;
+}
+
+size_t knn_bytes(mecuco_t h, int64_t N, int64_t nrows, int k, size_t start) {
+    KnnPlan p = plan_knn(h, N, nrows, k);
+    Carver c(nullptr, start);
+    float *a, *b;
+    int32_t *d, *e;
+    knn_scratch(c, p, N, &a, &b, &d, &e);
+    return c.off;
+}
+
+mecuco_status begin_call(mecuco_t h, cudaStream_t s) {
+    h->launches = 0;
+    h->knn_rows = 0;
+    CK(cudaSetDevice(h->device));
+    CK(cudaMemsetAsync(h->ctr, 0, offsetof(DevCounters, status), s));
+    return MECUCO_OK;
+}
+
+mecuco_status ensure_items(mecuco_t h, int k) {
+    if (h->m3_items_k == k) return MECUCO_OK;
+    if (h->m3_items) {
+        CK(cudaDeviceSynchronize());
+        cudaFree(h->m3_items);
+        h->m3_items = nullptr;
+        h->m3_items_k = -1;
+    }
+    int n = m3_items(k);
+    std::vector<int32_t> host((size_t)n);
+    m3_build_items(k, host.data());
+    if (cudaMalloc(&h->m3_items, sizeof(int32_t) * n) != cudaSuccess) {
+        (void)cudaGetLastError();
+        h->m3_items = nullptr;
+        return MECUCO_ERR_OOM;
+    }
+    CK(cudaMemcpy(h->m3_items, host.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+    h->m3_items_k = k;
+    return MECUCO_OK;
+}
+
+struct EstBufs {
+    float *G, *R, *Q, *M, *sig, *U;
+};
+void est_scratch(Carver &c, int64_t chunk, int k, EstBufs *b) {
+    b->G = c.take<float>((size_t)chunk * k * k);
+    b->R = c.take<float>((size_t)chunk * k);
+    b->Q = c.take<float>((size_t)chunk * k * k);
+    b->M = c.take<float>((size_t)chunk * m3_pair_floats(k));
+    b->sig = c.take<float>((size_t)chunk * k);
+    b->U = c.take<float>((size_t)chunk * k * k);
+}
+
+int64_t est_chunk(mecuco_t h, int64_t nrows, int k) {
+    const int64_t per_point = m3_pair_floats(k) + 3LL * k * k + 3LL * k;
+    int64_t chunk = h->chunk_points;
+    if (chunk <= 0) {
+        chunk = (int64_t)(((size_t)2 << 30) / (per_point * sizeof(float)));
+        chunk = std::max<int64_t>(256, std::min<int64_t>(chunk, 65536));
+    }
+    return std::min(chunk, nrows);
+}
+
+mecuco_status run_curvature(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, int k,
+                            const int32_t *idx, int include_self, mecuco_variant var, mecuco_precision prec,
+                            int64_t rb, int64_t re, float *kappa_out, float *lambda_out, float *U_out,
+                            float *s_out, cudaStream_t s) {
+    if (prec != MECUCO_PREC_FP32) return MECUCO_ERR_UNSUPPORTED;
+    mecuco_status st = ensure_items(h, k);
+    if (st != MECUCO_OK) return st;
+    const int64_t nrows = re - rb;
+    const int64_t chunk = est_chunk(h, nrows, k);
+    // workspace: [idx of the range, if computed here] then kNN scratch, reused by the estimator
+    const size_t idx_bytes = idx ? 0 : align_up((size_t)nrows * k * sizeof(int32_t), 256);
+    size_t need = idx ? 0 : knn_bytes(h, N, nrows, k, idx_bytes);
+    {
+        Carver c(nullptr, idx_bytes);
+        EstBufs b;
+        est_scratch(c, chunk, k, &b);
+        need = std::max(need, c.off);
+    }
+    st = ensure(h->ws, h->ws_bytes, need);
+    if (st != MECUCO_OK) return st;
+    const int32_t *nbr = idx;
+    if (!idx) {
+        int32_t *idx_buf = reinterpret_cast<int32_t *>(h->ws);
+        st = run_knn(h, X, dt, N, m, ld, k, include_self, prec, rb, re, idx_buf, nullptr, s, idx_bytes);
+        if (st != MECUCO_OK) return st;
+        nbr = idx_buf;
+    }
+    Carver c(h->ws, idx_bytes);
+    EstBufs b;
+    est_scratch(c, chunk, k, &b);
+    const int fp64 = h->jacobi_fp64 >= 0 ? h->jacobi_fp64 : (prec == MECUCO_PREC_BF16_MIXED ? 1 : 0);
+    for (int64_t p0 = 0; p0 < nrows; p0 += chunk) {
+        const int64_t np = std::min(chunk, nrows - p0);
+        const int32_t *nb = nbr + p0 * k;
+        float *Ud = U_out ? U_out + p0 * (int64_t)k * k : b.U;
+        LAUNCH(h, MECUCO_STAGE_GRAM, s,
+               launch_patch_gram(X, dt, N, m, ld, nb, k, 0, np, b.G, b.R, var == MECUCO_FAST_HAAR ? b.Q : nullptr,
+                                 h->ctr, s));
+        LAUNCH(h, MECUCO_STAGE_MOMENTS, s, launch_patch_m3(X, dt, N, m, ld, nb, k, 0, np, b.M, h->m3_items, h->ctr, s));
+        LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(b.G, k, np, fp64, h->jacobi_max_sweeps, b.sig, Ud, h->ctr, s));
+        LAUNCH(h, MECUCO_STAGE_ESTIMATOR, s,
+               launch_estimator(b.sig, Ud, b.M, b.R, b.Q, k, m, np, (int)var, kappa_out + p0,
+                                lambda_out ? lambda_out + p0 * k : nullptr, s_out ? s_out + p0 * k : nullptr, h->ctr,
+                                s));
+    }
+    return MECUCO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mecuco_status_string(mecuco_status st) {
+    switch (st) {
+        case MECUCO_OK: return "ok";
+        case MECUCO_ERR_INVALID_ARG: return "invalid argument";
+        case MECUCO_ERR_UNSUPPORTED: return "unsupported by this build";
+        case MECUCO_ERR_OOM: return "out of memory";
+        case MECUCO_ERR_CUDA: return "CUDA error";
+        case MECUCO_ERR_NOT_CONVERGED: return "eigensolver hit its sweep cap";
+        case MECUCO_ERR_TIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+const char *mecuco_last_error_message(void) { return g_errmsg; }
+
+mecuco_status mecuco_create(mecuco_t *out, int device) {
+    if (!out) return MECUCO_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) { set_err("cudaGetDeviceCount", e); return MECUCO_ERR_CUDA; }
+    if (device < 0 || device >= ndev) return MECUCO_ERR_INVALID_ARG;
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, device));
+    if (prop.major != 10 || prop.minor != 3) return MECUCO_ERR_UNSUPPORTED;
+    CK(cudaSetDevice(device));
+    mecuco_ctx *h = new (std::nothrow) mecuco_ctx();
+    if (!h) return MECUCO_ERR_OOM;
+    h->device = device;
+    h->num_sms = prop.multiProcessorCount;
+    if (cudaMalloc(&h->ctr, sizeof(DevCounters)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete h;
+        return MECUCO_ERR_OOM;
+    }
+    if (cudaMemset(h->ctr, 0, sizeof(DevCounters)) != cudaSuccess) {
+        cudaFree(h->ctr);
+        delete h;
+        return MECUCO_ERR_CUDA;
+    }
+    *out = h;
+    return MECUCO_OK;
+}
+
+mecuco_status mecuco_destroy(mecuco_t h) {
+    if (!h) return MECUCO_OK;
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    for (auto &ep : h->events) {
+        cudaEventDestroy(ep.a);
+        cudaEventDestroy(ep.b);
+    }
+    if (h->ws) cudaFree(h->ws);
+    if (h->io) cudaFree(h->io);
+    if (h->ctr) cudaFree(h->ctr);
+    if (h->m3_items) cudaFree(h->m3_items);
+    delete h;
+    return MECUCO_OK;
+}
+
+mecuco_status mecuco_set_option(mecuco_t h, mecuco_option opt, int64_t v) {
+    if (!h) return MECUCO_ERR_INVALID_ARG;
+    switch (opt) {
+        case MECUCO_OPT_KNN_MARGIN:
+            if (v < 0 || v > 96) return MECUCO_ERR_INVALID_ARG;
+            h->knn_margin = v;
+            break;
+        case MECUCO_OPT_JACOBI_FP64:
+            if (v < -1 || v > 1) return MECUCO_ERR_INVALID_ARG;
+            h->jacobi_fp64 = (int)v;
+            break;
+        case MECUCO_OPT_JACOBI_MAX_SWEEPS:
+            if (v < 1 || v > 1000) return MECUCO_ERR_INVALID_ARG;
+            h->jacobi_max_sweeps = (int)v;
+            break;
+        case MECUCO_OPT_CHUNK_POINTS:
+            if (v < 0) return MECUCO_ERR_INVALID_ARG;
+            h->chunk_points = v;
+            break;
+        case MECUCO_OPT_KNN_QUERY_CHUNK:
+            if (v < 0) return MECUCO_ERR_INVALID_ARG;
+            h->knn_qchunk = v;
+            break;
+        case MECUCO_OPT_PROFILE:
+            if (v < 0 || v > 1) return MECUCO_ERR_INVALID_ARG;
+            h->profile = (int)v;
+            break;
+        default: return MECUCO_ERR_INVALID_ARG;
+    }
+    return MECUCO_OK;
+}
+
+mecuco_status mecuco_knn_range(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, int k,
+                               int include_self, mecuco_precision prec, int64_t rb, int64_t re, int32_t *idx_out,
+                               float *dist_out, void *stream) {
+    mecuco_status st = check_common(h, X, dt, N, m, ld, k, include_self);
+    if (st != MECUCO_OK) return st;
+    if ((st = check_range(N, rb, re)) != MECUCO_OK) return st;
+    if (!idx_out) return MECUCO_ERR_INVALID_ARG;
+    if (prec != MECUCO_PREC_FP32 && prec != MECUCO_PREC_BF16_MIXED) return MECUCO_ERR_INVALID_ARG;
+    if (prec != MECUCO_PREC_FP32) return MECUCO_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = begin_call(h, s)) != MECUCO_OK) return st;
+    if ((st = ensure(h->ws, h->ws_bytes, knn_bytes(h, N, re - rb, k, 0))) != MECUCO_OK) return st;
+    return run_knn(h, X, dt, N, m, ld, k, include_self, prec, rb, re, idx_out, dist_out, s, 0);
+}
+
+mecuco_status mecuco_knn(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, int k,
+                         int include_self, mecuco_precision prec, int32_t *idx_out, float *dist_out, void *stream) {
+    return mecuco_knn_range(h, X, dt, N, m, ld, k, include_self, prec, 0, N, idx_out, dist_out, stream);
+}
+
+mecuco_status mecuco_curvature_range(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
+                                     int k, const int32_t *idx, int include_self, mecuco_variant var,
+                                     mecuco_precision prec, int64_t rb, int64_t re, float *kappa_out,
+                                     float *lambda_out, float *U_out, float *s_out, void *stream) {
+    mecuco_status st = check_common(h, X, dt, N, m, ld, k, include_self);
+    if (st != MECUCO_OK) return st;
+    if ((st = check_range(N, rb, re)) != MECUCO_OK) return st;
+    if (!kappa_out) return MECUCO_ERR_INVALID_ARG;
+    if (var != MECUCO_FAST_LITERAL && var != MECUCO_FAST_HAAR) return MECUCO_ERR_INVALID_ARG;
+    if (prec != MECUCO_PREC_FP32 && prec != MECUCO_PREC_BF16_MIXED) return MECUCO_ERR_INVALID_ARG;
+    if (prec != MECUCO_PREC_FP32) return MECUCO_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = begin_call(h, s)) != MECUCO_OK) return st;
+    return run_curvature(h, X, dt, N, m, ld, k, idx, include_self, var, prec, rb, re, kappa_out, lambda_out, U_out,
+                         s_out, s);
+}
+
+mecuco_status mecuco_curvature(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, int k,
+                               const int32_t *idx, int include_self, mecuco_variant var, mecuco_precision prec,
+                               float *kappa_out, float *lambda_out, float *U_out, float *s_out, void *stream) {
+    return mecuco_curvature_range(h, X, dt, N, m, ld, k, idx, include_self, var, prec, 0, N, kappa_out, lambda_out,
+                                  U_out, s_out, stream);
+}
+
+mecuco_status mecuco_curvature_host(mecuco_t h, const void *X_host, mecuco_dtype dt, int64_t N, int64_t m,
+                                    int64_t ld, int k, int include_self, mecuco_variant var, mecuco_precision prec,
+                                    float *kappa_host_out, int32_t *idx_host_out, void *stream) {
+    mecuco_status st = check_common(h, X_host, dt, N, m, ld, k, include_self);
+    if (st != MECUCO_OK) return st;
+    if (!kappa_host_out) return MECUCO_ERR_INVALID_ARG;
+    if (var != MECUCO_FAST_LITERAL && var != MECUCO_FAST_HAAR) return MECUCO_ERR_INVALID_ARG;
+    if (prec != MECUCO_PREC_FP32 && prec != MECUCO_PREC_BF16_MIXED) return MECUCO_ERR_INVALID_ARG;
+    if (prec != MECUCO_PREC_FP32) return MECUCO_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = begin_call(h, s)) != MECUCO_OK) return st;
+    const size_t elt = dt == MECUCO_BF16 ? 2 : 4;
+    const size_t xbytes = ((size_t)(N - 1) * ld + m) * elt;
+    Carver t(nullptr);
+    t.take<char>(xbytes);
+    t.take<float>((size_t)N);
+    t.take<int32_t>((size_t)N * k);
+    if ((st = ensure(h->io, h->io_bytes, t.off)) != MECUCO_OK) return st;
+    Carver c(h->io);
+    char *Xd = c.take<char>(xbytes);
+    float *kd = c.take<float>((size_t)N);
+    int32_t *id = c.take<int32_t>((size_t)N * k);
+    CK(cudaMemcpyAsync(Xd, X_host, xbytes, cudaMemcpyHostToDevice, s));
+    if ((st = ensure(h->ws, h->ws_bytes, knn_bytes(h, N, N, k, 0))) != MECUCO_OK) return st;
+    if ((st = run_knn(h, Xd, dt, N, m, ld, k, include_self, prec, 0, N, id, nullptr, s, 0)) != MECUCO_OK) return st;
+    if ((st = run_curvature(h, Xd, dt, N, m, ld, k, id, include_self, var, prec, 0, N, kd, nullptr, nullptr, nullptr,
+                            s)) != MECUCO_OK)
+        return st;
+    CK(cudaMemcpyAsync(kappa_host_out, kd, sizeof(float) * N, cudaMemcpyDeviceToHost, s));
+    if (idx_host_out) CK(cudaMemcpyAsync(idx_host_out, id, sizeof(int32_t) * N * k, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return MECUCO_OK;
+}
+
+mecuco_status mecuco_get_last_status(mecuco_t h, void *stream) {
+    if (!h) return MECUCO_ERR_INVALID_ARG;
+    CK(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    DevCounters c;
+    CK(cudaMemcpyAsync(&c, h->ctr, sizeof(c), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaMemsetAsync(&h->ctr->status, 0, sizeof(unsigned), s));
+    CK(cudaStreamSynchronize(s));
+    if (c.status & DEV_TIMEOUT) return MECUCO_ERR_TIMEOUT;
+    if (c.status & DEV_INVALID) return MECUCO_ERR_INVALID_ARG;
+    if (c.status & DEV_NOT_CONVERGED) return MECUCO_ERR_NOT_CONVERGED;
+    return MECUCO_OK;
+}
+
+mecuco_status mecuco_get_stats(mecuco_t h, mecuco_stats *out, void *stream) {
+    if (!h || !out) return MECUCO_ERR_INVALID_ARG;
+    CK(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    DevCounters c;
+    CK(cudaMemcpyAsync(&c, h->ctr, sizeof(c), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    out->knn_rows = h->knn_rows;
+    out->knn_uncertified = (int64_t)c.knn_uncertified;
+    out->knn_fallback_rows = (int64_t)c.knn_fallback_rows;
+    out->jacobi_max_sweeps = (int64_t)c.jacobi_max_sweeps;
+    out->jacobi_not_converged = (int64_t)c.jacobi_not_converged;
+    out->rank_deficient = (int64_t)c.rank_deficient;
+    out->kernel_launches = h->launches;
+    return MECUCO_OK;
+}
+
+mecuco_status mecuco_get_stage_times(mecuco_t h, double *ms_out, int64_t *launches_out, void *stream) {
+    if (!h || !ms_out || !launches_out) return MECUCO_ERR_INVALID_ARG;
+    CK(cudaSetDevice(h->device));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    mecuco_status st = flush_events(h);
+    if (st != MECUCO_OK) return st;
+    for (int i = 0; i < MECUCO_STAGE_COUNT; ++i) {
+        ms_out[i] = h->stage_ms[i];
+        launches_out[i] = h->stage_n[i];
+        h->stage_ms[i] = 0.0;
+        h->stage_n[i] = 0;
+    }
+    return MECUCO_OK;
+}
+
+}  // extern "C"

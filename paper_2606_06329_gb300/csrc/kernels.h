@@ -1,0 +1,96 @@
+// kernels.h - host launchers of the MeCuCo CUDA kernels (internal, C++ linkage).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mecuco.h"
+
+namespace mecuco {
+
+struct DevCounters;
+
+// ---- Step 1: kNN -----------------------------------------------------------
+// Squared row norms |x_i|^2 (FP32 accumulation), i in [0, N).
+cudaError_t launch_rownorm(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
+                           float *norms, cudaStream_t s);
+
+// Candidate search, plain FP32 on the CUDA cores.  Queries [q0, q0 + nq) against
+// all N rows, candidate range split in `nsplit` parts; per (query, split) the
+// kc smallest approximate distances |x|^2 + |y|^2 - 2 x.y are written to
+// cand_d / cand_i at [(q - q0) * nsplit + split] * kc (unused slots: +inf, -1).
+cudaError_t launch_knn_simt(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
+                            const float *norms, int64_t q0, int64_t nq, int kc, int nsplit,
+                            int include_self, float *cand_d, int32_t *cand_i, cudaStream_t s);
+
+// Candidate search, BF16 operands on the tensor cores (tcgen05, TMEM accumulators,
+// TMA-fed shared memory), same output contract as launch_knn_simt.  Xb is BF16
+// row-major with ldb % 8 == 0 and a 16-byte aligned base (X itself when it is
+// stored that way, else a copy made by launch_to_bf16).  kc <= 128.
+cudaError_t launch_knn_tc(const void *Xb, int64_t N, int64_t m, int64_t ldb, const float *norms,
+                          int64_t q0, int64_t nq, int kc, int nsplit, int include_self,
+                          float *cand_d, int32_t *cand_i, DevCounters *ctr, cudaStream_t s);
+size_t knn_tc_smem_bytes(int kc);
+// BF16 copy of X (round to nearest even) with leading dimension ldb >= m.
+cudaError_t launch_to_bf16(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, void *Y,
+                           int64_t ldb, cudaStream_t s);
+
+// Exact re-rank of the L = kc * nsplit candidates of each query by a
+// compensated (float-float) sum of (x_a - y_a)^2, top-k by (distance, index),
+// and the certification test; uncertified rows get flags[q - q0] = 1.
+// idx_out / dist_out point at query q0's row (row q - q0 is written).
+cudaError_t launch_knn_rerank(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
+                              const float *norms, int64_t q0, int64_t nq, int kc, int nsplit, int k,
+                              const float *cand_d, const int32_t *cand_i, int32_t *idx_out,
+                              float *dist_out, int32_t *flags, DevCounters *ctr, cudaStream_t s);
+
+// Exact full scan for the flagged rows of [q0, q0 + nq) (outputs as above).
+cudaError_t launch_knn_fallback(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
+                                int64_t q0, int64_t nq, int k, int include_self, const int32_t *flags,
+                                int32_t *idx_out, float *dist_out, DevCounters *ctr, cudaStream_t s);
+
+// ---- Steps 2-3: patch moments -------------------------------------------
+// For points [p0, p0 + np) (idx row p, outputs at p - p0); callers pass idx
+// already offset to the chunk and p0 = 0.  Centred patch X_c from idx; writes
+//   G   np x k x k   X_c X_c^T (full symmetric)
+//   R   np x k       X_c 1_m
+//   Q   np x k x k   X_c diag(c) X_c^T, c_a = sum_j X_c[j,a]^2   (nullable)
+// Neighbour indices outside [0, N) are read as row 0 and raise
+// MECUCO_ERR_INVALID_ARG in the device status word.
+cudaError_t launch_patch_gram(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
+                              const int32_t *idx, int k, int64_t p0, int64_t np, float *G,
+                              float *R, float *Q, DevCounters *ctr, cudaStream_t s);
+
+// Third moments M[j,r,t] = sum_a X_c[j,a] X_c[r,a] X_c[t,a], stored pair-major:
+// D[pair(a,b)][c] = M[a][b][c] for a <= b, every c; np x m3_pair_floats(k) floats.
+// `items` is the work-item list built by m3_build_items.
+cudaError_t launch_patch_m3(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
+                            const int32_t *idx, int k, int64_t p0, int64_t np, float *M,
+                            const int32_t *items, DevCounters *ctr, cudaStream_t s);
+
+__host__ __device__ inline int pair_index(int a, int b, int k) { return a * k - (a * (a - 1)) / 2 + (b - a); }
+inline int64_t m3_pair_floats(int k) { return (int64_t)k * (k + 1) / 2 * k; }
+#ifdef __CUDACC__
+__device__ inline int64_t m3_pair_floats_d(int k) { return (int64_t)k * (k + 1) / 2 * k; }
+#endif
+// Work items (j, Rb, Tb) with Rb >= j / 8 and Tb >= Rb over nb = ceil(k / 8)
+// blocks of 8, packed j | Rb << 8 | Tb << 16.
+int m3_items(int k);
+void m3_build_items(int k, int32_t *items /* m3_items(k) */);
+
+// ---- Step 3: k x k eigensolve -----------------------------------------------
+// One warp per patch, parallel-order two-sided Jacobi.  G: np x k x k.
+// Outputs sigma (np x k, descending) and U (np x k x k, column l = eigenvector).
+cudaError_t launch_jacobi(const float *G, int k, int64_t np, int fp64, int max_sweeps,
+                          float *sigma, float *U, DevCounters *ctr, cudaStream_t s);
+
+// ---- Step 4: k-space estimator ----------------------------------------------
+// sigma/U from launch_jacobi, M pair-major from launch_patch_m3, R and Q from
+// launch_patch_gram (Q only for the Haar variant).  Writes kappa (np) and,
+// when not NULL, lambda_out (np x k) and the singular values s_out (np x k).
+cudaError_t launch_estimator(const float *sigma, const float *U, const float *M, const float *R,
+                             const float *Q, int k, int64_t m, int64_t np, int variant,
+                             float *kappa, float *lambda_out, float *s_out, DevCounters *ctr,
+                             cudaStream_t s);
+
+}  // namespace mecuco

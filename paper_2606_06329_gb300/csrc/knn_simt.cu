@@ -1,0 +1,390 @@
+// knn_simt.cu - Step 1 (Sec. 3 Step 1, eq. knn; Alg. 1 kNN-Graph): candidate
+// search with FP32 arithmetic on the CUDA cores, the exact re-rank with its
+// certification test, and the exact full-scan fallback.
+//
+// Candidate search: a CTA owns BM = 128 query rows and sweeps the candidate
+// rows of its split in BN = 128 tiles.  Each of 256 threads accumulates an
+// 8 x 8 block of dot products x_i . y_j over BK = 8 wide K slices staged in
+// shared memory; the epilogue forms d~ = |x|^2 + |y|^2 - 2 x.y and one thread
+// per query row folds the tile into that row's list of the kc smallest d~
+// (unsorted, with its current maximum tracked as the admission threshold).
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mecuco {
+
+template <typename T>
+__global__ void rownorm_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld,
+                               float *__restrict__ out) {
+    int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    int lane = threadIdx.x & 31;
+    if (row >= N) return;
+    const T *x = X + row * ld;
+    float acc = 0.f;
+    for (int64_t a = lane; a < m; a += 32) {
+        float v = load_elem(x + a);
+        acc = fmaf(v, v, acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) out[row] = acc;
+}
+
+cudaError_t launch_rownorm(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
+                           float *norms, cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    dim3 block(256), grid((unsigned)((N + 7) / 8));
+    if (dt == MECUCO_BF16)
+        rownorm_kernel<<<grid, block, 0, s>>>((const __nv_bfloat16 *)X, N, m, ld, norms);
+    else
+        rownorm_kernel<<<grid, block, 0, s>>>((const float *)X, N, m, ld, norms);
+    return cudaGetLastError();
+}
+
+namespace {
+constexpr int SBM = 128, SBN = 128, SBK = 8, STHREADS = 256;
+
+__device__ __forceinline__ void list_rescan(const float *Ld, int kc, int stride, int row, float &thr,
+                                            int &slot) {
+    float mx = -INFINITY;
+    int sl = 0;
+    for (int s = 0; s < kc; ++s) {
+        float v = Ld[s * stride + row];
+        if (v > mx) { mx = v; sl = s; }
+    }
+    thr = mx;
+    slot = sl;
+}
+}  // namespace
+
+template <typename T>
+__global__ void __launch_bounds__(STHREADS, 1)
+knn_simt_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld,
+                const float *__restrict__ norms, int64_t q0, int64_t nq, int kc, int nsplit,
+                int include_self, float *__restrict__ cand_d, int32_t *__restrict__ cand_i) {
+    extern __shared__ float smem[];
+    float *As = smem;                     // [SBK][SBM]
+    float *Bs = As + SBK * SBM;           // [SBK][SBN]
+    float *Ds = Bs + SBK * SBN;           // [SBM][SBN + 1]
+    float *qns = Ds + SBM * (SBN + 1);    // [SBM]
+    float *cns = qns + SBM;               // [SBN]
+    float *Ld = cns + SBN;                // [kc][SBM]
+    int *Li = reinterpret_cast<int *>(Ld + kc * SBM);  // [kc][SBM]
+
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t qb = q0 + (int64_t)blockIdx.x * SBM;
+    const int64_t qend = q0 + nq;
+    const int split = blockIdx.y;
+    const int64_t per = (N + nsplit - 1) / nsplit;
+    const int64_t cbeg = (int64_t)split * per;
+    const int64_t cend = min(N, cbeg + per);
+
+    for (int r = tid; r < SBM; r += STHREADS) qns[r] = (qb + r < qend) ? norms[qb + r] : 0.f;
+    int cnt = 0, slot = 0;
+    float thr = INFINITY;
+
+    for (int64_t c0 = cbeg; c0 < cend; c0 += SBN) {
+        for (int c = tid; c < SBN; c += STHREADS) cns[c] = (c0 + c < cend) ? norms[c0 + c] : 0.f;
+        float acc[8][8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+        for (int64_t k0 = 0; k0 < m; k0 += SBK) {
+            // stage the BM x BK query slice and BN x BK candidate slice (transposed)
+#pragma unroll
+            for (int e = 0; e < (SBM * SBK) / STHREADS; ++e) {
+                int lin = tid + e * STHREADS;
+                int r = lin / SBK, kk = lin % SBK;
+                int64_t gq = qb + r, ga = k0 + kk;
+                As[kk * SBM + r] = (gq < qend && ga < m) ? load_elem(X + gq * ld + ga) : 0.f;
+                int64_t gc = c0 + r;
+                Bs[kk * SBN + r] = (gc < cend && ga < m) ? load_elem(X + gc * ld + ga) : 0.f;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < SBK; ++kk) {
+                float a[8], b[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) a[i] = As[kk * SBM + ty + 16 * i];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) b[j] = Bs[kk * SBN + tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+            }
+            __syncthreads();
+        }
+        // epilogue: approximate distances into Ds
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            int r = ty + 16 * i;
+            int64_t gq = qb + r;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                int c = tx + 16 * j;
+                int64_t gc = c0 + c;
+                float d = qns[r] + cns[c] - 2.f * acc[i][j];
+                if (gq >= qend || gc >= cend || (!include_self && gc == gq)) d = INFINITY;
+                Ds[r * (SBN + 1) + c] = d;
+            }
+        }
+        __syncthreads();
+        if (tid < SBM) {
+            const int row = tid;
+            for (int c = 0; c < SBN; ++c) {
+                float d = Ds[row * (SBN + 1) + c];
+                if (!(d < thr)) continue;
+                int j = (int)(c0 + c);
+                if (cnt < kc) {
+                    Ld[cnt * SBM + row] = d;
+                    Li[cnt * SBM + row] = j;
+                    ++cnt;
+                    if (cnt == kc) list_rescan(Ld, kc, SBM, row, thr, slot);
+                } else {
+                    Ld[slot * SBM + row] = d;
+                    Li[slot * SBM + row] = j;
+                    list_rescan(Ld, kc, SBM, row, thr, slot);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (tid < SBM && qb + tid < qend) {
+        int64_t base = ((qb + tid - q0) * nsplit + split) * (int64_t)kc;
+        for (int s = 0; s < kc; ++s) {
+            bool used = s < cnt;
+            cand_d[base + s] = used ? Ld[s * SBM + tid] : INFINITY;
+            cand_i[base + s] = used ? Li[s * SBM + tid] : -1;
+        }
+    }
+}
+
+cudaError_t launch_knn_simt(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
+                            const float *norms, int64_t q0, int64_t nq, int kc, int nsplit,
+                            int include_self, float *cand_d, int32_t *cand_i, cudaStream_t s) {
+    if (nq <= 0) return cudaSuccess;
+    size_t smem = sizeof(float) * (size_t)(2 * SBK * SBM + SBM * (SBN + 1) + SBM + SBN) +
+                  (size_t)kc * SBM * (sizeof(float) + sizeof(int));
+    dim3 grid((unsigned)((nq + SBM - 1) / SBM), (unsigned)nsplit), block(STHREADS);
+    cudaError_t e;
+    if (dt == MECUCO_BF16) {
+        e = cudaFuncSetAttribute(knn_simt_kernel<__nv_bfloat16>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        knn_simt_kernel<<<grid, block, smem, s>>>((const __nv_bfloat16 *)X, N, m, ld, norms, q0, nq,
+                                                  kc, nsplit, include_self, cand_d, cand_i);
+    } else {
+        e = cudaFuncSetAttribute(knn_simt_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        knn_simt_kernel<<<grid, block, smem, s>>>((const float *)X, N, m, ld, norms, q0, nq, kc,
+                                                  nsplit, include_self, cand_d, cand_i);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Exact re-rank + certification.  One warp per query row.  Each candidate's
+// squared distance sum_a (x_a - y_a)^2 is accumulated as a float-float pair
+// (TwoSum of the difference, FMA TwoProd of the square), so it carries ~2^-44
+// relative error: ranks agree with an FP64 brute force except at ties closer
+// than that.  Certification: every row left out of the candidate set has
+// d~ >= thr (the smallest admission threshold of the full splits), so its true
+// distance is >= thr - delta with delta bounding |d~ - d|; the row is certified
+// when thr - delta exceeds the exact k-th distance.  delta is taken as 4x the
+// largest |d~ - d| seen on this row's own candidates plus 2^-16 (|x|^2 + |y|max^2)
+// relative slack: the accumulation error of the candidate search has no
+// documented worst-case bound on the tensor-core path, so the test is an
+// a-posteriori one with a safety factor, and rows failing it are re-solved
+// exactly by the full scan.
+// ---------------------------------------------------------------------------
+constexpr int RR_WARPS = 4;
+constexpr int RR_MAXL = 1024;
+
+template <typename T>
+__global__ void __launch_bounds__(RR_WARPS * 32)
+knn_rerank_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld,
+                  const float *__restrict__ norms, int64_t q0, int64_t nq, int kc, int nsplit, int k,
+                  const float *__restrict__ cand_d, const int32_t *__restrict__ cand_i,
+                  int32_t *__restrict__ idx_out, float *__restrict__ dist_out,
+                  int32_t *__restrict__ flags, DevCounters *ctr) {
+    extern __shared__ float rsm[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int L = kc * nsplit;
+    float *hi = rsm + (size_t)w * L * 3;
+    float *lo = hi + L;
+    int *ci = reinterpret_cast<int *>(lo + L);
+    const int64_t qi = (int64_t)blockIdx.x * RR_WARPS + w;
+    if (qi >= nq) return;
+    const int64_t q = q0 + qi;
+    const float *cd = cand_d + qi * (int64_t)L;
+    const int32_t *cidx = cand_i + qi * (int64_t)L;
+    const T *xq = X + q * ld;
+
+    float err_obs = 0.f, nmax = 0.f;
+    for (int c = 0; c < L; ++c) {
+        int j = cidx[c];
+        ff acc{0.f, 0.f};
+        if (j >= 0) {
+            const T *xj = X + (int64_t)j * ld;
+            for (int64_t a = lane; a < m; a += 32) ff_acc_sqdiff(acc, load_elem(xq + a), load_elem(xj + a));
+            acc = ff_warp_sum(acc);
+            float approx = cd[c];
+            err_obs = fmaxf(err_obs, fabsf(approx - acc.hi));
+            nmax = fmaxf(nmax, norms[j]);
+        } else {
+            acc.hi = INFINITY;
+        }
+        if (lane == 0) { hi[c] = acc.hi; lo[c] = acc.lo; ci[c] = j; }
+    }
+    __syncwarp();
+    // thresholds: a split whose list is full admitted only d~ < its max
+    float thr = INFINITY;
+    for (int sp = 0; sp < nsplit; ++sp) {
+        float mx = -INFINITY;
+        bool full = true;
+        for (int c = lane; c < kc; c += 32) {
+            float v = cd[sp * kc + c];
+            full = full && (cidx[sp * kc + c] >= 0);
+            mx = fmaxf(mx, v);
+        }
+        mx = warp_max(mx);
+        full = __all_sync(0xffffffffu, full);
+        if (full) thr = fminf(thr, mx);
+    }
+    // rank each candidate by (hi, lo, index); write the k best in order
+    float theta = 0.f;
+    for (int c = lane; c < L; c += 32) {
+        int j = ci[c];
+        if (j < 0) continue;
+        ff me{hi[c], lo[c]};
+        int rank = 0;
+        for (int o = 0; o < L; ++o) {
+            if (ci[o] < 0) continue;
+            if (ff_less(ff{hi[o], lo[o]}, ci[o], me, j)) ++rank;
+        }
+        if (rank < k) {
+            idx_out[qi * k + rank] = j;
+            if (dist_out) dist_out[qi * k + rank] = me.hi + me.lo;
+        }
+        if (rank == k - 1) theta = me.hi;
+    }
+    theta = warp_max(theta);
+    if (lane == 0) {
+        float delta = 4.f * err_obs + ldexpf(norms[q] + nmax, -16);
+        int ok = (thr == INFINITY) || (thr - delta > theta);
+        flags[qi] = ok ? 0 : 1;
+        if (!ok) atomicAdd(&ctr->knn_uncertified, 1ull);
+    }
+}
+
+cudaError_t launch_knn_rerank(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
+                              const float *norms, int64_t q0, int64_t nq, int kc, int nsplit, int k,
+                              const float *cand_d, const int32_t *cand_i, int32_t *idx_out,
+                              float *dist_out, int32_t *flags, DevCounters *ctr, cudaStream_t s) {
+    if (nq <= 0) return cudaSuccess;
+    int L = kc * nsplit;
+    if (L > RR_MAXL) return cudaErrorInvalidValue;
+    size_t smem = (size_t)RR_WARPS * L * 3 * sizeof(float);
+    dim3 grid((unsigned)((nq + RR_WARPS - 1) / RR_WARPS)), block(RR_WARPS * 32);
+    cudaError_t e;
+    if (dt == MECUCO_BF16) {
+        e = cudaFuncSetAttribute(knn_rerank_kernel<__nv_bfloat16>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        knn_rerank_kernel<<<grid, block, smem, s>>>((const __nv_bfloat16 *)X, N, m, ld, norms, q0, nq,
+                                                    kc, nsplit, k, cand_d, cand_i, idx_out, dist_out,
+                                                    flags, ctr);
+    } else {
+        e = cudaFuncSetAttribute(knn_rerank_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        knn_rerank_kernel<<<grid, block, smem, s>>>((const float *)X, N, m, ld, norms, q0, nq, kc,
+                                                    nsplit, k, cand_d, cand_i, idx_out, dist_out, flags,
+                                                    ctr);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Exact full scan for flagged rows: one CTA of 8 warps per query; warp w takes
+// candidates j = w, w + 8, ...; each distance is a warp-cooperative compensated
+// sum; lane 0 keeps the warp's k best in shared memory (sorted insertion);
+// finally the 8 lists are merged by rank.
+// ---------------------------------------------------------------------------
+constexpr int FB_WARPS = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(FB_WARPS * 32)
+knn_fallback_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, int64_t q0,
+                    int64_t nq, int k, int include_self, const int32_t *__restrict__ flags,
+                    int32_t *__restrict__ idx_out, float *__restrict__ dist_out, DevCounters *ctr) {
+    extern __shared__ float fsm[];
+    float *bh = fsm;                       // [FB_WARPS][k]
+    float *bl = bh + FB_WARPS * k;         // [FB_WARPS][k]
+    int *bi = reinterpret_cast<int *>(bl + FB_WARPS * k);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t qi = blockIdx.x; qi < nq; qi += gridDim.x) {
+        if (flags[qi] == 0) continue;  // uniform across the CTA
+        const int64_t q = q0 + qi;
+        const T *xq = X + q * ld;
+        float *mh = bh + w * k, *ml = bl + w * k;
+        int *mi = bi + w * k;
+        if (lane == 0)
+            for (int s = 0; s < k; ++s) { mh[s] = INFINITY; ml[s] = 0.f; mi[s] = 0x7fffffff; }
+        __syncwarp();
+        for (int64_t j = w; j < N; j += FB_WARPS) {
+            if (!include_self && j == q) continue;
+            const T *xj = X + j * ld;
+            ff acc{0.f, 0.f};
+            for (int64_t a = lane; a < m; a += 32) ff_acc_sqdiff(acc, load_elem(xq + a), load_elem(xj + a));
+            acc = ff_warp_sum(acc);
+            if (lane == 0 && ff_less(acc, (int)j, ff{mh[k - 1], ml[k - 1]}, mi[k - 1])) {
+                int pos = k - 1;
+                while (pos > 0 && ff_less(acc, (int)j, ff{mh[pos - 1], ml[pos - 1]}, mi[pos - 1])) {
+                    mh[pos] = mh[pos - 1]; ml[pos] = ml[pos - 1]; mi[pos] = mi[pos - 1];
+                    --pos;
+                }
+                mh[pos] = acc.hi; ml[pos] = acc.lo; mi[pos] = (int)j;
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        // merge: rank every entry among all FB_WARPS * k entries
+        for (int e = threadIdx.x; e < FB_WARPS * k; e += blockDim.x) {
+            if (bi[e] == 0x7fffffff) continue;
+            ff me{bh[e], bl[e]};
+            int rank = 0;
+            for (int o = 0; o < FB_WARPS * k; ++o)
+                if (bi[o] != 0x7fffffff && ff_less(ff{bh[o], bl[o]}, bi[o], me, bi[e])) ++rank;
+            if (rank < k) {
+                idx_out[qi * k + rank] = bi[e];
+                if (dist_out) dist_out[qi * k + rank] = me.hi + me.lo;
+            }
+        }
+        if (threadIdx.x == 0) atomicAdd(&ctr->knn_fallback_rows, 1ull);
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_knn_fallback(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
+                                int64_t q0, int64_t nq, int k, int include_self, const int32_t *flags,
+                                int32_t *idx_out, float *dist_out, DevCounters *ctr, cudaStream_t s) {
+    if (nq <= 0) return cudaSuccess;
+    size_t smem = (size_t)FB_WARPS * k * 3 * sizeof(float);
+    unsigned grid = (unsigned)(nq < 4096 ? nq : 4096);
+    if (dt == MECUCO_BF16)
+        knn_fallback_kernel<<<grid, FB_WARPS * 32, smem, s>>>((const __nv_bfloat16 *)X, N, m, ld, q0, nq,
+                                                              k, include_self, flags, idx_out, dist_out,
+                                                              ctr);
+    else
+        knn_fallback_kernel<<<grid, FB_WARPS * 32, smem, s>>>((const float *)X, N, m, ld, q0, nq, k,
+                                                              include_self, flags, idx_out, dist_out, ctr);
+    return cudaGetLastError();
+}
+
+}  // namespace mecuco

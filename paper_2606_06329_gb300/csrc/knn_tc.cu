@@ -1,0 +1,321 @@
+// knn_tc.cu - Step 1 (Sec. 3 Step 1, eq. knn; Alg. 1 kNN-Graph) candidate
+// search on the 5th-generation tensor cores: BF16 x BF16 -> FP32 distance GEMM
+// with the per-row candidate selection fused into the TMEM drain.
+//
+// CTA = 128 query rows (the MMA's M, one TMEM lane each) sweeping its split of
+// the candidate rows in tiles of 256 (the MMA's N).  Warp roles:
+//   warp 0      TMA producer: for every (candidate tile, 64-wide K block) loads
+//               the 128 x 64 query slice and the 256 x 64 candidate slice
+//               (128-byte swizzled, zero-filled past the matrix edges) into a
+//               NSTAGE-deep ring of shared-memory stages.
+//   warp 1      allocates 512 TMEM columns (two 256-column FP32 accumulators)
+//               and issues tcgen05.mma (M=128, N=256, K=16) from one lane,
+//               committing each stage back to the producer and each finished
+//               tile to the epilogue.
+//   warps 2-5   epilogue: drain one accumulator (thread = query row) while the
+//               MMA fills the other; d~ = |x|^2 + |y|^2 - 2 x.y; values below
+//               the row's admission threshold enter its kc-slot candidate list
+//               (distances in shared memory, indices straight to global).
+// Every mbarrier wait is bounded; a timeout sets MECUCO_ERR_TIMEOUT in the
+// device status word, raises a CTA-wide abort flag, drains the copies and MMAs
+// already in flight (also bounded), frees TMEM and returns.
+#include <cudaTypedefs.h>
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc_ptx.cuh"
+
+namespace mecuco {
+
+namespace {
+constexpr int TBM = 128;        // query rows per CTA (MMA M)
+constexpr int TBN = 256;        // candidate rows per tile (MMA N)
+constexpr int TBK = 64;         // K elements per stage (one 128-byte swizzle row)
+constexpr int NSTAGE = 3;
+constexpr int A_BYTES = TBM * TBK * 2;   // 16 KB
+constexpr int B_BYTES = TBN * TBK * 2;   // 32 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int TC_THREADS = 192;
+constexpr long long WAIT_LIMIT = 4000000000LL;  // ~2 s of SM clock per wait
+constexpr uint32_t IDESC = tc::idesc_bf16_f32(TBM, TBN);
+
+struct ListState {
+    float thr;  // admission threshold: the largest distance held once the list is full
+    int cnt;    // slots in use
+    int slot;   // slot holding thr
+};
+
+// Rare path of the drain: put (d, c) into the row's kc-slot list (distances in
+// shared memory at Ld[slot * TBM + row], indices to global at out[slot]); once
+// the list is full each admission replaces the current maximum.
+__device__ __noinline__ ListState list_insert(ListState st, float d, int c, float *Ld, int32_t *out, int row, int kc) {
+    int s = st.cnt < kc ? st.cnt : st.slot;
+    Ld[s * TBM + row] = d;
+    out[s] = c;
+    if (st.cnt < kc) {
+        ++st.cnt;
+        if (st.cnt < kc) return st;
+    }
+    float mx = -INFINITY;
+    int sl = 0;
+    for (int s2 = 0; s2 < kc; ++s2) {
+        float v = Ld[s2 * TBM + row];
+        if (v > mx) { mx = v; sl = s2; }
+    }
+    st.thr = mx;
+    st.slot = sl;
+    return st;
+}
+
+struct TcShared {
+    uint64_t full[NSTAGE];
+    uint64_t empty[NSTAGE];
+    uint64_t tfull[2];
+    uint64_t tempty[2];
+    uint32_t tmem_base;
+    int abort;
+};
+}  // namespace
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, int64_t N,
+              int64_t m, const float *__restrict__ norms, int64_t q0, int64_t nq, int kc, int nsplit,
+              int include_self, float *__restrict__ cand_d, int32_t *__restrict__ cand_i, DevCounters *ctr) {
+    extern __shared__ __align__(1024) uint8_t tsm_raw[];
+    // 1024-byte aligned stage ring, then candidate distances [kc][TBM], then barriers
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tsm_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *stages = base;
+    float *Ld = reinterpret_cast<float *>(base + NSTAGE * STAGE_BYTES);
+    TcShared *sh = reinterpret_cast<TcShared *>(Ld + (size_t)kc * TBM);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t qb = q0 + (int64_t)blockIdx.x * TBM;
+    const int64_t qend = q0 + nq;
+    const int split = blockIdx.y;
+    const int64_t per = (N + nsplit - 1) / nsplit;
+    const int64_t cbeg = (int64_t)split * per;
+    const int64_t cend = min(N, cbeg + per);
+    const int ntiles = cend > cbeg ? (int)((cend - cbeg + TBN - 1) / TBN) : 0;
+    const int nkb = (int)((m + TBK - 1) / TBK);
+    volatile int *abort_flag = &sh->abort;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTAGE; ++s) {
+            tc::mbar_init(tc::smem_u32(&sh->full[s]), 1);
+            tc::mbar_init(tc::smem_u32(&sh->empty[s]), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            tc::mbar_init(tc::smem_u32(&sh->tfull[a]), 1);
+            tc::mbar_init(tc::smem_u32(&sh->tempty[a]), 4 * 32);
+        }
+        sh->abort = 0;
+        tc::fence_mbar_init();
+        tc::prefetch_tmap(&map_a);
+        tc::prefetch_tmap(&map_b);
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tc::smem_u32(&sh->tmem_base), 512);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = sh->tmem_base;
+
+    if (warp == 0) {
+        // ------------------------------ TMA producer ----------------------------
+        if (lane == 0) {
+            int it = 0;
+            bool ok = true;
+            for (int t = 0; t < ntiles && ok; ++t) {
+                const int c0 = (int)(cbeg + (int64_t)t * TBN);
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = it % NSTAGE;
+                    const uint32_t par = ((it / NSTAGE) & 1) ^ 1;
+                    if (!tc::mbar_wait(tc::smem_u32(&sh->empty[s]), par, abort_flag, WAIT_LIMIT)) { ok = false; break; }
+                    const uint32_t sa = tc::smem_u32(stages + s * STAGE_BYTES);
+                    const uint32_t fb = tc::smem_u32(&sh->full[s]);
+                    tc::mbar_expect_tx(fb, STAGE_BYTES);
+                    tc::tma_load_2d(sa, &map_a, fb, kb * TBK, (int)qb);
+                    tc::tma_load_2d(sa + A_BYTES, &map_b, fb, kb * TBK, c0);
+                }
+            }
+            if (!ok) {
+                atomicOr(&ctr->status, (unsigned)DEV_TIMEOUT);
+                sh->abort = 1;
+            }
+            // drain: every issued stage must have landed before the CTA can exit
+            const int issued = it;
+            for (int j = issued - NSTAGE; j < issued; ++j) {
+                if (j < 0) continue;
+                tc::mbar_wait(tc::smem_u32(&sh->full[j % NSTAGE]), (j / NSTAGE) & 1, abort_flag, WAIT_LIMIT);
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------ MMA issuer ------------------------------
+        if (lane == 0) {
+            int it = 0;
+            bool ok = true;
+            int t = 0;
+            for (; t < ntiles && ok; ++t) {
+                const int acc = t & 1;
+                if (!tc::mbar_wait(tc::smem_u32(&sh->tempty[acc]), ((t >> 1) & 1) ^ 1, abort_flag, WAIT_LIMIT)) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after();
+                const uint32_t dt = tmem + (uint32_t)(acc * TBN);
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = it % NSTAGE;
+                    if (!tc::mbar_wait(tc::smem_u32(&sh->full[s]), (it / NSTAGE) & 1, abort_flag, WAIT_LIMIT)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after();
+                    const uint32_t sa = tc::smem_u32(stages + s * STAGE_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < TBK / 16; ++kk) {
+                        const uint64_t ad = tc::sdesc_sw128(sa + kk * 32);
+                        const uint64_t bd = tc::sdesc_sw128(sa + A_BYTES + kk * 32);
+                        tc::mma_f16(dt, ad, bd, IDESC, (kb | kk) != 0);
+                    }
+                    tc::commit(tc::smem_u32(&sh->empty[s]));
+                }
+                if (ok) tc::commit(tc::smem_u32(&sh->tfull[acc]));
+            }
+            if (!ok) {
+                atomicOr(&ctr->status, (unsigned)DEV_TIMEOUT);
+                sh->abort = 1;
+            }
+            // drain: the last commit covers every MMA issued by this thread
+            if (it > 0) {
+                const int j = it - 1;
+                tc::mbar_wait(tc::smem_u32(&sh->empty[j % NSTAGE]), (j / NSTAGE) & 1, abort_flag, WAIT_LIMIT);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------ epilogue ---------------------------------
+        const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
+        const int row = quarter * 32 + lane;
+        const int64_t gq = qb + row;
+        const bool valid_row = gq < qend;
+        const float qn = valid_row ? norms[gq] : 0.f;
+        const int64_t out_base = valid_row ? ((gq - q0) * nsplit + split) * (int64_t)kc : 0;
+        ListState st{valid_row ? INFINITY : -INFINITY, 0, 0};
+        int32_t *out_i = cand_i + out_base;
+        for (int t = 0; t < ntiles; ++t) {
+            const int acc = t & 1;
+            if (!tc::mbar_wait(tc::smem_u32(&sh->tfull[acc]), (t >> 1) & 1, abort_flag, WAIT_LIMIT)) {
+                atomicOr(&ctr->status, (unsigned)DEV_TIMEOUT);
+                sh->abort = 1;
+                break;
+            }
+            tc::fence_after();
+            const int64_t c0 = cbeg + (int64_t)t * TBN;
+            const bool masked = (c0 + TBN > cend) || (!include_self && gq >= c0 && gq < c0 + TBN);
+            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * TBN);
+#pragma unroll 1
+            for (int ch = 0; ch < TBN / 32; ++ch) {
+                uint32_t r[32];
+                tc::tmem_ld_32x32b_x32(taddr + ch * 32, r);
+                tc::tmem_ld_wait();
+                const int64_t cb = c0 + ch * 32;
+                const float *cnp = norms + cb;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int64_t c = cb + j;
+                    const float cn = (c < N) ? __ldg(cnp + j) : 0.f;
+                    float d = fmaf(-2.f, __uint_as_float(r[j]), qn + cn);
+                    if (masked && (c >= cend || (!include_self && c == gq))) d = INFINITY;
+                    if (d < st.thr) st = list_insert(st, d, (int)c, Ld, out_i, row, kc);
+                }
+            }
+            tc::fence_before();
+            tc::mbar_arrive(tc::smem_u32(&sh->tempty[acc]));
+        }
+        if (valid_row) {
+            for (int s2 = 0; s2 < kc; ++s2) {
+                const bool used = s2 < st.cnt;
+                cand_d[out_base + s2] = used ? Ld[s2 * TBM + row] : INFINITY;
+                if (!used) out_i[s2] = -1;
+            }
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc::fence_after();
+        tc::tmem_dealloc(tmem, 512);
+    }
+}
+
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+bool make_map(CUtensorMap *map, const void *Xb, int64_t N, int64_t m, int64_t ldb, int box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)N};
+    cuuint64_t strides[1] = {(cuuint64_t)ldb * 2};
+    cuuint32_t box[2] = {(cuuint32_t)TBK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(Xb), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+}  // namespace
+
+size_t knn_tc_smem_bytes(int kc) {
+    return 1024 + (size_t)NSTAGE * STAGE_BYTES + (size_t)kc * TBM * sizeof(float) + sizeof(TcShared) + 64;
+}
+
+cudaError_t launch_knn_tc(const void *Xb, int64_t N, int64_t m, int64_t ldb, const float *norms, int64_t q0,
+                          int64_t nq, int kc, int nsplit, int include_self, float *cand_d, int32_t *cand_i,
+                          DevCounters *ctr, cudaStream_t s) {
+    if (nq <= 0) return cudaSuccess;
+    if ((reinterpret_cast<uintptr_t>(Xb) & 15) || (ldb % 8) != 0) return cudaErrorInvalidValue;
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, Xb, N, m, ldb, TBM) || !make_map(&mb, Xb, N, m, ldb, TBN)) return cudaErrorInvalidValue;
+    const size_t smem = knn_tc_smem_bytes(kc);
+    cudaError_t e = cudaFuncSetAttribute(knn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((nq + TBM - 1) / TBM), (unsigned)nsplit);
+    knn_tc_kernel<<<grid, TC_THREADS, smem, s>>>(ma, mb, N, m, norms, q0, nq, kc, nsplit, include_self, cand_d,
+                                                  cand_i, ctr);
+    return cudaGetLastError();
+}
+
+// FP32 -> BF16 copy (round to nearest even) with a padded leading dimension.
+__global__ void to_bf16_kernel(const float *__restrict__ X, int64_t N, int64_t m, int64_t ld,
+                               __nv_bfloat16 *__restrict__ Y, int64_t ldb) {
+    const int64_t row = blockIdx.x;
+    for (int64_t a = threadIdx.x; a < ldb; a += blockDim.x)
+        Y[row * ldb + a] = __float2bfloat16_rn(a < m ? X[row * ld + a] : 0.f);
+}
+
+cudaError_t launch_to_bf16(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, void *Y, int64_t ldb,
+                           cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    if (dt == MECUCO_BF16) {
+        return cudaMemcpy2DAsync(Y, (size_t)ldb * 2, X, (size_t)ld * 2, (size_t)m * 2, (size_t)N,
+                                 cudaMemcpyDeviceToDevice, s);
+    }
+    to_bf16_kernel<<<(unsigned)N, 256, 0, s>>>((const float *)X, N, m, ld, (__nv_bfloat16 *)Y, ldb);
+    return cudaGetLastError();
+}
+
+}  // namespace mecuco
