@@ -56,11 +56,26 @@ static void *xmalloc(size_t bytes) {
     return p;
 }
 
+/* Input element types of the dataset-level entry points; each element is
+ * widened exactly to double before any arithmetic. */
+enum { ORC_F64 = 0, ORC_F32 = 1, ORC_BF16 = 2 };
+
+static double elem(const void *X, int elt, int64_t i) {
+    if (elt == ORC_F32) return (double)((const float *)X)[i];
+    if (elt == ORC_BF16) {
+        uint32_t bits = (uint32_t)((const uint16_t *)X)[i] << 16;
+        float f;
+        memcpy(&f, &bits, sizeof f);
+        return (double)f;
+    }
+    return ((const double *)X)[i];
+}
+
 /* ------------------------------------------------------------------------- */
 /* Step 1: brute-force kNN.  d(i,j) = sum_a (x_ia - x_ja)^2, k smallest by     */
 /* (d, j).  rows == NULL means every row is a query.                           */
 /* ------------------------------------------------------------------------- */
-int orc_knn(const double *X, int64_t n, int64_t m, const int64_t *rows, int64_t nrows,
+int orc_knn(const void *X, int elt, int64_t n, int64_t m, const int64_t *rows, int64_t nrows,
             int k, int include_self, int32_t *idx_out, double *dist_out, int nthreads) {
     if (k < 1 || (int64_t)k > n - (include_self ? 0 : 1)) return 1;
     int64_t nq = rows ? nrows : n;
@@ -70,16 +85,16 @@ int orc_knn(const double *X, int64_t n, int64_t m, const int64_t *rows, int64_t 
 #endif
     for (int64_t r = 0; r < nq; ++r) {
         int64_t q = rows ? rows[r] : r;
-        const double *xq = X + q * m;
+        double *xq = (double *)xmalloc(sizeof(double) * (size_t)m);
+        for (int64_t a = 0; a < m; ++a) xq[a] = elem(X, elt, q * m + a);
         double *bd = dist_out + r * k;
         int32_t *bi = idx_out + r * k;
         int cnt = 0;
         for (int64_t j = 0; j < n; ++j) {
             if (j == q && !include_self) continue;
-            const double *xj = X + j * m;
             double d = 0.0;
             for (int64_t a = 0; a < m; ++a) {
-                double t = xq[a] - xj[a];
+                double t = xq[a] - elem(X, elt, j * m + a);
                 d += t * t;
             }
             if (cnt == k) {
@@ -96,6 +111,7 @@ int orc_knn(const double *X, int64_t n, int64_t m, const int64_t *rows, int64_t 
             bi[pos] = (int32_t)j;
             ++cnt;
         }
+        free(xq);
     }
     return 0;
 }
@@ -103,13 +119,17 @@ int orc_knn(const double *X, int64_t n, int64_t m, const int64_t *rows, int64_t 
 /* ------------------------------------------------------------------------- */
 /* Step 2: centroid xbar = k^-1 sum_j x_j and X_c = [x_j - xbar] (k x m).       */
 /* ------------------------------------------------------------------------- */
-void orc_center_patch(const double *X, int64_t m, const int32_t *nb, int k, double *Xc) {
+static void center_patch_typed(const void *X, int elt, int64_t m, const int32_t *nb, int k, double *Xc) {
     for (int64_t a = 0; a < m; ++a) {
         double s = 0.0;
-        for (int j = 0; j < k; ++j) s += X[(int64_t)nb[j] * m + a];
+        for (int j = 0; j < k; ++j) s += elem(X, elt, (int64_t)nb[j] * m + a);
         double mean = s / (double)k;
-        for (int j = 0; j < k; ++j) Xc[(int64_t)j * m + a] = X[(int64_t)nb[j] * m + a] - mean;
+        for (int j = 0; j < k; ++j) Xc[(int64_t)j * m + a] = elem(X, elt, (int64_t)nb[j] * m + a) - mean;
     }
+}
+
+void orc_center_patch(const double *X, int64_t m, const int32_t *nb, int k, double *Xc) {
+    center_patch_typed(X, ORC_F64, m, nb, k, Xc);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -454,7 +474,7 @@ double orc_naive_patch(int k, int64_t m, const double *Xc, const double *W) {
 /* mode 1 = Exact (Theorem 1).  idx: n x k neighbour lists.  terms (optional) */
 /* n x T_NTERMS (Fast only), lam (optional) n x k.                            */
 /* ------------------------------------------------------------------------- */
-int orc_curvature(const double *X, int64_t n, int64_t m, int k, const int32_t *idx,
+int orc_curvature(const void *X, int elt, int64_t n, int64_t m, int k, const int32_t *idx,
                   const int64_t *rows, int64_t nrows, int mode, int variant, int route,
                   double *kappa, double *terms, double *lam, int nthreads) {
     int64_t nq = rows ? nrows : n;
@@ -465,7 +485,8 @@ int orc_curvature(const double *X, int64_t n, int64_t m, int k, const int32_t *i
     for (int64_t r = 0; r < nq; ++r) {
         int64_t i = rows ? rows[r] : r;
         double *Xc = (double *)xmalloc(sizeof(double) * (size_t)k * (size_t)m);
-        orc_center_patch(X, m, idx + i * k, k, Xc);
+        center_patch_typed(X, elt, m, idx + i * k, k, Xc);
+        (void)n;
         if (mode == 1) {
             kappa[r] = orc_exact_patch(k, m, Xc, NULL, NULL);
         } else {

@@ -65,7 +65,7 @@ def _load():
             build()
             lib = C.CDLL(_LIB)
             d, i64, i32, p = C.c_double, C.c_int64, C.c_int, C.c_void_p
-            lib.orc_knn.argtypes = [p, i64, i64, p, i64, i32, i32, p, p, i32]
+            lib.orc_knn.argtypes = [p, i32, i64, i64, p, i64, i32, i32, p, p, i32]
             lib.orc_knn.restype = i32
             lib.orc_center_patch.argtypes = [p, i64, p, i32, p]
             lib.orc_center_patch.restype = None
@@ -81,7 +81,7 @@ def _load():
             lib.orc_hht.restype = None
             lib.orc_naive_patch.argtypes = [i32, i64, p, p]
             lib.orc_naive_patch.restype = d
-            lib.orc_curvature.argtypes = [p, i64, i64, i32, p, p, i64, i32, i32, i32, p, p, p, i32]
+            lib.orc_curvature.argtypes = [p, i32, i64, i64, i32, p, p, i64, i32, i32, i32, p, p, p, i32]
             lib.orc_curvature.restype = i32
             lib.orc_grad_fd.argtypes = [p, i64, i64, i32, p, i32, i32, p, p, i64, p, p, i32]
             lib.orc_grad_fd.restype = i32
@@ -93,6 +93,20 @@ def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(a), dtype=np.float64)
 
 
+def _typed(X, bf16_bits: bool):
+    """(array, element code) for the dataset-level entry points: float32 and
+    bfloat16 bit patterns (uint16, with bf16_bits=True) are passed as they
+    are and widened exactly to double inside the oracle."""
+    X = np.asarray(X)
+    if bf16_bits or X.dtype == np.uint16:
+        if X.dtype != np.uint16:
+            raise TypeError("bf16 inputs must be uint16 bit patterns")
+        return np.ascontiguousarray(X), 2
+    if X.dtype == np.float32:
+        return np.ascontiguousarray(X), 1
+    return _f64(X), 0
+
+
 def _ptr(a: np.ndarray):
     return a.ctypes.data_as(C.c_void_p)
 
@@ -101,17 +115,18 @@ def _threads(nthreads):
     return int(nthreads) if nthreads else (os.cpu_count() or 1)
 
 
-def knn(X, k: int, rows=None, include_self: bool = False, nthreads=None):
+def knn(X, k: int, rows=None, include_self: bool = False, nthreads=None, bf16_bits: bool = False):
     """k nearest neighbours of each query row (all rows, or ``rows``) by
     brute force in FP64; returns (idx int32 [q, k], dist float64 [q, k])
-    sorted by (distance, index)."""
-    X = _f64(X)
+    sorted by (distance, index).  X may be float64, float32 or bfloat16 bit
+    patterns (uint16); elements are widened exactly to double."""
+    X, elt = _typed(X, bf16_bits)
     n, m = X.shape
     r = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
     nq = n if r is None else r.size
     idx = np.empty((nq, k), dtype=np.int32)
     dist = np.empty((nq, k), dtype=np.float64)
-    rc = _load().orc_knn(_ptr(X), n, m, None if r is None else _ptr(r), nq, k,
+    rc = _load().orc_knn(_ptr(X), elt, n, m, None if r is None else _ptr(r), nq, k,
                          int(bool(include_self)), _ptr(idx), _ptr(dist), _threads(nthreads))
     if rc != 0:
         raise ValueError("oracle knn: invalid k for this n")
@@ -193,10 +208,10 @@ def hht(W):
 
 
 def curvature(X, k: int, idx, rows=None, mode: str = "fast", variant: int = LITERAL,
-              route: int = 0, nthreads=None, return_terms: bool = False):
+              route: int = 0, nthreads=None, return_terms: bool = False, bf16_bits: bool = False):
     """Alg. 1 per-point loop over the query rows (all rows, or ``rows``)
-    with frozen neighbour lists ``idx`` (n x k)."""
-    X = _f64(X)
+    with frozen neighbour lists ``idx`` (n x k).  X as for ``knn``."""
+    X, elt = _typed(X, bf16_bits)
     n, m = X.shape
     idx = np.ascontiguousarray(idx, dtype=np.int32)
     r = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
@@ -204,7 +219,7 @@ def curvature(X, k: int, idx, rows=None, mode: str = "fast", variant: int = LITE
     kappa = np.empty(nq)
     terms = np.empty((nq, len(TERMS))) if return_terms else None
     lam = np.empty((nq, k)) if return_terms else None
-    _load().orc_curvature(_ptr(X), n, m, k, _ptr(idx), None if r is None else _ptr(r), nq,
+    _load().orc_curvature(_ptr(X), elt, n, m, k, _ptr(idx), None if r is None else _ptr(r), nq,
                           1 if mode == "exact" else 0, int(variant), int(route),
                           _ptr(kappa), None if terms is None else _ptr(terms),
                           None if lam is None else _ptr(lam), _threads(nthreads))

@@ -55,6 +55,8 @@ struct mecuco_ctx {
     DevCounters *ctr = nullptr;
     int32_t *m3_items = nullptr;
     int m3_items_k = -1;
+    int32_t *pair_ab = nullptr;
+    int pair_ab_k = -1;
     // options
     int64_t knn_margin = 32;
     int jacobi_fp64 = -1;
@@ -174,29 +176,45 @@ int candidate_capacity(mecuco_t h, int k) {
 struct KnnPlan {
     int kc, nsplit;
     int64_t qchunk;
+    bool tc;        // candidate search on the tensor cores (BF16 operands)
+    bool bf16_copy; // the tensor-core path needs a BF16 copy of X
+    int64_t ldb;    // leading dimension of the BF16 operand
 };
 
-KnnPlan plan_knn(mecuco_t h, int64_t N, int64_t nrows, int k) {
+KnnPlan plan_knn(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, int64_t nrows, int k,
+                 mecuco_precision prec) {
     KnnPlan p;
     p.kc = candidate_capacity(h, k);
+    p.tc = prec == MECUCO_PREC_BF16_MIXED;
+    const bool direct = dt == MECUCO_BF16 && ld % 8 == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+    p.bf16_copy = p.tc && !direct;
+    p.ldb = direct ? ld : (m + 7) / 8 * 8;
     p.qchunk = h->knn_qchunk > 0 ? h->knn_qchunk : (int64_t)1 << 18;
     if (p.qchunk > nrows) p.qchunk = nrows;
-    // keep >= 2 CTAs per SM busy: split the candidate range when there are
-    // few query blocks (the re-rank then sees kc * nsplit candidates per row)
+    // keep every SM busy (tensor-core kernel: 1 CTA/SM; CUDA-core kernel: 2):
+    // split the candidate range when there are few query blocks (the re-rank
+    // then sees kc * nsplit candidates per row)
     const int64_t qblocks = (p.qchunk + 127) / 128;
-    const int64_t want = 2LL * h->num_sms;
+    const int64_t want = (p.tc ? 1LL : 2LL) * h->num_sms;
     p.nsplit = 1;
     if (qblocks < want) p.nsplit = (int)std::min<int64_t>((want + qblocks - 1) / qblocks, 1024 / p.kc);
     while (p.nsplit > 1 && (N + p.nsplit - 1) / p.nsplit < p.kc) --p.nsplit;
     return p;
 }
 
+struct KnnBufs {
+    float *norms, *cand_d;
+    int32_t *cand_i, *flags;
+    void *xb;
+};
+
 // Scratch of run_knn, carved after `start`.
-void knn_scratch(Carver &c, const KnnPlan &p, int64_t N, float **norms, float **cd, int32_t **ci, int32_t **fl) {
-    *norms = c.take<float>((size_t)N);
-    *cd = c.take<float>((size_t)p.qchunk * p.nsplit * p.kc);
-    *ci = c.take<int32_t>((size_t)p.qchunk * p.nsplit * p.kc);
-    *fl = c.take<int32_t>((size_t)p.qchunk);
+void knn_scratch(Carver &c, const KnnPlan &p, int64_t N, KnnBufs *b) {
+    b->norms = c.take<float>((size_t)N);
+    b->cand_d = c.take<float>((size_t)p.qchunk * p.nsplit * p.kc);
+    b->cand_i = c.take<int32_t>((size_t)p.qchunk * p.nsplit * p.kc);
+    b->flags = c.take<int32_t>((size_t)p.qchunk);
+    b->xb = p.bf16_copy ? (void *)c.take<uint16_t>((size_t)N * p.ldb) : nullptr;
 }
 
 // kNN of query rows [rb, re) (outputs relative to rb); scratch at ws + start,
@@ -204,35 +222,45 @@ void knn_scratch(Carver &c, const KnnPlan &p, int64_t N, float **norms, float **
 mecuco_status run_knn(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, int k,
                       int include_self, mecuco_precision prec, int64_t rb, int64_t re, int32_t *idx_out,
                       float *dist_out, cudaStream_t s, size_t start) {
-    if (prec != MECUCO_PREC_FP32) return MECUCO_ERR_UNSUPPORTED;
-    KnnPlan p = plan_knn(h, N, re - rb, k);
+    KnnPlan p = plan_knn(h, X, dt, N, m, ld, re - rb, k, prec);
     Carver c(h->ws, start);
-    float *norms, *cand_d;
-    int32_t *cand_i, *flags;
-    knn_scratch(c, p, N, &norms, &cand_d, &cand_i, &flags);
-    LAUNCH(h, MECUCO_STAGE_ROWNORM, s, launch_rownorm(X, dt, N, m, ld, norms, s));
+    KnnBufs b;
+    knn_scratch(c, p, N, &b);
+    LAUNCH(h, MECUCO_STAGE_ROWNORM, s, launch_rownorm(X, dt, N, m, ld, b.norms, s));
+    const void *Xb = X;
+    if (p.bf16_copy) {
+        CK(launch_to_bf16(X, dt, N, m, ld, b.xb, p.ldb, s));
+        ++h->launches;
+        Xb = b.xb;
+    }
     for (int64_t q0 = rb; q0 < re; q0 += p.qchunk) {
         int64_t nq = std::min(p.qchunk, re - q0);
         int32_t *io = idx_out + (q0 - rb) * k;
         float *dout = dist_out ? dist_out + (q0 - rb) * k : nullptr;
-        LAUNCH(h, MECUCO_STAGE_KNN_SEARCH, s,
-               launch_knn_simt(X, dt, N, m, ld, norms, q0, nq, p.kc, p.nsplit, include_self, cand_d, cand_i, s));
-        LAUNCH(h, MECUCO_STAGE_KNN_RERANK, s,
-               launch_knn_rerank(X, dt, N, m, ld, norms, q0, nq, p.kc, p.nsplit, k, cand_d, cand_i, io, dout, flags,
+        if (p.tc)
+            LAUNCH(h, MECUCO_STAGE_KNN_SEARCH, s,
+                   launch_knn_tc(Xb, N, m, p.ldb, b.norms, q0, nq, p.kc, p.nsplit, include_self, b.cand_d, b.cand_i,
                                  h->ctr, s));
+        else
+            LAUNCH(h, MECUCO_STAGE_KNN_SEARCH, s,
+                   launch_knn_simt(X, dt, N, m, ld, b.norms, q0, nq, p.kc, p.nsplit, include_self, b.cand_d,
+                                   b.cand_i, s));
+        LAUNCH(h, MECUCO_STAGE_KNN_RERANK, s,
+               launch_knn_rerank(X, dt, N, m, ld, b.norms, q0, nq, p.kc, p.nsplit, k, b.cand_d, b.cand_i, io, dout,
+                                 b.flags, h->ctr, s));
         LAUNCH(h, MECUCO_STAGE_KNN_FALLBACK, s,
-               launch_knn_fallback(X, dt, N, m, ld, q0, nq, k, include_self, flags, io, dout, h->ctr, s));
+               launch_knn_fallback(X, dt, N, m, ld, q0, nq, k, include_self, b.flags, io, dout, h->ctr, s));
     }
     h->knn_rows += re - rb;
     return MECUCO_OK;
 }
 
-size_t knn_bytes(mecuco_t h, int64_t N, int64_t nrows, int k, size_t start) {
-    KnnPlan p = plan_knn(h, N, nrows, k);
+size_t knn_bytes(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, int64_t nrows, int k,
+                 mecuco_precision prec, size_t start) {
+    KnnPlan p = plan_knn(h, X, dt, N, m, ld, nrows, k, prec);
     Carver c(nullptr, start);
-    float *a, *b;
-    int32_t *d, *e;
-    knn_scratch(c, p, N, &a, &b, &d, &e);
+    KnnBufs b;
+    knn_scratch(c, p, N, &b);
     return c.off;
 }
 
@@ -241,6 +269,27 @@ mecuco_status begin_call(mecuco_t h, cudaStream_t s) {
     h->knn_rows = 0;
     CK(cudaSetDevice(h->device));
     CK(cudaMemsetAsync(h->ctr, 0, offsetof(DevCounters, status), s));
+    return MECUCO_OK;
+}
+
+mecuco_status ensure_pairs(mecuco_t h, int k) {
+    if (h->pair_ab_k == k) return MECUCO_OK;
+    if (h->pair_ab) {
+        CK(cudaDeviceSynchronize());
+        cudaFree(h->pair_ab);
+        h->pair_ab = nullptr;
+        h->pair_ab_k = -1;
+    }
+    const int n = k * (k + 1) / 2;
+    std::vector<int32_t> host((size_t)n);
+    moments_tc_build_pairs(k, host.data());
+    if (cudaMalloc(&h->pair_ab, sizeof(int32_t) * n) != cudaSuccess) {
+        (void)cudaGetLastError();
+        h->pair_ab = nullptr;
+        return MECUCO_ERR_OOM;
+    }
+    CK(cudaMemcpy(h->pair_ab, host.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+    h->pair_ab_k = k;
     return MECUCO_OK;
 }
 
@@ -291,14 +340,15 @@ mecuco_status run_curvature(mecuco_t h, const void *X, mecuco_dtype dt, int64_t 
                             const int32_t *idx, int include_self, mecuco_variant var, mecuco_precision prec,
                             int64_t rb, int64_t re, float *kappa_out, float *lambda_out, float *U_out,
                             float *s_out, cudaStream_t s) {
-    if (prec != MECUCO_PREC_FP32) return MECUCO_ERR_UNSUPPORTED;
     mecuco_status st = ensure_items(h, k);
     if (st != MECUCO_OK) return st;
+    const bool tc_moments = prec == MECUCO_PREC_BF16_MIXED;
+    if (tc_moments && (st = ensure_pairs(h, k)) != MECUCO_OK) return st;
     const int64_t nrows = re - rb;
     const int64_t chunk = est_chunk(h, nrows, k);
     // workspace: [idx of the range, if computed here] then kNN scratch, reused by the estimator
     const size_t idx_bytes = idx ? 0 : align_up((size_t)nrows * k * sizeof(int32_t), 256);
-    size_t need = idx ? 0 : knn_bytes(h, N, nrows, k, idx_bytes);
+    size_t need = idx ? 0 : knn_bytes(h, X, dt, N, m, ld, nrows, k, prec, idx_bytes);
     {
         Carver c(nullptr, idx_bytes);
         EstBufs b;
@@ -322,10 +372,17 @@ mecuco_status run_curvature(mecuco_t h, const void *X, mecuco_dtype dt, int64_t 
         const int64_t np = std::min(chunk, nrows - p0);
         const int32_t *nb = nbr + p0 * k;
         float *Ud = U_out ? U_out + p0 * (int64_t)k * k : b.U;
-        LAUNCH(h, MECUCO_STAGE_GRAM, s,
-               launch_patch_gram(X, dt, N, m, ld, nb, k, 0, np, b.G, b.R, var == MECUCO_FAST_HAAR ? b.Q : nullptr,
-                                 h->ctr, s));
-        LAUNCH(h, MECUCO_STAGE_MOMENTS, s, launch_patch_m3(X, dt, N, m, ld, nb, k, 0, np, b.M, h->m3_items, h->ctr, s));
+        if (tc_moments) {
+            LAUNCH(h, MECUCO_STAGE_MOMENTS, s,
+                   launch_moments_tc(X, dt, N, m, ld, nb, k, np, h->pair_ab, b.M, b.G, b.R,
+                                     var == MECUCO_FAST_HAAR ? b.Q : nullptr, h->ctr, s));
+        } else {
+            LAUNCH(h, MECUCO_STAGE_GRAM, s,
+                   launch_patch_gram(X, dt, N, m, ld, nb, k, 0, np, b.G, b.R,
+                                     var == MECUCO_FAST_HAAR ? b.Q : nullptr, h->ctr, s));
+            LAUNCH(h, MECUCO_STAGE_MOMENTS, s,
+                   launch_patch_m3(X, dt, N, m, ld, nb, k, 0, np, b.M, h->m3_items, h->ctr, s));
+        }
         LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(b.G, k, np, fp64, h->jacobi_max_sweeps, b.sig, Ud, h->ctr, s));
         LAUNCH(h, MECUCO_STAGE_ESTIMATOR, s,
                launch_estimator(b.sig, Ud, b.M, b.R, b.Q, k, m, np, (int)var, kappa_out + p0,
@@ -395,6 +452,7 @@ mecuco_status mecuco_destroy(mecuco_t h) {
     if (h->io) cudaFree(h->io);
     if (h->ctr) cudaFree(h->ctr);
     if (h->m3_items) cudaFree(h->m3_items);
+    if (h->pair_ab) cudaFree(h->pair_ab);
     delete h;
     return MECUCO_OK;
 }
@@ -439,10 +497,10 @@ mecuco_status mecuco_knn_range(mecuco_t h, const void *X, mecuco_dtype dt, int64
     if ((st = check_range(N, rb, re)) != MECUCO_OK) return st;
     if (!idx_out) return MECUCO_ERR_INVALID_ARG;
     if (prec != MECUCO_PREC_FP32 && prec != MECUCO_PREC_BF16_MIXED) return MECUCO_ERR_INVALID_ARG;
-    if (prec != MECUCO_PREC_FP32) return MECUCO_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = begin_call(h, s)) != MECUCO_OK) return st;
-    if ((st = ensure(h->ws, h->ws_bytes, knn_bytes(h, N, re - rb, k, 0))) != MECUCO_OK) return st;
+    if ((st = ensure(h->ws, h->ws_bytes, knn_bytes(h, X, dt, N, m, ld, re - rb, k, prec, 0))) != MECUCO_OK)
+        return st;
     return run_knn(h, X, dt, N, m, ld, k, include_self, prec, rb, re, idx_out, dist_out, s, 0);
 }
 
@@ -461,7 +519,6 @@ mecuco_status mecuco_curvature_range(mecuco_t h, const void *X, mecuco_dtype dt,
     if (!kappa_out) return MECUCO_ERR_INVALID_ARG;
     if (var != MECUCO_FAST_LITERAL && var != MECUCO_FAST_HAAR) return MECUCO_ERR_INVALID_ARG;
     if (prec != MECUCO_PREC_FP32 && prec != MECUCO_PREC_BF16_MIXED) return MECUCO_ERR_INVALID_ARG;
-    if (prec != MECUCO_PREC_FP32) return MECUCO_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = begin_call(h, s)) != MECUCO_OK) return st;
     return run_curvature(h, X, dt, N, m, ld, k, idx, include_self, var, prec, rb, re, kappa_out, lambda_out, U_out,
@@ -483,7 +540,6 @@ mecuco_status mecuco_curvature_host(mecuco_t h, const void *X_host, mecuco_dtype
     if (!kappa_host_out) return MECUCO_ERR_INVALID_ARG;
     if (var != MECUCO_FAST_LITERAL && var != MECUCO_FAST_HAAR) return MECUCO_ERR_INVALID_ARG;
     if (prec != MECUCO_PREC_FP32 && prec != MECUCO_PREC_BF16_MIXED) return MECUCO_ERR_INVALID_ARG;
-    if (prec != MECUCO_PREC_FP32) return MECUCO_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = begin_call(h, s)) != MECUCO_OK) return st;
     const size_t elt = dt == MECUCO_BF16 ? 2 : 4;
@@ -498,7 +554,7 @@ mecuco_status mecuco_curvature_host(mecuco_t h, const void *X_host, mecuco_dtype
     float *kd = c.take<float>((size_t)N);
     int32_t *id = c.take<int32_t>((size_t)N * k);
     CK(cudaMemcpyAsync(Xd, X_host, xbytes, cudaMemcpyHostToDevice, s));
-    if ((st = ensure(h->ws, h->ws_bytes, knn_bytes(h, N, N, k, 0))) != MECUCO_OK) return st;
+    if ((st = ensure(h->ws, h->ws_bytes, knn_bytes(h, Xd, dt, N, m, ld, N, k, prec, 0))) != MECUCO_OK) return st;
     if ((st = run_knn(h, Xd, dt, N, m, ld, k, include_self, prec, 0, N, id, nullptr, s, 0)) != MECUCO_OK) return st;
     if ((st = run_curvature(h, Xd, dt, N, m, ld, k, id, include_self, var, prec, 0, N, kd, nullptr, nullptr, nullptr,
                             s)) != MECUCO_OK)

@@ -78,6 +78,16 @@ __device__ inline int64_t m3_pair_floats_d(int k) { return (int64_t)k * (k + 1) 
 int m3_items(int k);
 void m3_build_items(int k, int32_t *items /* m3_items(k) */);
 
+// BF16-mixed form: G, R, Q and the pair-major M of each patch from one
+// tensor-core GEMM per 128-pair tile (BF16 operands, FP32 accumulation).
+// pair_ab[p] = a | b << 16 for pair index p (built by moments_tc_build_pairs);
+// idx points at the chunk's first neighbour row; Q may be NULL.
+cudaError_t launch_moments_tc(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, const int32_t *idx,
+                              int k, int64_t np, const int32_t *pair_ab, float *M, float *G, float *R, float *Q,
+                              DevCounters *ctr, cudaStream_t s);
+void moments_tc_build_pairs(int k, int32_t *pair_ab /* k(k+1)/2 */);
+size_t moments_tc_smem_bytes();
+
 // ---- Step 3: k x k eigensolve -----------------------------------------------
 // One warp per patch, parallel-order two-sided Jacobi.  G: np x k x k.
 // Outputs sigma (np x k, descending) and U (np x k x k, column l = eigenvector).

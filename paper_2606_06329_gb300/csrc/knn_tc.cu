@@ -37,7 +37,7 @@ constexpr int A_BYTES = TBM * TBK * 2;   // 16 KB
 constexpr int B_BYTES = TBN * TBK * 2;   // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int TC_THREADS = 192;
-constexpr long long WAIT_LIMIT = 4000000000LL;  // ~2 s of SM clock per wait
+constexpr long long WAIT_LIMIT = 1000000000LL;  // ~0.5 s of SM clock per wait
 constexpr uint32_t IDESC = tc::idesc_bf16_f32(TBM, TBN);
 
 struct ListState {
@@ -99,6 +99,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
     const int ntiles = cend > cbeg ? (int)((cend - cbeg + TBN - 1) / TBN) : 0;
     const int nkb = (int)((m + TBK - 1) / TBK);
     volatile int *abort_flag = &sh->abort;
+    __shared__ int never;  // a flag that stays 0: drain waits are bounded by time only
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NSTAGE; ++s) {
@@ -109,7 +110,10 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
             tc::mbar_init(tc::smem_u32(&sh->tfull[a]), 1);
             tc::mbar_init(tc::smem_u32(&sh->tempty[a]), 4 * 32);
         }
-        sh->abort = 0;
+        // circuit breaker: once any CTA of this launch timed out, later CTAs skip
+        // the work (their lists come out empty) instead of timing out one by one
+        sh->abort = (*(volatile unsigned *)&ctr->status & DEV_TIMEOUT) ? 1 : 0;
+        never = 0;
         tc::fence_mbar_init();
         tc::prefetch_tmap(&map_a);
         tc::prefetch_tmap(&map_b);
@@ -128,7 +132,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
         if (lane == 0) {
             int it = 0;
             bool ok = true;
-            for (int t = 0; t < ntiles && ok; ++t) {
+            for (int t = 0; t < ntiles && ok && !*abort_flag; ++t) {
                 const int c0 = (int)(cbeg + (int64_t)t * TBN);
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const int s = it % NSTAGE;
@@ -146,10 +150,11 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
                 sh->abort = 1;
             }
             // drain: every issued stage must have landed before the CTA can exit
+            // (bounded by time only: the abort flag must not cut this wait short)
             const int issued = it;
             for (int j = issued - NSTAGE; j < issued; ++j) {
                 if (j < 0) continue;
-                tc::mbar_wait(tc::smem_u32(&sh->full[j % NSTAGE]), (j / NSTAGE) & 1, abort_flag, WAIT_LIMIT);
+                tc::mbar_wait(tc::smem_u32(&sh->full[j % NSTAGE]), (j / NSTAGE) & 1, &never, WAIT_LIMIT);
             }
         }
     } else if (warp == 1) {
@@ -158,7 +163,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
             int it = 0;
             bool ok = true;
             int t = 0;
-            for (; t < ntiles && ok; ++t) {
+            for (; t < ntiles && ok && !*abort_flag; ++t) {
                 const int acc = t & 1;
                 if (!tc::mbar_wait(tc::smem_u32(&sh->tempty[acc]), ((t >> 1) & 1) ^ 1, abort_flag, WAIT_LIMIT)) {
                     ok = false;
@@ -191,7 +196,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
             // drain: the last commit covers every MMA issued by this thread
             if (it > 0) {
                 const int j = it - 1;
-                tc::mbar_wait(tc::smem_u32(&sh->empty[j % NSTAGE]), (j / NSTAGE) & 1, abort_flag, WAIT_LIMIT);
+                tc::mbar_wait(tc::smem_u32(&sh->empty[j % NSTAGE]), (j / NSTAGE) & 1, &never, WAIT_LIMIT);
             }
         }
         __syncwarp();
@@ -205,7 +210,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
         const int64_t out_base = valid_row ? ((gq - q0) * nsplit + split) * (int64_t)kc : 0;
         ListState st{valid_row ? INFINITY : -INFINITY, 0, 0};
         int32_t *out_i = cand_i + out_base;
-        for (int t = 0; t < ntiles; ++t) {
+        for (int t = 0; t < ntiles && !*abort_flag; ++t) {
             const int acc = t & 1;
             if (!tc::mbar_wait(tc::smem_u32(&sh->tfull[acc]), (t >> 1) & 1, abort_flag, WAIT_LIMIT)) {
                 atomicOr(&ctr->status, (unsigned)DEV_TIMEOUT);

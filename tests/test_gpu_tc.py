@@ -1,0 +1,83 @@
+"""Tensor-core (tcgen05, BF16 operands, FP32 accumulation) candidate search:
+after the exact re-rank its neighbour lists must equal the FP64 brute force
+(tie rule as for the plain path), with the candidate margin certified for
+every row (no row may need the exact full-scan fallback on these inputs, which
+would mask a wrong distance GEMM)."""
+import numpy as np
+import pytest
+
+from paper_2606_06329_gb300 import synth
+
+from gpu_helpers import knn_mismatches, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_06329_gb300 import api, build
+    build.build()
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+def _bf16(bits):
+    return torch.from_numpy(bits.view(np.int16)).view(torch.bfloat16)
+
+
+def _check(ctx, orc, Xt, X64, k, rows=None, max_uncert=0):
+    Xd = Xt.cuda()
+    idx = ctx.mecuco_knn(Xd, k, precision="bf16_mixed")
+    torch.cuda.synchronize()
+    st = ctx.mecuco_get_stats()
+    assert ctx.mecuco_get_last_status() == 0
+    idx = idx.cpu().numpy()
+    ref_idx, ref_d = orc.knn(X64, k, rows=rows)
+    got = idx if rows is None else idx[rows]
+    assert knn_mismatches(X64, got, ref_idx, ref_d, rows=rows) == []
+    assert st["knn_uncertified"] <= max_uncert, st
+    assert st["knn_fallback_rows"] == st["knn_uncertified"]
+    return idx
+
+
+@pytest.mark.parametrize("n,m,k", [(1000, 128, 8), (1037, 200, 16), (300, 64, 64), (700, 4096, 32)])
+def test_tc_knn_bf16_storage(ctx, orc, n, m, k):
+    bits = synth.curved_patches(n=n, m=m, n_patches=3, seed=n + m)
+    _check(ctx, orc, _bf16(bits), synth.bf16_bits_to_f32(bits).astype(np.float64), k)
+
+
+def test_tc_knn_fp32_input_small_m(ctx, orc):
+    X = synth.sphere(n=2000, m=32, seed=1)
+    _check(ctx, orc, torch.from_numpy(X), X.astype(np.float64), 10)
+
+
+def test_tc_knn_sparse_clusters(ctx, orc):
+    X = synth.sparse_clusters(n=6000, m=784, seed=2)
+    # BF16 rounding of FP32 inputs perturbs d~ by ~1e-2 here: the margin may
+    # leave a few rows uncertified, which the exact fallback then re-solves
+    _check(ctx, orc, torch.from_numpy(X), X.astype(np.float64), 50, max_uncert=60)
+
+
+def test_tc_knn_matches_plain_path(ctx):
+    bits = synth.curved_patches(n=20000, m=512, n_patches=8, seed=3)
+    Xd = _bf16(bits).cuda()
+    a = ctx.mecuco_knn(Xd, 24, precision="bf16_mixed")
+    b = ctx.mecuco_knn(Xd, 24, precision="fp32")
+    assert torch.equal(a, b)
+
+
+def test_tc_curvature_bf16_mixed(ctx, orc):
+    bits = synth.curved_patches(n=3000, m=1024, n_patches=3, seed=5)
+    X64 = synth.bf16_bits_to_f32(bits).astype(np.float64)
+    Xd = _bf16(bits).cuda()
+    k = 32
+    kap = ctx.mecuco_curvature(Xd, k, precision="bf16_mixed")
+    idx = ctx.mecuco_knn(Xd, k, precision="bf16_mixed")
+    torch.cuda.synchronize()
+    rows = np.random.default_rng(0).choice(3000, 48, replace=False)
+    ref = orc.curvature(X64, k, idx.cpu().numpy(), rows=rows)
+    assert rel_err(kap.cpu().numpy()[rows], ref).max() < 1e-4
