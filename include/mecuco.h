@@ -185,6 +185,26 @@ MECUCO_API mecuco_status mecuco_curvature_host(mecuco_t h, const void *X_host, m
                                     mecuco_variant var, mecuco_precision prec,
                                     float *kappa_host_out, int32_t *idx_host_out, void *stream);
 
+/* Allocation-free k-nearest-neighbour search (the paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory -
+ * code under a framework that owns all device memory through its own pool,
+ * services with a fixed device-memory budget, and code that must not incur
+ * the implicit synchronisation of cudaMalloc/cudaFree).  It takes no context,
+ * calls no cudaMalloc/cudaFree and uses a fixed 32 MiB scratch array compiled
+ * into the library, which every GPU holding this library's module keeps until
+ * the process exits.  Runs on the calling thread's current device; X, idx_out
+ * and dist_out as for mecuco_knn with MECUCO_PREC_FP32, and the lists are the
+ * same as that call returns.  N above 4,194,304 rows is rejected with
+ * MECUCO_ERR_INVALID_ARG.  The first call on a device looks up the scratch
+ * array's device address (it may load the module); make that call before any
+ * stream capture.  All calls share the scratch and it keeps the last call's
+ * contents; calls whose GPU work overlaps (other streams, other host threads
+ * on the same device) race on it and must be serialised by the caller.
+ * Device-side counters of this entry point are not reported. */
+MECUCO_API mecuco_status mecuco_knn_noalloc(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
+                                            int k, int include_self, int32_t *idx_out, float *dist_out,
+                                            void *stream);
+
 /* Status OR-ed on the device by the calls since the previous query, then
  * cleared.  Synchronises `stream` first. */
 MECUCO_API mecuco_status mecuco_get_last_status(mecuco_t h, void *stream);

@@ -56,6 +56,7 @@ SIGNATURES = {
     "mecuco_curvature_range": (_st, [_p, _p, _i32, _i64, _i64, _i64, _i32, _p, _i32, _i32, _i32, _i64, _i64,
                                      _p, _p, _p, _p, _p]),
     "mecuco_curvature_host": (_st, [_p, _p, _i32, _i64, _i64, _i64, _i32, _i32, _i32, _i32, _p, _p, _p]),
+    "mecuco_knn_noalloc": (_st, [_p, _i32, _i64, _i64, _i64, _i32, _i32, _p, _p, _p]),
     "mecuco_get_last_status": (_st, [_p, _p]),
     "mecuco_get_stats": (_st, [_p, C.POINTER(mecuco_stats), _p]),
     "mecuco_get_stage_times": (_st, [_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), _p]),

@@ -23,6 +23,11 @@ void set_err(const char *where, cudaError_t e) {
 }
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+}  // namespace
+
+void mecuco::set_error_text(const char *msg) { snprintf(g_errmsg, sizeof(g_errmsg), "%s", msg); }
+
+namespace {
 
 // Offsets into one device buffer, 256-byte aligned.  Sizing and carving use
 // the same sequence of take() calls, first with base == nullptr.

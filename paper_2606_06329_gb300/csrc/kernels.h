@@ -10,6 +10,9 @@ namespace mecuco {
 
 struct DevCounters;
 
+// Text returned by mecuco_last_error_message() for this thread.
+void set_error_text(const char *msg);
+
 // ---- Step 1: kNN -----------------------------------------------------------
 // Squared row norms |x_i|^2 (FP32 accumulation), i in [0, N).
 cudaError_t launch_rownorm(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
