@@ -78,15 +78,18 @@ typedef enum { MECUCO_FAST_LITERAL = 0, MECUCO_FAST_HAAR = 1 } mecuco_variant;
  *               FP32 on the CUDA cores; FP32 Jacobi.  (the plain form)
  *   BF16_MIXED: distance GEMM in BF16 on the tensor cores with FP32
  *               accumulation and an FP32 exact re-rank of the candidates;
- *               patch moments from BF16 operands with FP32 accumulation;
- *               FP64 Jacobi eigensolve and rotation accumulation.  (the
- *               chosen form) */
+ *               patch moments (G, R, Q, third moments) from BF16 operands on
+ *               the tensor cores with FP32 accumulation; Jacobi sweeps in FP32
+ *               followed by an FP64 refinement of the eigenpairs (FP64
+ *               products and eigenvector accumulation).  (the chosen form) */
 typedef enum { MECUCO_PREC_FP32 = 0, MECUCO_PREC_BF16_MIXED = 1 } mecuco_precision;
 
 /* Tunable options (mecuco_set_option).  Values are int64. */
 typedef enum {
     MECUCO_OPT_KNN_MARGIN = 0,       /* extra candidates kept per row before the exact re-rank (default 32) */
-    MECUCO_OPT_JACOBI_FP64 = 1,      /* -1: by precision (default), 0: FP32 sweeps, 1: FP64 sweeps */
+    MECUCO_OPT_JACOBI_FP64 = 1,      /* -1: by precision (default: 0 for FP32, 1 for BF16_MIXED);
+                                        0: FP32 sweeps; 1: FP32 sweeps + one FP64 refinement step;
+                                        2: every sweep in FP64 */
     MECUCO_OPT_JACOBI_MAX_SWEEPS = 2,/* sweep cap of the eigensolver (default 40) */
     MECUCO_OPT_CHUNK_POINTS = 3,     /* points per estimator chunk (0 = automatic) */
     MECUCO_OPT_KNN_QUERY_CHUNK = 4,  /* query rows per kNN launch (0 = automatic) */

@@ -389,6 +389,7 @@ mecuco_status run_curvature(mecuco_t h, const void *X, mecuco_dtype dt, int64_t 
                    launch_patch_m3(X, dt, N, m, ld, nb, k, 0, np, b.M, h->m3_items, h->ctr, s));
         }
         LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(b.G, k, np, fp64, h->jacobi_max_sweeps, b.sig, Ud, h->ctr, s));
+        if (fp64 == 1) ++h->launches;  // the FP64 refinement is a second kernel
         LAUNCH(h, MECUCO_STAGE_ESTIMATOR, s,
                launch_estimator(b.sig, Ud, b.M, b.R, b.Q, k, m, np, (int)var, kappa_out + p0,
                                 lambda_out ? lambda_out + p0 * k : nullptr, s_out ? s_out + p0 * k : nullptr, h->ctr,
@@ -470,7 +471,7 @@ mecuco_status mecuco_set_option(mecuco_t h, mecuco_option opt, int64_t v) {
             h->knn_margin = v;
             break;
         case MECUCO_OPT_JACOBI_FP64:
-            if (v < -1 || v > 1) return MECUCO_ERR_INVALID_ARG;
+            if (v < -1 || v > 2) return MECUCO_ERR_INVALID_ARG;
             h->jacobi_fp64 = (int)v;
             break;
         case MECUCO_OPT_JACOBI_MAX_SWEEPS:

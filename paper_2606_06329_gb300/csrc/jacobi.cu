@@ -158,6 +158,109 @@ jacobi_kernel(const float *__restrict__ G, int k, int64_t np, int max_sweeps, fl
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP64 refinement of an FP32 eigendecomposition (one step of the iterative
+// refinement for symmetric eigenproblems of Ogita & Aishima, Japan J. Indust.
+// Appl. Math. 35 (2018)), every product and sum in FP64.  With X the k x k
+// eigenvector estimate from the FP32 sweeps and A = G in FP64:
+//   R = I - X^T X,   S = X^T A X,   lam_i = S_ii / (1 - R_ii),
+//   E_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i)  if |lam_i - lam_j| > delta,
+//   E_ij = R_ij / 2 otherwise (and on the diagonal),   X' = X + X E.
+// From FP32-accurate X (~2^-23) one step gives eigenvectors accurate to the
+// square of that, i.e. to FP64 level, and re-orthogonalises them.  delta =
+// 2^-18 max|lam| treats eigenvalues closer than the FP32 estimate can resolve
+// as a cluster (only orthogonalised).  One CTA (RT threads) per patch; results
+// re-sorted descending.
+// ---------------------------------------------------------------------------
+constexpr int RT = 256;
+
+__global__ void __launch_bounds__(RT)
+jacobi_refine64_kernel(const float *__restrict__ G, int k, float *__restrict__ sigma, float *__restrict__ U) {
+    extern __shared__ __align__(16) unsigned char rsm[];
+    const int ld = k + 1;
+    double *A = reinterpret_cast<double *>(rsm);  // [k][ld]
+    double *X = A + (size_t)k * ld;                 // [k][ld]
+    double *T = X + (size_t)k * ld;                 // A X, then X E
+    double *S = T + (size_t)k * ld;                 // X^T A X
+    double *Rm = S + (size_t)k * ld;                // I - X^T X, then E
+    double *lam = Rm + (size_t)k * ld;              // [k]
+    __shared__ double s_lmax;
+    const int tid = threadIdx.x;
+    const int64_t pt = blockIdx.x;
+    const float *g = G + pt * (int64_t)k * k;
+    float *u = U + pt * (int64_t)k * k;
+    const int kk = k * k;
+    for (int e = tid; e < kk; e += RT) {
+        const int r = e / k, c = e % k;
+        A[r * ld + c] = (double)g[e];
+        X[r * ld + c] = (double)u[e];
+    }
+    __syncthreads();
+    // T = A X ; Rm = I - X^T X
+    for (int e = tid; e < kk; e += RT) {
+        const int r = e / k, c = e % k;
+        double t = 0.0, q = 0.0;
+        for (int j = 0; j < k; ++j) {
+            t = fma(A[r * ld + j], X[j * ld + c], t);
+            q = fma(X[j * ld + r], X[j * ld + c], q);
+        }
+        T[r * ld + c] = t;
+        Rm[r * ld + c] = (r == c ? 1.0 : 0.0) - q;
+    }
+    __syncthreads();
+    // S = X^T T
+    for (int e = tid; e < kk; e += RT) {
+        const int r = e / k, c = e % k;
+        double t = 0.0;
+        for (int j = 0; j < k; ++j) t = fma(X[j * ld + r], T[j * ld + c], t);
+        S[r * ld + c] = t;
+    }
+    __syncthreads();
+    if (tid < k) lam[tid] = S[tid * ld + tid] / (1.0 - Rm[tid * ld + tid]);
+    __syncthreads();
+    if (tid == 0) {
+        double mx = 0.0;
+        for (int i = 0; i < k; ++i) mx = fmax(mx, fabs(lam[i]));
+        s_lmax = mx;
+    }
+    __syncthreads();
+    const double delta = 3.814697265625e-06 * s_lmax;  // 2^-18 max|lam|
+    // E (in place of Rm): needs the old R_ij and R_ji, read before any write
+    double ev[(64 * 64 + RT - 1) / RT];
+    int ne = 0;
+    for (int e = tid; e < kk; e += RT, ++ne) {
+        const int i = e / k, j = e % k;
+        const double rij = 0.5 * (Rm[i * ld + j] + Rm[j * ld + i]);
+        const double sij = 0.5 * (S[i * ld + j] + S[j * ld + i]);
+        double v;
+        if (i == j || fabs(lam[i] - lam[j]) <= delta) v = 0.5 * rij;
+        else v = (sij + lam[j] * rij) / (lam[j] - lam[i]);
+        ev[ne] = v;
+    }
+    __syncthreads();
+    ne = 0;
+    for (int e = tid; e < kk; e += RT, ++ne) Rm[(e / k) * ld + (e % k)] = ev[ne];
+    __syncthreads();
+    // X' = X + X E
+    for (int e = tid; e < kk; e += RT) {
+        const int r = e / k, c = e % k;
+        double t = X[r * ld + c];
+        for (int j = 0; j < k; ++j) t = fma(X[r * ld + j], Rm[j * ld + c], t);
+        T[r * ld + c] = t;
+    }
+    __syncthreads();
+    // write back, columns re-sorted by lam descending
+    float *sg = sigma + pt * (int64_t)k;
+    for (int i = tid; i < k; i += RT) {
+        int rank = 0;
+        for (int j = 0; j < k; ++j) rank += (lam[j] > lam[i]) || (lam[j] == lam[i] && j < i);
+        sg[rank] = (float)lam[i];
+        for (int r = 0; r < k; ++r) u[r * k + rank] = (float)T[r * ld + i];
+    }
+}
+
+size_t refine64_smem_bytes(int k) { return (size_t)5 * k * (k + 1) * sizeof(double) + (size_t)k * sizeof(double); }
+
 size_t jacobi_smem_bytes(int k, int fp64) {
     const int kp = (k + 1) & ~1;
     const size_t real = fp64 ? sizeof(double) : sizeof(float);
@@ -167,10 +270,20 @@ size_t jacobi_smem_bytes(int k, int fp64) {
 cudaError_t launch_jacobi(const float *G, int k, int64_t np, int fp64, int max_sweeps, float *sigma, float *U,
                           DevCounters *ctr, cudaStream_t s) {
     if (np <= 0) return cudaSuccess;
-    if (k > 128) return cudaErrorInvalidValue;
-    const size_t smem = jacobi_smem_bytes(k, fp64);
+    if (k > 64) return cudaErrorInvalidValue;
     cudaError_t e;
-    if (fp64) {
+    if (fp64 == 1) {
+        // FP32 sweeps, then one FP64 refinement step
+        e = launch_jacobi(G, k, np, 0, max_sweeps, sigma, U, ctr, s);
+        if (e != cudaSuccess) return e;
+        const size_t rs = refine64_smem_bytes(k);
+        e = cudaFuncSetAttribute(jacobi_refine64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs);
+        if (e != cudaSuccess) return e;
+        jacobi_refine64_kernel<<<(unsigned)np, RT, rs, s>>>(G, k, sigma, U);
+        return cudaGetLastError();
+    }
+    const size_t smem = jacobi_smem_bytes(k, fp64);
+    if (fp64 == 2) {
         e = cudaFuncSetAttribute(jacobi_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         jacobi_kernel<double><<<(unsigned)np, JT, smem, s>>>(G, k, np, max_sweeps, sigma, U, ctr);

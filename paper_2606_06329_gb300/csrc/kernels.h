@@ -92,8 +92,10 @@ void moments_tc_build_pairs(int k, int32_t *pair_ab /* k(k+1)/2 */);
 size_t moments_tc_smem_bytes();
 
 // ---- Step 3: k x k eigensolve -----------------------------------------------
-// One warp per patch, parallel-order two-sided Jacobi.  G: np x k x k.
+// Parallel-order two-sided Jacobi, one CTA per patch.  G: np x k x k.
 // Outputs sigma (np x k, descending) and U (np x k x k, column l = eigenvector).
+// fp64: 0 = FP32 sweeps; 1 = FP32 sweeps then one FP64 refinement step;
+// 2 = every sweep in FP64.
 cudaError_t launch_jacobi(const float *G, int k, int64_t np, int fp64, int max_sweeps,
                           float *sigma, float *U, DevCounters *ctr, cudaStream_t s);
 

@@ -70,14 +70,25 @@ def test_tc_knn_matches_plain_path(ctx):
     assert torch.equal(a, b)
 
 
-def test_tc_curvature_bf16_mixed(ctx, orc):
-    bits = synth.curved_patches(n=3000, m=1024, n_patches=3, seed=5)
-    X64 = synth.bf16_bits_to_f32(bits).astype(np.float64)
+# BF16-mixed form: patch moments from BF16 operands (relative rounding 2^-9 per
+# product) with FP32 accumulation; its error against the FP64 oracle is
+# reported, and bounded here well above what BF16 rounding produces.
+BF16_KAPPA_TOL = 2e-2
+
+
+@pytest.mark.parametrize("k,variant", [(32, "literal"), (64, "literal"), (20, "haar"), (10, "literal")])
+def test_tc_curvature_bf16_mixed(ctx, orc, k, variant):
+    bits = synth.curved_patches(n=3000, m=1024, n_patches=3, seed=5 + k)
     Xd = _bf16(bits).cuda()
-    k = 32
-    kap = ctx.mecuco_curvature(Xd, k, precision="bf16_mixed")
+    out = ctx.mecuco_curvature(Xd, k, precision="bf16_mixed", variant=variant, return_lambda=True)
     idx = ctx.mecuco_knn(Xd, k, precision="bf16_mixed")
     torch.cuda.synchronize()
+    assert ctx.mecuco_get_last_status() == 0
     rows = np.random.default_rng(0).choice(3000, 48, replace=False)
-    ref = orc.curvature(X64, k, idx.cpu().numpy(), rows=rows)
-    assert rel_err(kap.cpu().numpy()[rows], ref).max() < 1e-4
+    ref, _, ref_lam = orc.curvature(bits, k, idx.cpu().numpy(), rows=rows, return_terms=True,
+                                    variant=orc.HAAR if variant == "haar" else orc.LITERAL)
+    err = rel_err(out["kappa"].cpu().numpy()[rows], ref)
+    print(f"bf16_mixed k={k} {variant}: max rel err {err.max():.3e}, median {np.median(err):.3e}")
+    assert err.max() < BF16_KAPPA_TOL
+    lam = out["lambda"].cpu().numpy()[rows]
+    assert np.allclose(lam[:, :k - 1], ref_lam[:, :k - 1], rtol=2e-2, atol=1e-3 * ref_lam[:, 0:1])
