@@ -106,7 +106,8 @@ typedef enum {
     MECUCO_STAGE_MOMENTS = 5,    /* gather, centre, third moments M */
     MECUCO_STAGE_JACOBI = 6,     /* k x k eigensolve */
     MECUCO_STAGE_ESTIMATOR = 7,  /* k-space Fast estimator */
-    MECUCO_STAGE_COUNT = 8
+    MECUCO_STAGE_ADJOINT = 8,    /* k-space adjoint + patch adjoint and scatter */
+    MECUCO_STAGE_COUNT = 9
 } mecuco_stage;
 
 /* Counters of the last completed call (valid after the stream is synchronised). */
@@ -178,6 +179,24 @@ MECUCO_API mecuco_status mecuco_curvature_range(mecuco_t h, const void *X, mecuc
                                                 mecuco_precision prec, int64_t row_begin,
                                                 int64_t row_end, float *kappa_out, float *lambda_out,
                                                 float *U_out, float *s_out, void *stream);
+
+/* Adjoint of the Fast-mode curvature with the neighbour lists frozen:
+ * dX_out = d(sum_i dkappa_i K_i) / dX, where K_i is the curvature of
+ * mecuco_curvature for the same (X, idx, var, prec).  K = |f| is differentiated
+ * as sign(f) df (0 at f = 0).  Every patch's moments and eigenpairs are
+ * recomputed (nothing is kept from the forward call); the per-point adjoint
+ * runs in k-space (through the derivative of the symmetric eigendecomposition,
+ * which is unbounded for coinciding eigenvalues) and is scattered onto the
+ * neighbour rows with atomic adds (summation order, hence the last bits, vary
+ * between runs).
+ *   X       device, N x m (ld) of dtype dt
+ *   idx     device, N x k int32 neighbour lists (required)
+ *   dkappa  device, N floats
+ *   dX_out  device, N x m floats (row stride m), overwritten */
+MECUCO_API mecuco_status mecuco_curvature_backward(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m,
+                                                   int64_t ld, int k, const int32_t *idx, mecuco_variant var,
+                                                   mecuco_precision prec, const float *dkappa, float *dX_out,
+                                                   void *stream);
 
 /* The same computation with HOST buffers (pageable or pinned): X_host is
  * copied to the device, the path runs, kappa (and idx if idx_host_out is not

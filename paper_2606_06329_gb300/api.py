@@ -137,6 +137,21 @@ class Context:
         N.check(st, "mecuco_curvature_range")
         return kappa
 
+    def mecuco_curvature_backward(self, X: torch.Tensor, k: int, idx: torch.Tensor, dkappa: torch.Tensor,
+                                  variant: str = "literal", precision: str = "fp32"):
+        """dX = d(sum_i dkappa_i K_i)/dX with the neighbour lists idx frozen (float32, N x m)."""
+        _check_x(X, self.device)
+        n, m = X.shape
+        if idx.dtype != torch.int32 or tuple(idx.shape) != (n, k) or not idx.is_contiguous():
+            raise ValueError("idx must be a contiguous int32 (N, k) tensor")
+        dk = dkappa.to(device=X.device, dtype=torch.float32).contiguous()
+        dX = torch.empty((n, m), dtype=torch.float32, device=X.device)
+        st = self.lib.mecuco_curvature_backward(self.handle, _ptr(X), _dtype_code(X), n, m, X.stride(0), int(k),
+                                                _ptr(idx), _VAR[variant], _PREC[precision], _ptr(dk), _ptr(dX),
+                                                _stream(self.device))
+        N.check(st, "mecuco_curvature_backward")
+        return dX
+
     def mecuco_get_stage_times(self) -> dict:
         ms = (C.c_double * len(N.STAGES))()
         cnt = (C.c_int64 * len(N.STAGES))()

@@ -203,6 +203,9 @@ KnnPlan plan_knn(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t 
     const int64_t want = (p.tc ? 1LL : 2LL) * h->num_sms;
     p.nsplit = 1;
     if (qblocks < want) p.nsplit = (int)std::min<int64_t>((want + qblocks - 1) / qblocks, 1024 / p.kc);
+    // tensor-core search: at least 2 splits, so a wave of the persistent CTAs
+    // (one per SM) touches num_sms / 2 query tiles, which stay in L2
+    if (p.tc) p.nsplit = std::max(p.nsplit, std::min(2, 1024 / p.kc));
     while (p.nsplit > 1 && (N + p.nsplit - 1) / p.nsplit < p.kc) --p.nsplit;
     return p;
 }
@@ -211,6 +214,8 @@ struct KnnBufs {
     float *norms, *cand_d;
     int32_t *cand_i, *flags;
     void *xb;
+    float *merged_d;    // merged lists (tensor-core path with nsplit > 1)
+    int32_t *merged_i;
 };
 
 // Scratch of run_knn, carved after `start`.
@@ -220,6 +225,9 @@ void knn_scratch(Carver &c, const KnnPlan &p, int64_t N, KnnBufs *b) {
     b->cand_i = c.take<int32_t>((size_t)p.qchunk * p.nsplit * p.kc);
     b->flags = c.take<int32_t>((size_t)p.qchunk);
     b->xb = p.bf16_copy ? (void *)c.take<uint16_t>((size_t)N * p.ldb) : nullptr;
+    const bool merge = p.tc && p.nsplit > 1 && !p.bf16_copy;
+    b->merged_d = merge ? c.take<float>((size_t)p.qchunk * p.kc) : nullptr;
+    b->merged_i = merge ? c.take<int32_t>((size_t)p.qchunk * p.kc) : nullptr;
 }
 
 // kNN of query rows [rb, re) (outputs relative to rb); scratch at ws + start,
@@ -242,17 +250,31 @@ mecuco_status run_knn(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int
         int64_t nq = std::min(p.qchunk, re - q0);
         int32_t *io = idx_out + (q0 - rb) * k;
         float *dout = dist_out ? dist_out + (q0 - rb) * k : nullptr;
-        if (p.tc)
+        const float *rd = b.cand_d;
+        const int32_t *ri = b.cand_i;
+        int rsplit = p.nsplit;
+        if (p.tc) {
             LAUNCH(h, MECUCO_STAGE_KNN_SEARCH, s,
                    launch_knn_tc(Xb, N, m, p.ldb, b.norms, q0, nq, p.kc, p.nsplit, include_self, b.cand_d, b.cand_i,
                                  h->ctr, s));
-        else
+            // BF16 storage: merge the split lists down to kc before the re-rank.  A
+            // BF16 copy of FP32 data perturbs d~ more, so its rows keep the whole
+            // nsplit * kc pool for the certification margin.
+            if (b.merged_d) {
+                LAUNCH(h, MECUCO_STAGE_KNN_RERANK, s,
+                       launch_knn_merge(b.cand_d, b.cand_i, nq, p.kc, p.nsplit, b.merged_d, b.merged_i, s));
+                rd = b.merged_d;
+                ri = b.merged_i;
+                rsplit = 1;
+            }
+        } else {
             LAUNCH(h, MECUCO_STAGE_KNN_SEARCH, s,
                    launch_knn_simt(X, dt, N, m, ld, b.norms, q0, nq, p.kc, p.nsplit, include_self, b.cand_d,
                                    b.cand_i, s));
+        }
         LAUNCH(h, MECUCO_STAGE_KNN_RERANK, s,
-               launch_knn_rerank(X, dt, N, m, ld, b.norms, q0, nq, p.kc, p.nsplit, k, b.cand_d, b.cand_i, io, dout,
-                                 b.flags, h->ctr, s));
+               launch_knn_rerank(X, dt, N, m, ld, b.norms, q0, nq, p.kc, rsplit, k, rd, ri, io, dout, b.flags, h->ctr,
+                                 s));
         LAUNCH(h, MECUCO_STAGE_KNN_FALLBACK, s,
                launch_knn_fallback(X, dt, N, m, ld, q0, nq, k, include_self, b.flags, io, dout, h->ctr, s));
     }
@@ -536,6 +558,67 @@ mecuco_status mecuco_curvature(mecuco_t h, const void *X, mecuco_dtype dt, int64
                                float *kappa_out, float *lambda_out, float *U_out, float *s_out, void *stream) {
     return mecuco_curvature_range(h, X, dt, N, m, ld, k, idx, include_self, var, prec, 0, N, kappa_out, lambda_out,
                                   U_out, s_out, stream);
+}
+
+mecuco_status mecuco_curvature_backward(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
+                                        int k, const int32_t *idx, mecuco_variant var, mecuco_precision prec,
+                                        const float *dkappa, float *dX_out, void *stream) {
+    mecuco_status st = check_common(h, X, dt, N, m, ld, k, 1);  // idx is given: k <= N
+    if (st != MECUCO_OK) return st;
+    if (!idx || !dkappa || !dX_out) return MECUCO_ERR_INVALID_ARG;
+    if (var != MECUCO_FAST_LITERAL && var != MECUCO_FAST_HAAR) return MECUCO_ERR_INVALID_ARG;
+    if (prec != MECUCO_PREC_FP32 && prec != MECUCO_PREC_BF16_MIXED) return MECUCO_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = begin_call(h, s)) != MECUCO_OK) return st;
+    if ((st = ensure_items(h, k)) != MECUCO_OK) return st;
+    const bool tc_moments = prec == MECUCO_PREC_BF16_MIXED;
+    if (tc_moments && (st = ensure_pairs(h, k)) != MECUCO_OK) return st;
+    // per point: forward buffers + dG, dR, dQ + C and dM (k^3 each)
+    const int64_t per_point = m3_pair_floats(k) + 6LL * k * k + 4LL * k + 2LL * k * k * k;
+    int64_t chunk = h->chunk_points > 0 ? h->chunk_points
+                                         : std::max<int64_t>(256, std::min<int64_t>(65536, ((int64_t)2 << 30) /
+                                                                                             (per_point * 4)));
+    chunk = std::min(chunk, N);
+    Carver t(nullptr);
+    EstBufs b;
+    est_scratch(t, chunk, k, &b);
+    t.take<float>((size_t)chunk * k * k);
+    t.take<float>((size_t)chunk * k);
+    t.take<float>((size_t)chunk * k * k);
+    t.take<float>((size_t)chunk * k * k * k);
+    t.take<float>((size_t)chunk * k * k * k);
+    if ((st = ensure(h->ws, h->ws_bytes, t.off)) != MECUCO_OK) return st;
+    Carver c(h->ws);
+    est_scratch(c, chunk, k, &b);
+    float *dG = c.take<float>((size_t)chunk * k * k);
+    float *dR = c.take<float>((size_t)chunk * k);
+    float *dQ = c.take<float>((size_t)chunk * k * k);
+    float *Cb = c.take<float>((size_t)chunk * k * k * k);
+    float *dM = c.take<float>((size_t)chunk * k * k * k);
+    CK(cudaMemsetAsync(dX_out, 0, sizeof(float) * (size_t)N * m, s));
+    const int fp64 = h->jacobi_fp64 >= 0 ? h->jacobi_fp64 : (prec == MECUCO_PREC_BF16_MIXED ? 1 : 0);
+    const bool need_q = var == MECUCO_FAST_HAAR;
+    for (int64_t p0 = 0; p0 < N; p0 += chunk) {
+        const int64_t np = std::min(chunk, N - p0);
+        const int32_t *nb = idx + p0 * k;
+        if (tc_moments) {
+            LAUNCH(h, MECUCO_STAGE_MOMENTS, s,
+                   launch_moments_tc(X, dt, N, m, ld, nb, k, np, h->pair_ab, b.M, b.G, b.R, need_q ? b.Q : nullptr,
+                                     h->ctr, s));
+        } else {
+            LAUNCH(h, MECUCO_STAGE_GRAM, s,
+                   launch_patch_gram(X, dt, N, m, ld, nb, k, 0, np, b.G, b.R, need_q ? b.Q : nullptr, h->ctr, s));
+            LAUNCH(h, MECUCO_STAGE_MOMENTS, s,
+                   launch_patch_m3(X, dt, N, m, ld, nb, k, 0, np, b.M, h->m3_items, h->ctr, s));
+        }
+        LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(b.G, k, np, fp64, h->jacobi_max_sweeps, b.sig, b.U, h->ctr, s));
+        if (fp64 == 1) ++h->launches;
+        LAUNCH(h, MECUCO_STAGE_ADJOINT, s,
+               launch_adjoint(X, dt, N, m, ld, nb, k, np, (int)var, b.sig, b.U, b.M, b.R, b.Q, dkappa + p0, dG, dR, dQ,
+                              Cb, dM, dX_out, m, s));
+        ++h->launches;  // two kernels
+    }
+    return MECUCO_OK;
 }
 
 mecuco_status mecuco_curvature_host(mecuco_t h, const void *X_host, mecuco_dtype dt, int64_t N, int64_t m,

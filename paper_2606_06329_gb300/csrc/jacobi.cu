@@ -8,7 +8,9 @@
 //   1. the table threads compute each pair's rotation from the current 2 x 2
 //      block: tau = (a_qq - a_pp) / (2 a_pq), t = sign(tau) / (|tau| +
 //      sqrt(1 + tau^2)), c = 1/sqrt(1 + t^2), s = t c (the rotation zeroing
-//      a_pq); pairs with |a_pq| <= eps sqrt(|a_pp a_qq|) get (c, s) = (1, 0);
+//      a_pq); pairs with |a_pq| <= eps sqrt(|a_pp a_qq|) are skipped, and the
+//      rotating pairs are compacted into the round's table (late sweeps are
+//      cheap because few pairs still rotate);
 //   2. A <- A J (each thread walks one row over its share of the pairs),
 //   3. A <- J^T A (one column per thread), a_pq := 0 for rotated pairs,
 //   4. U <- U J.
@@ -54,6 +56,7 @@ jacobi_kernel(const float *__restrict__ G, int k, int64_t np, int max_sweeps, fl
     int *tp = reinterpret_cast<int *>(ts + h);  // [h] p
     int *tq = tp + h;                           // [h] q
     __shared__ int s_rot;
+    __shared__ int s_act;  // rotations in the current round (compacted table length)
 
     const int tid = threadIdx.x;
     const int64_t patch = blockIdx.x;
@@ -63,16 +66,14 @@ jacobi_kernel(const float *__restrict__ G, int k, int64_t np, int max_sweeps, fl
         A[r * ld + c] = (r < k && c < k) ? (Real)g[r * k + c] : (Real)0;
         V[r * ld + c] = (r == c) ? (Real)1 : (Real)0;
     }
-    if (tid == 0) s_rot = 0;
+    if (tid == 0) { s_rot = 0; s_act = 0; }
     __syncthreads();
     const Real eps = JacobiEps<Real>::rel();
-    // thread -> (line, pair half) for the row/column/U walks: kp lines, JT/kp pair groups
+    // thread -> (line, pair group) for the row/column/U walks: kp lines, JT/kp groups
     const int groups = JT / kp > 0 ? JT / kp : 1;
     const int line = tid % kp;
     const int grp = tid / kp;
     const bool walker = tid < kp * groups;
-    const int per = (h + groups - 1) / groups;
-    const int i0 = grp * per, i1 = min(h, i0 + per);
 
     int sweep = 0;
     bool converged = false;
@@ -84,17 +85,19 @@ jacobi_kernel(const float *__restrict__ G, int k, int64_t np, int max_sweeps, fl
                 else { a = (round + tid) % (kp - 1); b = (round + kp - 1 - tid) % (kp - 1); }
                 const int p = a < b ? a : b, q = a < b ? b : a;
                 const Real app = A[p * ld + p], aqq = A[q * ld + q], apq = A[p * ld + q];
-                Real c = 1, s = 0;
                 if (fabs(apq) > eps * sqrt(fabs(app * aqq)) && apq != (Real)0) {
                     const Real tau = (aqq - app) / (2 * apq);
                     const Real t = (tau >= 0 ? (Real)1 : (Real)-1) / (fabs(tau) + sqrt((Real)1 + tau * tau));
-                    c = (Real)1 / sqrt((Real)1 + t * t);
-                    s = t * c;
-                    atomicAdd(&s_rot, 1);
+                    const Real c = (Real)1 / sqrt((Real)1 + t * t);
+                    // rotations of one round commute: keep only those that rotate, in any order
+                    const int slot = atomicAdd(&s_act, 1);
+                    tc[slot] = c; ts[slot] = t * c; tp[slot] = p; tq[slot] = q;
                 }
-                tc[tid] = c; ts[tid] = s; tp[tid] = p; tq[tid] = q;
             }
             __syncthreads();
+            const int nact = s_act;
+            const int per = (nact + groups - 1) / groups;
+            const int i0 = grp * per, i1 = min(nact, i0 + per);
             // A <- A J (thread walks row `line`)
             if (walker && line < kp) {
                 Real *row = A + line * ld;
@@ -124,10 +127,11 @@ jacobi_kernel(const float *__restrict__ G, int k, int64_t np, int max_sweeps, fl
                 }
             }
             __syncthreads();
-            if (tid < h && ts[tid] != (Real)0) {
+            if (tid < nact) {
                 A[tp[tid] * ld + tq[tid]] = 0;
                 A[tq[tid] * ld + tp[tid]] = 0;
             }
+            if (tid == 0) { s_rot += nact; s_act = 0; }
             __syncthreads();
         }
         const int rot = s_rot;

@@ -34,6 +34,10 @@ cudaError_t launch_knn_tc(const void *Xb, int64_t N, int64_t m, int64_t ldb, con
                           int64_t q0, int64_t nq, int kc, int nsplit, int include_self,
                           float *cand_d, int32_t *cand_i, DevCounters *ctr, cudaStream_t s);
 size_t knn_tc_smem_bytes(int kc);
+// Merge nsplit per-split lists (layout of launch_knn_simt) into one list of the
+// kc smallest per query (out: nq x kc); certification carries over.
+cudaError_t launch_knn_merge(const float *in_d, const int32_t *in_i, int64_t nq, int kc, int nsplit, float *out_d,
+                             int32_t *out_i, cudaStream_t s);
 // BF16 copy of X (round to nearest even) with leading dimension ldb >= m.
 cudaError_t launch_to_bf16(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, void *Y,
                            int64_t ldb, cudaStream_t s);
@@ -107,5 +111,15 @@ cudaError_t launch_estimator(const float *sigma, const float *U, const float *M,
                              const float *Q, int k, int64_t m, int64_t np, int variant,
                              float *kappa, float *lambda_out, float *s_out, DevCounters *ctr,
                              cudaStream_t s);
+
+// ---- adjoint ---------------------------------------------------------------
+// d(sum_i gk_i K_i)/dX for the points of one chunk (idx offset to the chunk),
+// accumulated into dX (row stride ldd) with atomics.  Inputs are the forward's
+// sigma/U/M/R/Q of the chunk; dG, dR, dQ (np x k x k, k, k x k), C and dMbuf
+// (np x k^3 each) are scratch.
+cudaError_t launch_adjoint(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, const int32_t *idx,
+                           int k, int64_t np, int variant, const float *sigma, const float *U, const float *M,
+                           const float *R, const float *Q, const float *gk, float *dG, float *dR, float *dQ, float *C,
+                           float *dMbuf, float *dX, int64_t ldd, cudaStream_t s);
 
 }  // namespace mecuco

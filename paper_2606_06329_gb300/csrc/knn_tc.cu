@@ -2,8 +2,9 @@
 // search on the 5th-generation tensor cores: BF16 x BF16 -> FP32 distance GEMM
 // with the per-row candidate selection fused into the TMEM drain.
 //
-// CTA = 128 query rows (the MMA's M, one TMEM lane each) sweeping its split of
-// the candidate rows in tiles of 256 (the MMA's N).  Warp roles:
+// Persistent CTAs (one per SM); a work item = 128 query rows (the MMA's M, one
+// TMEM lane each) against one split of the candidate rows, swept in tiles of
+// 256 (the MMA's N).  Warp roles:
 //   warp 0      TMA producer: for every (candidate tile, 64-wide K block) loads
 //               the 128 x 64 query slice and the 256 x 64 candidate slice
 //               (128-byte swizzled, zero-filled past the matrix edges) into a
@@ -82,6 +83,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, int64_t N,
               int64_t m, const float *__restrict__ norms, int64_t q0, int64_t nq, int kc, int nsplit,
               int include_self, float *__restrict__ cand_d, int32_t *__restrict__ cand_i, DevCounters *ctr) {
+    // Persistent: CTA b takes work items b, b + G, b + 2G, ... (G = gridDim.x),
+    // item = (query block item / nsplit, candidate split item % nsplit).  All
+    // CTAs start their items together and every item has the same number of
+    // tiles, so the CTAs sweep the same candidate tiles in lockstep (each tile
+    // comes from HBM about once per wave) and a wave touches only
+    // G / nsplit query tiles, which stay resident in L2.
     extern __shared__ __align__(1024) uint8_t tsm_raw[];
     // 1024-byte aligned stage ring, then candidate distances [kc][TBM], then barriers
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tsm_raw) + 1023) & ~(uintptr_t)1023);
@@ -90,13 +97,9 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
     TcShared *sh = reinterpret_cast<TcShared *>(Ld + (size_t)kc * TBM);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t qb = q0 + (int64_t)blockIdx.x * TBM;
     const int64_t qend = q0 + nq;
-    const int split = blockIdx.y;
+    const int64_t nitems = ((nq + TBM - 1) / TBM) * nsplit;
     const int64_t per = (N + nsplit - 1) / nsplit;
-    const int64_t cbeg = (int64_t)split * per;
-    const int64_t cend = min(N, cbeg + per);
-    const int ntiles = cend > cbeg ? (int)((cend - cbeg + TBN - 1) / TBN) : 0;
     const int nkb = (int)((m + TBK - 1) / TBK);
     volatile int *abort_flag = &sh->abort;
     __shared__ int never;  // a flag that stays 0: drain waits are bounded by time only
@@ -132,6 +135,11 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
         if (lane == 0) {
             int it = 0;
             bool ok = true;
+            for (int64_t item = blockIdx.x; item < nitems && ok && !*abort_flag; item += gridDim.x) {
+            const int split = (int)(item % nsplit);
+            const int64_t qb = q0 + (item / nsplit) * TBM;
+            const int64_t cbeg = (int64_t)split * per, cend = min(N, cbeg + per);
+            const int ntiles = cend > cbeg ? (int)((cend - cbeg + TBN - 1) / TBN) : 0;
             for (int t = 0; t < ntiles && ok && !*abort_flag; ++t) {
                 const int c0 = (int)(cbeg + (int64_t)t * TBN);
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
@@ -144,6 +152,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
                     tc::tma_load_2d(sa, &map_a, fb, kb * TBK, (int)qb);
                     tc::tma_load_2d(sa + A_BYTES, &map_b, fb, kb * TBK, c0);
                 }
+            }
             }
             if (!ok) {
                 atomicOr(&ctr->status, (unsigned)DEV_TIMEOUT);
@@ -162,8 +171,12 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
         if (lane == 0) {
             int it = 0;
             bool ok = true;
-            int t = 0;
-            for (; t < ntiles && ok && !*abort_flag; ++t) {
+            int t = 0;  // tiles issued so far by this CTA (all items)
+            for (int64_t item = blockIdx.x; item < nitems && ok && !*abort_flag; item += gridDim.x) {
+            const int split = (int)(item % nsplit);
+            const int64_t cbeg = (int64_t)split * per, cend = min(N, cbeg + per);
+            const int ntiles = cend > cbeg ? (int)((cend - cbeg + TBN - 1) / TBN) : 0;
+            for (int tt = 0; tt < ntiles && ok && !*abort_flag; ++tt, ++t) {
                 const int acc = t & 1;
                 if (!tc::mbar_wait(tc::smem_u32(&sh->tempty[acc]), ((t >> 1) & 1) ^ 1, abort_flag, WAIT_LIMIT)) {
                     ok = false;
@@ -189,6 +202,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
                 }
                 if (ok) tc::commit(tc::smem_u32(&sh->tfull[acc]));
             }
+            }
             if (!ok) {
                 atomicOr(&ctr->status, (unsigned)DEV_TIMEOUT);
                 sh->abort = 1;
@@ -204,47 +218,54 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
         // ------------------------------ epilogue ---------------------------------
         const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
         const int row = quarter * 32 + lane;
-        const int64_t gq = qb + row;
-        const bool valid_row = gq < qend;
-        const float qn = valid_row ? norms[gq] : 0.f;
-        const int64_t out_base = valid_row ? ((gq - q0) * nsplit + split) * (int64_t)kc : 0;
-        ListState st{valid_row ? INFINITY : -INFINITY, 0, 0};
-        int32_t *out_i = cand_i + out_base;
-        for (int t = 0; t < ntiles && !*abort_flag; ++t) {
-            const int acc = t & 1;
-            if (!tc::mbar_wait(tc::smem_u32(&sh->tfull[acc]), (t >> 1) & 1, abort_flag, WAIT_LIMIT)) {
-                atomicOr(&ctr->status, (unsigned)DEV_TIMEOUT);
-                sh->abort = 1;
-                break;
-            }
-            tc::fence_after();
-            const int64_t c0 = cbeg + (int64_t)t * TBN;
-            const bool masked = (c0 + TBN > cend) || (!include_self && gq >= c0 && gq < c0 + TBN);
-            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * TBN);
-#pragma unroll 1
-            for (int ch = 0; ch < TBN / 32; ++ch) {
-                uint32_t r[32];
-                tc::tmem_ld_32x32b_x32(taddr + ch * 32, r);
-                tc::tmem_ld_wait();
-                const int64_t cb = c0 + ch * 32;
-                const float *cnp = norms + cb;
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int64_t c = cb + j;
-                    const float cn = (c < N) ? __ldg(cnp + j) : 0.f;
-                    float d = fmaf(-2.f, __uint_as_float(r[j]), qn + cn);
-                    if (masked && (c >= cend || (!include_self && c == gq))) d = INFINITY;
-                    if (d < st.thr) st = list_insert(st, d, (int)c, Ld, out_i, row, kc);
+        int t = 0;  // tiles drained so far by this CTA (all items)
+        for (int64_t item = blockIdx.x; item < nitems && !*abort_flag; item += gridDim.x) {
+            const int split = (int)(item % nsplit);
+            const int64_t qb = q0 + (item / nsplit) * TBM;
+            const int64_t cbeg = (int64_t)split * per, cend = min(N, cbeg + per);
+            const int ntiles = cend > cbeg ? (int)((cend - cbeg + TBN - 1) / TBN) : 0;
+            const int64_t gq = qb + row;
+            const bool valid_row = gq < qend;
+            const float qn = valid_row ? norms[gq] : 0.f;
+            const int64_t out_base = valid_row ? ((gq - q0) * nsplit + split) * (int64_t)kc : 0;
+            ListState st{valid_row ? INFINITY : -INFINITY, 0, 0};
+            int32_t *out_i = cand_i + out_base;
+            for (int tt = 0; tt < ntiles && !*abort_flag; ++tt, ++t) {
+                const int acc = t & 1;
+                if (!tc::mbar_wait(tc::smem_u32(&sh->tfull[acc]), (t >> 1) & 1, abort_flag, WAIT_LIMIT)) {
+                    atomicOr(&ctr->status, (unsigned)DEV_TIMEOUT);
+                    sh->abort = 1;
+                    break;
                 }
+                tc::fence_after();
+                const int64_t c0 = cbeg + (int64_t)tt * TBN;
+                const bool masked = (c0 + TBN > cend) || (!include_self && gq >= c0 && gq < c0 + TBN);
+                const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * TBN);
+#pragma unroll 1
+                for (int ch = 0; ch < TBN / 32; ++ch) {
+                    uint32_t r[32];
+                    tc::tmem_ld_32x32b_x32(taddr + ch * 32, r);
+                    tc::tmem_ld_wait();
+                    const int64_t cb = c0 + ch * 32;
+                    const float *cnp = norms + cb;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int64_t c = cb + j;
+                        const float cn = (c < N) ? __ldg(cnp + j) : 0.f;
+                        float d = fmaf(-2.f, __uint_as_float(r[j]), qn + cn);
+                        if (masked && (c >= cend || (!include_self && c == gq))) d = INFINITY;
+                        if (d < st.thr) st = list_insert(st, d, (int)c, Ld, out_i, row, kc);
+                    }
+                }
+                tc::fence_before();
+                tc::mbar_arrive(tc::smem_u32(&sh->tempty[acc]));
             }
-            tc::fence_before();
-            tc::mbar_arrive(tc::smem_u32(&sh->tempty[acc]));
-        }
-        if (valid_row) {
-            for (int s2 = 0; s2 < kc; ++s2) {
-                const bool used = s2 < st.cnt;
-                cand_d[out_base + s2] = used ? Ld[s2 * TBM + row] : INFINITY;
-                if (!used) out_i[s2] = -1;
+            if (valid_row) {
+                for (int s2 = 0; s2 < kc; ++s2) {
+                    const bool used = s2 < st.cnt;
+                    cand_d[out_base + s2] = used ? Ld[s2 * TBM + row] : INFINITY;
+                    if (!used) out_i[s2] = -1;
+                }
             }
         }
     }
@@ -298,9 +319,70 @@ cudaError_t launch_knn_tc(const void *Xb, int64_t N, int64_t m, int64_t ldb, con
     const size_t smem = knn_tc_smem_bytes(kc);
     cudaError_t e = cudaFuncSetAttribute(knn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)((nq + TBM - 1) / TBM), (unsigned)nsplit);
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int64_t items = ((nq + TBM - 1) / TBM) * nsplit;
+    dim3 grid((unsigned)(items < sms ? items : sms));  // persistent: one CTA per SM
     knn_tc_kernel<<<grid, TC_THREADS, smem, s>>>(ma, mb, N, m, norms, q0, nq, kc, nsplit, include_self, cand_d,
                                                   cand_i, ctr);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Merge of the per-split candidate lists of each query into one list of the kc
+// smallest approximate distances (ties to the lower index).  Every point left
+// out keeps d~ >= the merged list's maximum (a point rejected by split s has
+// d~ >= that split's maximum, which bounds the union's kc-th smallest from
+// above), so the re-rank's certification applies to the merged list unchanged.
+// One warp per query; rank counting over the nsplit * kc entries.
+// ---------------------------------------------------------------------------
+constexpr int MG_WARPS = 4;
+
+__global__ void __launch_bounds__(MG_WARPS * 32)
+knn_merge_kernel(const float *__restrict__ in_d, const int32_t *__restrict__ in_i, int64_t nq, int kc, int nsplit,
+                 float *__restrict__ out_d, int32_t *__restrict__ out_i) {
+    extern __shared__ float mgs[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int L = kc * nsplit;
+    float *d = mgs + (size_t)w * L * 2;
+    int *ix = reinterpret_cast<int *>(d + L);
+    const int64_t q = (int64_t)blockIdx.x * MG_WARPS + w;
+    if (q >= nq) return;
+    for (int c = lane; c < L; c += 32) {
+        d[c] = in_d[q * L + c];
+        ix[c] = in_i[q * L + c];
+    }
+    __syncwarp();
+    float *od = out_d + q * kc;
+    int32_t *oi = out_i + q * kc;
+    for (int c = lane; c < kc; c += 32) { od[c] = INFINITY; oi[c] = -1; }
+    __syncwarp();
+    for (int c = lane; c < L; c += 32) {
+        const int j = ix[c];
+        if (j < 0) continue;
+        const float dc = d[c];
+        int rank = 0;
+        for (int o = 0; o < L; ++o) {
+            const int jo = ix[o];
+            if (jo < 0) continue;
+            const float dd = d[o];
+            rank += (dd < dc) || (dd == dc && jo < j);
+        }
+        if (rank < kc) { od[rank] = dc; oi[rank] = j; }
+    }
+}
+
+cudaError_t launch_knn_merge(const float *in_d, const int32_t *in_i, int64_t nq, int kc, int nsplit, float *out_d,
+                             int32_t *out_i, cudaStream_t s) {
+    if (nq <= 0) return cudaSuccess;
+    const size_t smem = (size_t)MG_WARPS * kc * nsplit * 2 * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(knn_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    knn_merge_kernel<<<(unsigned)((nq + MG_WARPS - 1) / MG_WARPS), MG_WARPS * 32, smem, s>>>(in_d, in_i, nq, kc, nsplit,
+                                                                                             out_d, out_i);
     return cudaGetLastError();
 }
 

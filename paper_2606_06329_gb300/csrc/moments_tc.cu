@@ -1,6 +1,6 @@
 // moments_tc.cu - Steps 2-3 for the BF16-mixed form: gather and centre each
-// patch once per pass and produce, on the 5th-generation tensor cores, every
-// moment the estimator needs:
+// patch and produce, on the 5th-generation tensor cores, every moment the
+// estimator needs:
 //   M[a][b][t] = sum_c X_c[a,c] X_c[b,c] X_c[t,c]   (pairs a <= b, all t)
 //   G[a][b]    = sum_c X_c[a,c] X_c[b,c]             (= X_c X_c^T, eq. svd_cov)
 //   Q[a][b]    = sum_c w_c X_c[a,c] X_c[b,c],  w_c = sum_j X_c[j,c]^2 (Haar term)
@@ -10,16 +10,19 @@
 //   B = [X_c ; 1 ; w]                  (k + 2 rows, zero-padded to N = 16 ceil((k+2)/16))
 // so D[(a,b), t] = M[a][b][t], D[(a,b), k] = G[a][b], D[(a,b), k+1] = Q[a][b].
 //
-// One CTA (256 threads) per patch.  The column range of the patch is streamed
-// in 64-column chunks: the CUDA cores gather the k neighbour rows, centre each
-// column (x - mean over the k rows) in FP32, accumulate R, form w, and write Z
-// and B as BF16 into a 128-byte-swizzled, K-major operand buffer (two buffers,
-// so building chunk i+1 overlaps the MMAs of chunk i); one thread then issues
-// tcgen05.mma (M=128, N, K=16) for every tile of the current pass into TMEM
-// with FP32 accumulation.  TMEM holds up to TPP tiles, so the tiles are covered
-// in passes over the columns (re-reading the patch from L2).  After a pass the
-// 8 warps drain TMEM straight to the pair-major M buffer, G and Q.
-// Every mbarrier wait is bounded (MECUCO_ERR_TIMEOUT, no trap).
+// One CTA (512 threads) per patch.  The columns of the patch are streamed in
+// 64-column chunks: the CUDA cores gather the k neighbour rows (the next
+// chunk's loads are issued before the current chunk is processed, so their
+// latency hides behind it), centre each column (x - mean over the k rows) in
+// FP32, accumulate R, form w, and write Z and B as BF16 into a 128-byte-
+// swizzled K-major operand buffer (two buffers: building chunk i+1 overlaps
+// the MMAs of chunk i); one thread issues tcgen05.mma (M=128, N, K=16) for
+// every tile of the current pass into TMEM (FP32 accumulation).  TMEM holds up
+// to TPP tiles, so the tiles are covered in passes over the columns (re-reading
+// the patch from L2).  After a pass the warps drain TMEM through shared memory
+// so each tile's 128 pair rows (contiguous in the pair-major M buffer) leave as
+// coalesced stores.  Every mbarrier wait is bounded (MECUCO_ERR_TIMEOUT, no
+// trap).
 #include <math.h>
 
 #include "common.cuh"
@@ -29,14 +32,15 @@
 namespace mecuco {
 
 namespace {
-constexpr int MT_THREADS = 256;
-constexpr int MT_CH = 64;              // columns per chunk (one 128-byte swizzle row of BF16)
-constexpr int MT_TPP = 5;              // tiles per pass (shared-memory bound)
+constexpr int MT_THREADS = 512;
+constexpr int MT_CH = 64;                  // columns per chunk (one 128-byte swizzle row of BF16)
+constexpr int MT_TPP = 5;                  // tiles per pass (shared-memory bound)
 constexpr int MT_TILE_BYTES = 128 * 128;   // 128 rows x 128 bytes
 constexpr int MT_BMAX_ROWS = 80;           // k <= 64 -> N <= 80
 constexpr int MT_B_BYTES = MT_BMAX_ROWS * 128;
 constexpr int MT_BUF_BYTES = MT_TPP * MT_TILE_BYTES + MT_B_BYTES;
 constexpr int MT_XS_LD = 68;               // FP32 staging row stride (floats)
+constexpr int MT_XS_FLOATS = 64 * MT_XS_LD;
 constexpr long long MT_WAIT = 1000000000LL;
 
 __device__ __forceinline__ uint32_t sw128(int row, int unit16) {
@@ -48,13 +52,63 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t *>(&v);
 }
+
+// Raw gather of one 8-column unit of one row (zero past m).
+template <typename T>
+struct Unit8;
+template <>
+struct Unit8<__nv_bfloat16> {
+    uint4 v;
+    __device__ __forceinline__ void load(const __nv_bfloat16 *row, int64_t a, int64_t m, bool vec) {
+        if (vec && a + 8 <= m) {
+            v = __ldg(reinterpret_cast<const uint4 *>(row + a));
+        } else {
+            uint32_t h[8];
+            for (int e = 0; e < 8; ++e)
+                h[e] = (a + e < m) ? (uint32_t)__ldg(reinterpret_cast<const unsigned short *>(row) + a + e) : 0u;
+            v = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+        }
+    }
+    __device__ __forceinline__ void zero() { v = make_uint4(0, 0, 0, 0); }
+    __device__ __forceinline__ void store(float *dst) const {
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        float f[8];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            f[2 * e] = __uint_as_float(w[e] << 16);
+            f[2 * e + 1] = __uint_as_float(w[e] & 0xffff0000u);
+        }
+        reinterpret_cast<float4 *>(dst)[0] = make_float4(f[0], f[1], f[2], f[3]);
+        reinterpret_cast<float4 *>(dst)[1] = make_float4(f[4], f[5], f[6], f[7]);
+    }
+};
+template <>
+struct Unit8<float> {
+    float4 lo, hi;
+    __device__ __forceinline__ void load(const float *row, int64_t a, int64_t m, bool vec) {
+        if (vec && a + 8 <= m) {
+            lo = __ldg(reinterpret_cast<const float4 *>(row + a));
+            hi = __ldg(reinterpret_cast<const float4 *>(row + a) + 1);
+        } else {
+            float f[8];
+            for (int e = 0; e < 8; ++e) f[e] = (a + e < m) ? __ldg(row + a + e) : 0.f;
+            lo = make_float4(f[0], f[1], f[2], f[3]);
+            hi = make_float4(f[4], f[5], f[6], f[7]);
+        }
+    }
+    __device__ __forceinline__ void zero() { lo = hi = make_float4(0.f, 0.f, 0.f, 0.f); }
+    __device__ __forceinline__ void store(float *dst) const {
+        reinterpret_cast<float4 *>(dst)[0] = lo;
+        reinterpret_cast<float4 *>(dst)[1] = hi;
+    }
+};
 }  // namespace
 
 __host__ __device__ inline int moments_tc_n(int k) { return ((k + 2 + 15) / 16) * 16; }
 
 size_t moments_tc_smem_bytes() {
-    return 1024 + 2 * (size_t)MT_BUF_BYTES + (size_t)64 * MT_XS_LD * sizeof(float) + 64 * sizeof(float) +
-           MT_CH * sizeof(float) + 64;
+    return 1024 + 2 * (size_t)MT_BUF_BYTES + 2 * (size_t)MT_XS_FLOATS * sizeof(float) + 64 * sizeof(float) +
+           MT_CH * sizeof(float) + 8 * 64 * sizeof(float) + 64;
 }
 
 template <typename T>
@@ -64,9 +118,10 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
                   float *__restrict__ R, float *__restrict__ Q, DevCounters *ctr) {
     extern __shared__ __align__(1024) uint8_t msm_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(msm_raw) + 1023) & ~(uintptr_t)1023);
-    float *Xs = reinterpret_cast<float *>(base + 2 * MT_BUF_BYTES);  // [64][MT_XS_LD] centred chunk
-    float *Rs = Xs + 64 * MT_XS_LD;                                  // [64]
-    float *Ws = Rs + 64;                                             // [MT_CH] column weights w_c
+    float *Xs0 = reinterpret_cast<float *>(base + 2 * MT_BUF_BYTES);  // two [64][MT_XS_LD] staging chunks
+    float *Rs = Xs0 + 2 * MT_XS_FLOATS;                                // [64]
+    float *Ws = Rs + 64;                                               // [MT_CH] column weights w_c
+    float *Part = Ws + MT_CH;                                          // [8][64] centring partials
     __shared__ uint64_t mma_done[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int rows[64];
@@ -80,6 +135,7 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
     const int tpp = min(MT_TPP, 512 / Nb);
     const int nchunks = (int)((m + MT_CH - 1) / MT_CH);
     const uint32_t idesc = tc::idesc_bf16_f32(128, Nb);
+    const bool vec = (ld % 8 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
 
     if (tid < 64) {
         int r = 0;
@@ -106,66 +162,92 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
     tc::fence_after();
     const uint32_t tmem = tmem_slot;
     volatile int *abortp = &abort_flag;
-    // commits issued so far on mma_done[0] / mma_done[1] (uniform across threads)
-    uint32_t commits0 = 0, commits1 = 0;
+    uint32_t commits0 = 0, commits1 = 0;  // commits issued on mma_done[0] / [1] (uniform across threads)
+
+    // gather unit of this thread: row gj, 8-column group gg (64 rows x 8 groups = 512 units)
+    const int gj = tid >> 3, gg = tid & 7;
+    const T *grow = X + (int64_t)rows[gj] * ld;
+    Unit8<T> pre;
 
     for (int t0 = 0; t0 < ntiles && !*abortp; t0 += tpp) {
         const int nt = min(tpp, ntiles - t0);
+        // prologue: chunk 0 into staging 0
+        if (gj < k) pre.load(grow, gg * 8, m, vec); else pre.zero();
+        pre.store(Xs0 + gj * MT_XS_LD + gg * 8);
         for (int ci = 0; ci < nchunks; ++ci) {
             const int b = ci & 1;
+            float *Xs = Xs0 + b * MT_XS_FLOATS;
             uint8_t *ob = base + b * MT_BUF_BYTES;
             const int64_t a0 = (int64_t)ci * MT_CH;
-            const uint32_t cb = b ? commits1 : commits0;
-            // buffer b is free once the MMAs of the chunk that used it completed
-            if (cb > 0) {
-                if (!tc::mbar_wait(tc::smem_u32(&mma_done[b]), (cb - 1) & 1, abortp, MT_WAIT)) {
-                    if (tid == 0) { atomicOr(&ctr->status, (unsigned)DEV_TIMEOUT); abort_flag = 1; }
-                }
+            // issue the next chunk's loads now; they land while this chunk is processed
+            const bool has_next = ci + 1 < nchunks;
+            if (has_next) {
+                if (gj < k) pre.load(grow, a0 + MT_CH + gg * 8, m, vec); else pre.zero();
             }
-            // ---- gather the k rows of this chunk into FP32 staging (8 columns per unit)
-            for (int u = tid; u < 64 * 8; u += MT_THREADS) {
-                const int j = u >> 3, g = u & 7;
-                float v[8];
+            __syncthreads();  // staging b complete
+            // ---- centre each column over the k rows: thread (column cc, row group rg)
+            // owns rows 8 rg .. 8 rg + 7; column sums and sums of squares go through
+            // shared partials (8 groups per column)
+            {
+                const int cc = tid & 63, rg = tid >> 6;
+                float v[8], s = 0.f;
 #pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] = 0.f;
-                if (j < k) {
-                    const T *src = X + (int64_t)rows[j] * ld + a0 + g * 8;
-#pragma unroll
-                    for (int e = 0; e < 8; ++e)
-                        if (a0 + g * 8 + e < m) v[e] = load_elem(src + e);
+                for (int e = 0; e < 8; ++e) {
+                    v[e] = Xs[(rg * 8 + e) * MT_XS_LD + cc];  // rows >= k hold zeros
+                    s += v[e];
                 }
-                float4 *dst = reinterpret_cast<float4 *>(Xs + j * MT_XS_LD + g * 8);
-                dst[0] = make_float4(v[0], v[1], v[2], v[3]);
-                dst[1] = make_float4(v[4], v[5], v[6], v[7]);
-            }
-            __syncthreads();
-            // ---- centre each column, column weights w_c, row sums R
-            if (tid < MT_CH) {
-                float s = 0.f;
-                for (int j = 0; j < k; ++j) s += Xs[j * MT_XS_LD + tid];
-                const float mean = s / (float)k;
-                float w = 0.f;
-                for (int j = 0; j < k; ++j) {
-                    const float x = Xs[j * MT_XS_LD + tid] - mean;
-                    Xs[j * MT_XS_LD + tid] = x;
+                Part[rg * 64 + cc] = s;
+                __syncthreads();
+                float tot = 0.f;
+#pragma unroll
+                for (int g = 0; g < 8; ++g) tot += Part[g * 64 + cc];
+                const float mean = tot / (float)k;
+                float w = 0.f, rsum[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const bool real = rg * 8 + e < k;
+                    const float x = real ? v[e] - mean : 0.f;
+                    Xs[(rg * 8 + e) * MT_XS_LD + cc] = x;
                     w = fmaf(x, x, w);
+                    rsum[e] = x;
                 }
-                Ws[tid] = (a0 + tid < m) ? w : 0.f;
+                __syncthreads();  // every thread has read Part
+                Part[rg * 64 + cc] = w;
+                // row sums R (first pass only): warp-reduce each of the 8 rows over 32 columns
+                if (t0 == 0) {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const float r = warp_sum(rsum[e]);
+                        if (lane == 0 && rg * 8 + e < k) atomicAdd(&Rs[rg * 8 + e], r);
+                    }
+                }
+                __syncthreads();
+                if (rg == 0) {
+                    float ws = 0.f;
+#pragma unroll
+                    for (int g = 0; g < 8; ++g) ws += Part[g * 64 + cc];
+                    Ws[cc] = (a0 + cc < m) ? ws : 0.f;
+                }
+            }
+            // operand buffer b is free once the MMAs of the chunk that last used it completed
+            const uint32_t cb = b ? commits1 : commits0;
+            if (tid == 0 && cb > 0) {
+                if (!tc::mbar_wait(tc::smem_u32(&mma_done[b]), (cb - 1) & 1, abortp, MT_WAIT)) {
+                    atomicOr(&ctr->status, (unsigned)DEV_TIMEOUT);
+                    abort_flag = 1;
+                }
             }
             __syncthreads();
-            if (t0 == 0 && tid < k) {
-                float s = 0.f;
-                for (int c = 0; c < MT_CH; ++c) s += Xs[tid * MT_XS_LD + c];
-                Rs[tid] += s;
-            }
             // ---- B operand: rows 0..k-1 = X_c, row k = 1, row k+1 = w, rest 0
             uint8_t *bb = ob + MT_TPP * MT_TILE_BYTES;
             for (int u = tid; u < Nb * 8; u += MT_THREADS) {
                 const int r = u >> 3, g = u & 7;
                 float v[8];
                 if (r < k) {
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) v[e] = Xs[r * MT_XS_LD + g * 8 + e];
+                    const float4 lo = reinterpret_cast<const float4 *>(Xs + r * MT_XS_LD + g * 8)[0];
+                    const float4 hi = reinterpret_cast<const float4 *>(Xs + r * MT_XS_LD + g * 8)[1];
+                    v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w;
+                    v[4] = hi.x; v[5] = hi.y; v[6] = hi.z; v[7] = hi.w;
                 } else if (r == k) {
 #pragma unroll
                     for (int e = 0; e < 8; ++e) v[e] = (a0 + g * 8 + e < m) ? 1.f : 0.f;
@@ -176,9 +258,9 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
 #pragma unroll
                     for (int e = 0; e < 8; ++e) v[e] = 0.f;
                 }
-                uint4 pk = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
-                                      pack_bf16x2(v[6], v[7]));
-                *reinterpret_cast<uint4 *>(bb + sw128(r, g)) = pk;
+                *reinterpret_cast<uint4 *>(bb + sw128(r, g)) =
+                    make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                               pack_bf16x2(v[6], v[7]));
             }
             // ---- A operand: Z rows of this pass's tiles
             for (int u = tid; u < nt * 128 * 8; u += MT_THREADS) {
@@ -196,9 +278,10 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
                                     pack_bf16x2(a_hi.x * b_hi.x, a_hi.y * b_hi.y),
                                     pack_bf16x2(a_hi.z * b_hi.z, a_hi.w * b_hi.w));
                 }
-                const int tile = rl >> 7, row = rl & 127;
-                *reinterpret_cast<uint4 *>(ob + tile * MT_TILE_BYTES + sw128(row, g)) = pk;
+                *reinterpret_cast<uint4 *>(ob + (rl >> 7) * MT_TILE_BYTES + sw128(rl & 127, g)) = pk;
             }
+            // the next chunk's raw values go to the other staging buffer
+            if (has_next) pre.store(Xs0 + (b ^ 1) * MT_XS_FLOATS + gj * MT_XS_LD + gg * 8);
             // make the generic-proxy stores visible to the tensor core, then issue
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
@@ -217,34 +300,27 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
             if (b) ++commits1; else ++commits0;
         }
         // ---- wait for the last MMAs of the pass (bounded), then drain TMEM
-        if (commits0 > 0) tc::mbar_wait(tc::smem_u32(&mma_done[0]), (commits0 - 1) & 1, &never, MT_WAIT);
-        if (commits1 > 0) tc::mbar_wait(tc::smem_u32(&mma_done[1]), (commits1 - 1) & 1, &never, MT_WAIT);
+        if (tid == 0) {
+            if (commits0 > 0) tc::mbar_wait(tc::smem_u32(&mma_done[0]), (commits0 - 1) & 1, &never, MT_WAIT);
+            if (commits1 > 0) tc::mbar_wait(tc::smem_u32(&mma_done[1]), (commits1 - 1) & 1, &never, MT_WAIT);
+        }
+        __syncthreads();
         tc::fence_after();
-        const int quarter = warp & 3, half = warp >> 2;
-        for (int t = half; t < nt; t += 2) {
-            const int pr = (t0 + t) * 128 + quarter * 32 + lane;
-            const bool valid = pr < npairs;
+        // warp group wg = warp / 4 drains tiles wg, wg + 4, ... into its own staging
+        // slot (128 x k floats) in the now idle operand buffers
+        const int quarter = warp & 3, wg = warp >> 2;
+        const size_t slot_bytes = 128 * 64 * sizeof(float);
+        float *stage = reinterpret_cast<float *>(base + (size_t)wg * slot_bytes);
+        for (int tb = 0; tb < nt; tb += 4) {
+            const int t = tb + wg;
+            const bool active = t < nt;
+            const int row = quarter * 32 + lane;
+            const int pr = (t0 + t) * 128 + row;
+            const bool valid = active && pr < npairs;
             int pa = 0, pb = 0;
             if (valid) { const int code = __ldg(pair_ab + pr); pa = code & 0xffff; pb = code >> 16; }
-            float *mrow = M + (pt * (int64_t)npairs + (valid ? pr : 0)) * k;
-            for (int c0 = 0; c0 < Nb; c0 += 16) {
-                uint32_t r[32];
-                // 16 columns per load: use the x32 form on 32-column groups when possible
-                if (c0 + 32 <= Nb && (c0 & 31) == 0) {
-                    tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * Nb + c0), r);
-                    tc::tmem_ld_wait();
-                    if (valid) {
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const int col = c0 + j;
-                            const float v = __uint_as_float(r[j]);
-                            if (col < k) mrow[col] = v;
-                            else if (col == k) { G[pt * k * k + pa * k + pb] = v; G[pt * k * k + pb * k + pa] = v; }
-                            else if (col == k + 1 && Q) { Q[pt * k * k + pa * k + pb] = v; Q[pt * k * k + pb * k + pa] = v; }
-                        }
-                    }
-                    c0 += 16;
-                } else {
+            if (active) {
+                for (int c0 = 0; c0 < Nb; c0 += 16) {
                     uint32_t r16[16];
                     asm volatile(
                         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
@@ -254,19 +330,33 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
                           "=r"(r16[12]), "=r"(r16[13]), "=r"(r16[14]), "=r"(r16[15])
                         : "r"(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * Nb + c0)));
                     tc::tmem_ld_wait();
-                    if (valid) {
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const int col = c0 + j;
-                            const float v = __uint_as_float(r16[j]);
-                            if (col < k) mrow[col] = v;
-                            else if (col == k) { G[pt * k * k + pa * k + pb] = v; G[pt * k * k + pb * k + pa] = v; }
-                            else if (col == k + 1 && Q) { Q[pt * k * k + pa * k + pb] = v; Q[pt * k * k + pb * k + pa] = v; }
+                    for (int j = 0; j < 16; ++j) {
+                        const int col = c0 + j;
+                        const float v = __uint_as_float(r16[j]);
+                        if (col < k) stage[row * k + col] = v;
+                        else if (valid && col == k) {
+                            G[pt * k * k + pa * k + pb] = v;
+                            G[pt * k * k + pb * k + pa] = v;
+                        } else if (valid && col == k + 1 && Q) {
+                            Q[pt * k * k + pa * k + pb] = v;
+                            Q[pt * k * k + pb * k + pa] = v;
                         }
                     }
                 }
-                (void)r;
             }
+            __syncthreads();
+            // coalesced copy of the staged tiles: rows [r0, min(npairs, r0 + 128)) x k floats are contiguous
+            for (int g4 = 0; g4 < 4; ++g4) {
+                const int tt = tb + g4;
+                if (tt >= nt) break;
+                const int r0 = (t0 + tt) * 128;
+                const int nf = min(128, npairs - r0) * k;
+                const float *src = reinterpret_cast<const float *>(base + (size_t)g4 * slot_bytes);
+                float *dst = M + (pt * (int64_t)npairs + r0) * k;
+                for (int e = tid; e < nf; e += MT_THREADS) dst[e] = src[e];
+            }
+            __syncthreads();
         }
         tc::fence_before();
         __syncthreads();
