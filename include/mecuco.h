@@ -89,11 +89,15 @@ typedef enum {
     MECUCO_OPT_KNN_MARGIN = 0,       /* extra candidates kept per row before the exact re-rank (default 32) */
     MECUCO_OPT_JACOBI_FP64 = 1,      /* -1: by precision (default: 0 for FP32, 1 for BF16_MIXED);
                                         0: FP32 sweeps; 1: FP32 sweeps + one FP64 refinement step;
-                                        2: every sweep in FP64 */
+                                        2: every sweep in FP64; 3: as 1, eigenvalue clusters judged
+                                        relative to each pair.  The adjoint's rotated Gram uses 3
+                                        unless this option is set */
     MECUCO_OPT_JACOBI_MAX_SWEEPS = 2,/* sweep cap of the eigensolver (default 40) */
     MECUCO_OPT_CHUNK_POINTS = 3,     /* points per estimator chunk (0 = automatic) */
     MECUCO_OPT_KNN_QUERY_CHUNK = 4,  /* query rows per kNN launch (0 = automatic) */
-    MECUCO_OPT_PROFILE = 5           /* 1: bracket every kernel with CUDA events (mecuco_get_stage_times) */
+    MECUCO_OPT_PROFILE = 5,          /* 1: bracket every kernel with CUDA events (mecuco_get_stage_times) */
+    MECUCO_OPT_KNN_SPLITS = 6        /* candidate-range splits of the kNN search (0 = automatic, else 1..64;
+                                        capped so that splits * candidate capacity <= 1024) */
 } mecuco_option;
 
 /* Kernel stages, for mecuco_get_stage_times. */
@@ -180,11 +184,14 @@ MECUCO_API mecuco_status mecuco_curvature_range(mecuco_t h, const void *X, mecuc
                                                 int64_t row_end, float *kappa_out, float *lambda_out,
                                                 float *U_out, float *s_out, void *stream);
 
-/* Adjoint of the Fast-mode curvature with the neighbour lists frozen:
- * dX_out = d(sum_i dkappa_i K_i) / dX, where K_i is the curvature of
- * mecuco_curvature for the same (X, idx, var, prec).  K = |f| is differentiated
- * as sign(f) df (0 at f = 0).  Every patch's moments and eigenpairs are
- * recomputed (nothing is kept from the forward call); the per-point adjoint
+/* Adjoint of the Fast-mode curvature (Alg. 1; eqs. tnull, tA, tB, fast_curv)
+ * with the neighbour lists frozen: dX_out = d(sum_i dkappa_i K_i) / dX, where
+ * K_i is the curvature of mecuco_curvature for the same (X, idx, var).
+ * K = |f| is differentiated as sign(f) df (0 at f = 0).  Every patch's moments
+ * and eigenpairs are recomputed (nothing is kept from the forward call) in
+ * FP32 on a rotated copy of the patch (U0^T X_c, U0 the eigenvectors of a
+ * first Gram, which leaves K unchanged and keeps the small eigenvalues
+ * accurate), with FP64 refinement of the eigenpairs; the per-point adjoint
  * runs in k-space (through the derivative of the symmetric eigendecomposition,
  * which is unbounded for coinciding eigenvalues) and is scattered onto the
  * neighbour rows with atomic adds (summation order, hence the last bits, vary
@@ -195,8 +202,7 @@ MECUCO_API mecuco_status mecuco_curvature_range(mecuco_t h, const void *X, mecuc
  *   dX_out  device, N x m floats (row stride m), overwritten */
 MECUCO_API mecuco_status mecuco_curvature_backward(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m,
                                                    int64_t ld, int k, const int32_t *idx, mecuco_variant var,
-                                                   mecuco_precision prec, const float *dkappa, float *dX_out,
-                                                   void *stream);
+                                                   const float *dkappa, float *dX_out, void *stream);
 
 /* The same computation with HOST buffers (pageable or pinned): X_host is
  * copied to the device, the path runs, kappa (and idx if idx_host_out is not

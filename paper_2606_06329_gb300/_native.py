@@ -16,7 +16,8 @@ OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_
 F32, BF16 = 0, 1
 FAST_LITERAL, FAST_HAAR = 0, 1
 PREC_FP32, PREC_BF16_MIXED = 0, 1
-OPT_KNN_MARGIN, OPT_JACOBI_FP64, OPT_JACOBI_MAX_SWEEPS, OPT_CHUNK_POINTS, OPT_KNN_QUERY_CHUNK, OPT_PROFILE = range(6)
+(OPT_KNN_MARGIN, OPT_JACOBI_FP64, OPT_JACOBI_MAX_SWEEPS, OPT_CHUNK_POINTS, OPT_KNN_QUERY_CHUNK, OPT_PROFILE,
+ OPT_KNN_SPLITS) = range(7)
 STAGES = ("rownorm", "knn_search", "knn_rerank", "knn_fallback", "gram", "moments", "jacobi", "estimator", "adjoint")
 
 
@@ -55,7 +56,7 @@ SIGNATURES = {
     "mecuco_knn_range": (_st, [_p, _p, _i32, _i64, _i64, _i64, _i32, _i32, _i32, _i64, _i64, _p, _p, _p]),
     "mecuco_curvature_range": (_st, [_p, _p, _i32, _i64, _i64, _i64, _i32, _p, _i32, _i32, _i32, _i64, _i64,
                                      _p, _p, _p, _p, _p]),
-    "mecuco_curvature_backward": (_st, [_p, _p, _i32, _i64, _i64, _i64, _i32, _p, _i32, _i32, _p, _p, _p]),
+    "mecuco_curvature_backward": (_st, [_p, _p, _i32, _i64, _i64, _i64, _i32, _p, _i32, _p, _p, _p]),
     "mecuco_curvature_host": (_st, [_p, _p, _i32, _i64, _i64, _i64, _i32, _i32, _i32, _i32, _p, _p, _p]),
     "mecuco_knn_noalloc": (_st, [_p, _i32, _i64, _i64, _i64, _i32, _i32, _p, _p, _p]),
     "mecuco_get_last_status": (_st, [_p, _p]),

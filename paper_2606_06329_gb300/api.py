@@ -138,7 +138,7 @@ class Context:
         return kappa
 
     def mecuco_curvature_backward(self, X: torch.Tensor, k: int, idx: torch.Tensor, dkappa: torch.Tensor,
-                                  variant: str = "literal", precision: str = "fp32"):
+                                  variant: str = "literal"):
         """dX = d(sum_i dkappa_i K_i)/dX with the neighbour lists idx frozen (float32, N x m)."""
         _check_x(X, self.device)
         n, m = X.shape
@@ -147,7 +147,7 @@ class Context:
         dk = dkappa.to(device=X.device, dtype=torch.float32).contiguous()
         dX = torch.empty((n, m), dtype=torch.float32, device=X.device)
         st = self.lib.mecuco_curvature_backward(self.handle, _ptr(X), _dtype_code(X), n, m, X.stride(0), int(k),
-                                                _ptr(idx), _VAR[variant], _PREC[precision], _ptr(dk), _ptr(dX),
+                                                _ptr(idx), _VAR[variant], _ptr(dk), _ptr(dX),
                                                 _stream(self.device))
         N.check(st, "mecuco_curvature_backward")
         return dX

@@ -23,8 +23,7 @@ class MeCuCoCurvature(torch.autograd.Function):
     def backward(ctx, dkappa: torch.Tensor):
         X, idx = ctx.saved_tensors
         c = api.context(X.device.index or 0)
-        dX = c.mecuco_curvature_backward(X.detach(), ctx.k, idx, dkappa, variant=ctx.variant,
-                                         precision=ctx.precision)
+        dX = c.mecuco_curvature_backward(X.detach(), ctx.k, idx, dkappa, variant=ctx.variant)
         return dX.to(X.dtype), None, None, None, None
 
 

@@ -62,6 +62,7 @@ struct mecuco_ctx {
     int m3_items_k = -1;
     int32_t *pair_ab = nullptr;
     int pair_ab_k = -1;
+    int knn_splits = 0;
     // options
     int64_t knn_margin = 32;
     int jacobi_fp64 = -1;
@@ -206,6 +207,7 @@ KnnPlan plan_knn(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t 
     // tensor-core search: at least 2 splits, so a wave of the persistent CTAs
     // (one per SM) touches num_sms / 2 query tiles, which stay in L2
     if (p.tc) p.nsplit = std::max(p.nsplit, std::min(2, 1024 / p.kc));
+    if (h->knn_splits > 0) p.nsplit = std::min(h->knn_splits, 1024 / p.kc);
     while (p.nsplit > 1 && (N + p.nsplit - 1) / p.nsplit < p.kc) --p.nsplit;
     return p;
 }
@@ -307,9 +309,9 @@ mecuco_status ensure_pairs(mecuco_t h, int k) {
         h->pair_ab = nullptr;
         h->pair_ab_k = -1;
     }
-    const int n = k * (k + 1) / 2;
+    const int n = moments_tc_rows(k);
     std::vector<int32_t> host((size_t)n);
-    moments_tc_build_pairs(k, host.data());
+    moments_tc_build_rows(k, host.data());
     if (cudaMalloc(&h->pair_ab, sizeof(int32_t) * n) != cudaSuccess) {
         (void)cudaGetLastError();
         h->pair_ab = nullptr;
@@ -405,13 +407,13 @@ mecuco_status run_curvature(mecuco_t h, const void *X, mecuco_dtype dt, int64_t 
                                      var == MECUCO_FAST_HAAR ? b.Q : nullptr, h->ctr, s));
         } else {
             LAUNCH(h, MECUCO_STAGE_GRAM, s,
-                   launch_patch_gram(X, dt, N, m, ld, nb, k, 0, np, b.G, b.R,
+                   launch_patch_gram(X, dt, N, m, ld, nb, k, 0, np, nullptr, b.G, b.R,
                                      var == MECUCO_FAST_HAAR ? b.Q : nullptr, h->ctr, s));
             LAUNCH(h, MECUCO_STAGE_MOMENTS, s,
-                   launch_patch_m3(X, dt, N, m, ld, nb, k, 0, np, b.M, h->m3_items, h->ctr, s));
+                   launch_patch_m3(X, dt, N, m, ld, nb, k, 0, np, nullptr, b.M, h->m3_items, h->ctr, s));
         }
         LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(b.G, k, np, fp64, h->jacobi_max_sweeps, b.sig, Ud, h->ctr, s));
-        if (fp64 == 1) ++h->launches;  // the FP64 refinement is a second kernel
+        if (fp64 == 1 || fp64 == 3) ++h->launches;  // the FP64 refinement is a second kernel
         LAUNCH(h, MECUCO_STAGE_ESTIMATOR, s,
                launch_estimator(b.sig, Ud, b.M, b.R, b.Q, k, m, np, (int)var, kappa_out + p0,
                                 lambda_out ? lambda_out + p0 * k : nullptr, s_out ? s_out + p0 * k : nullptr, h->ctr,
@@ -493,7 +495,7 @@ mecuco_status mecuco_set_option(mecuco_t h, mecuco_option opt, int64_t v) {
             h->knn_margin = v;
             break;
         case MECUCO_OPT_JACOBI_FP64:
-            if (v < -1 || v > 2) return MECUCO_ERR_INVALID_ARG;
+            if (v < -1 || v > 3) return MECUCO_ERR_INVALID_ARG;
             h->jacobi_fp64 = (int)v;
             break;
         case MECUCO_OPT_JACOBI_MAX_SWEEPS:
@@ -511,6 +513,10 @@ mecuco_status mecuco_set_option(mecuco_t h, mecuco_option opt, int64_t v) {
         case MECUCO_OPT_PROFILE:
             if (v < 0 || v > 1) return MECUCO_ERR_INVALID_ARG;
             h->profile = (int)v;
+            break;
+        case MECUCO_OPT_KNN_SPLITS:
+            if (v < 0 || v > 64) return MECUCO_ERR_INVALID_ARG;
+            h->knn_splits = (int)v;
             break;
         default: return MECUCO_ERR_INVALID_ARG;
     }
@@ -561,20 +567,17 @@ mecuco_status mecuco_curvature(mecuco_t h, const void *X, mecuco_dtype dt, int64
 }
 
 mecuco_status mecuco_curvature_backward(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
-                                        int k, const int32_t *idx, mecuco_variant var, mecuco_precision prec,
-                                        const float *dkappa, float *dX_out, void *stream) {
+                                        int k, const int32_t *idx, mecuco_variant var, const float *dkappa,
+                                        float *dX_out, void *stream) {
     mecuco_status st = check_common(h, X, dt, N, m, ld, k, 1);  // idx is given: k <= N
     if (st != MECUCO_OK) return st;
     if (!idx || !dkappa || !dX_out) return MECUCO_ERR_INVALID_ARG;
     if (var != MECUCO_FAST_LITERAL && var != MECUCO_FAST_HAAR) return MECUCO_ERR_INVALID_ARG;
-    if (prec != MECUCO_PREC_FP32 && prec != MECUCO_PREC_BF16_MIXED) return MECUCO_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = begin_call(h, s)) != MECUCO_OK) return st;
     if ((st = ensure_items(h, k)) != MECUCO_OK) return st;
-    const bool tc_moments = prec == MECUCO_PREC_BF16_MIXED;
-    if (tc_moments && (st = ensure_pairs(h, k)) != MECUCO_OK) return st;
-    // per point: forward buffers + dG, dR, dQ + C and dM (k^3 each)
-    const int64_t per_point = m3_pair_floats(k) + 6LL * k * k + 4LL * k + 2LL * k * k * k;
+    // per point: forward buffers + U0 + dG, dR, dQ + C and dM (k^3 each)
+    const int64_t per_point = m3_pair_floats(k) + 7LL * k * k + 4LL * k + 2LL * k * k * k;
     int64_t chunk = h->chunk_points > 0 ? h->chunk_points
                                          : std::max<int64_t>(256, std::min<int64_t>(65536, ((int64_t)2 << 30) /
                                                                                              (per_point * 4)));
@@ -583,6 +586,7 @@ mecuco_status mecuco_curvature_backward(mecuco_t h, const void *X, mecuco_dtype 
     EstBufs b;
     est_scratch(t, chunk, k, &b);
     t.take<float>((size_t)chunk * k * k);
+    t.take<float>((size_t)chunk * k * k);
     t.take<float>((size_t)chunk * k);
     t.take<float>((size_t)chunk * k * k);
     t.take<float>((size_t)chunk * k * k * k);
@@ -590,32 +594,32 @@ mecuco_status mecuco_curvature_backward(mecuco_t h, const void *X, mecuco_dtype 
     if ((st = ensure(h->ws, h->ws_bytes, t.off)) != MECUCO_OK) return st;
     Carver c(h->ws);
     est_scratch(c, chunk, k, &b);
+    float *U0 = c.take<float>((size_t)chunk * k * k);
     float *dG = c.take<float>((size_t)chunk * k * k);
     float *dR = c.take<float>((size_t)chunk * k);
     float *dQ = c.take<float>((size_t)chunk * k * k);
     float *Cb = c.take<float>((size_t)chunk * k * k * k);
     float *dM = c.take<float>((size_t)chunk * k * k * k);
     CK(cudaMemsetAsync(dX_out, 0, sizeof(float) * (size_t)N * m, s));
-    const int fp64 = h->jacobi_fp64 >= 0 ? h->jacobi_fp64 : (prec == MECUCO_PREC_BF16_MIXED ? 1 : 0);
     const bool need_q = var == MECUCO_FAST_HAAR;
+    const int rot_mode = h->jacobi_fp64 >= 0 ? h->jacobi_fp64 : 3;
     for (int64_t p0 = 0; p0 < N; p0 += chunk) {
         const int64_t np = std::min(chunk, N - p0);
         const int32_t *nb = idx + p0 * k;
-        if (tc_moments) {
-            LAUNCH(h, MECUCO_STAGE_MOMENTS, s,
-                   launch_moments_tc(X, dt, N, m, ld, nb, k, np, h->pair_ab, b.M, b.G, b.R, need_q ? b.Q : nullptr,
-                                     h->ctr, s));
-        } else {
-            LAUNCH(h, MECUCO_STAGE_GRAM, s,
-                   launch_patch_gram(X, dt, N, m, ld, nb, k, 0, np, b.G, b.R, need_q ? b.Q : nullptr, h->ctr, s));
-            LAUNCH(h, MECUCO_STAGE_MOMENTS, s,
-                   launch_patch_m3(X, dt, N, m, ld, nb, k, 0, np, b.M, h->m3_items, h->ctr, s));
-        }
-        LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(b.G, k, np, fp64, h->jacobi_max_sweeps, b.sig, b.U, h->ctr, s));
-        if (fp64 == 1) ++h->launches;
+        // U0: eigenvectors of the plain FP32 Gram
+        LAUNCH(h, MECUCO_STAGE_GRAM, s,
+               launch_patch_gram(X, dt, N, m, ld, nb, k, 0, np, nullptr, b.G, b.R, nullptr, h->ctr, s));
+        LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(b.G, k, np, 0, h->jacobi_max_sweeps, b.sig, U0, h->ctr, s));
+        // moments of Z = U0^T X_c and the FP64-refined eigenpairs of its Gram
+        LAUNCH(h, MECUCO_STAGE_GRAM, s,
+               launch_patch_gram(X, dt, N, m, ld, nb, k, 0, np, U0, b.G, b.R, need_q ? b.Q : nullptr, h->ctr, s));
+        LAUNCH(h, MECUCO_STAGE_MOMENTS, s,
+               launch_patch_m3(X, dt, N, m, ld, nb, k, 0, np, U0, b.M, h->m3_items, h->ctr, s));
+        LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(b.G, k, np, rot_mode, h->jacobi_max_sweeps, b.sig, b.U, h->ctr, s));
+        if (rot_mode == 1 || rot_mode == 3) ++h->launches;  // the refinement kernel
         LAUNCH(h, MECUCO_STAGE_ADJOINT, s,
-               launch_adjoint(X, dt, N, m, ld, nb, k, np, (int)var, b.sig, b.U, b.M, b.R, b.Q, dkappa + p0, dG, dR, dQ,
-                              Cb, dM, dX_out, m, s));
+               launch_adjoint(X, dt, N, m, ld, nb, k, np, (int)var, U0, b.sig, b.U, b.M, b.R, b.Q, dkappa + p0, dG, dR,
+                              dQ, Cb, dM, dX_out, m, s));
         ++h->launches;  // two kernels
     }
     return MECUCO_OK;

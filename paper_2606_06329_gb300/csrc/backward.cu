@@ -22,6 +22,16 @@
 // adjoint dX_p = dX_c - 1 (1^T dX_c)/k and a scatter-add into dX rows idx[i,:].
 // Degenerate eigenvalue pairs make F unbounded; the difference is clamped at
 // 2^-40 max|s^2| in magnitude (the derivative there is not defined).
+//
+// Conditioning.  With s_min/s_max = 1e-3 the small eigenpairs of an FP32 Gram
+// carry relative errors near eps (s_max/s_min)^2 = 1e-1 and the s^-3 terms of
+// the adjoint amplify them.  K is invariant under any orthogonal rotation
+// Z = U0^T X_c of the point axis (tau, t_range, t_A, |G_tens|^2 and the Haar
+// sum are sums of squares over j), so the adjoint works on the rotated patch:
+// U0 = eigenvectors of the plain FP32 Gram (held fixed: K does not depend on
+// it), the moments of Z (whose Gram is nearly diagonal, error near
+// eps s_max/s_min) and the eigenpairs of that Gram; the formulas above give
+// dZ, and dX_c = U0 dZ.
 #include <math.h>
 
 #include "common.cuh"
@@ -282,13 +292,15 @@ adjoint_kspace_kernel(const float *__restrict__ sigma, const float *__restrict__
 }
 
 // Patch-space adjoint and scatter: one CTA (256 threads) per point; the patch
-// is re-gathered and centred in 32-column chunks; thread (column c, row
-// group) forms dX_c for its rows, the centring adjoint subtracts the column
-// mean, and the result is atomically added to dX rows idx[pt, :].
+// is re-gathered, centred and rotated (Z = U0^T X_c) in 32-column chunks;
+// thread (column c, row group) forms dZ for its rows, dX_c = U0 dZ, the
+// centring adjoint subtracts the column mean, and the result is atomically
+// added to dX rows idx[pt, :].
 template <typename T>
 __global__ void __launch_bounds__(256)
 adjoint_patch_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, const int32_t *__restrict__ idx, int k,
-                     int variant, const float *__restrict__ dG, const float *__restrict__ dR,
+                     int variant, const float *__restrict__ rot, const float *__restrict__ dG,
+                     const float *__restrict__ dR,
                      const float *__restrict__ dQ, const float *__restrict__ C, float *__restrict__ dX, int64_t ldd) {
     constexpr int CH = 32;
     extern __shared__ float psm[];
@@ -296,6 +308,7 @@ adjoint_patch_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, 
     float(*Ys)[CH + 1] = reinterpret_cast<float(*)[CH + 1]>(psm + 64 * (CH + 1));
     float *sdG = psm + 2 * 64 * (CH + 1);
     float *sdQ = sdG + 64 * 64;
+    float(*Us)[65] = reinterpret_cast<float(*)[65]>(sdQ + 64 * 64);
     __shared__ int rows[64];
     const int tid = threadIdx.x;
     const int64_t pt = blockIdx.x;
@@ -308,6 +321,7 @@ adjoint_patch_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, 
         sdG[e] = dG[pt * (int64_t)kk + e];
         sdQ[e] = (variant == MECUCO_FAST_HAAR) ? dQ[pt * (int64_t)kk + e] : 0.f;
     }
+    load_rotation(rot + pt * (int64_t)kk, k, Us);
     __syncthreads();
     const float *Cp = C + pt * (int64_t)kk * k;
     const float *dRp = dR + pt * k;
@@ -319,12 +333,13 @@ adjoint_patch_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, 
         }
         __syncthreads();
         if (tid < CH) {
-            float s = 0.f;
-            for (int j = 0; j < k; ++j) s += Xs[j][tid];
-            const float mean = s / (float)k;
-            for (int j = 0; j < k; ++j) Xs[j][tid] -= mean;
+            double sd = 0.0;  // centred values rounded once from FP64, as in the rotated moments
+            for (int j = 0; j < k; ++j) sd += (double)Xs[j][tid];
+            const double md = sd / (double)k;
+            for (int j = 0; j < k; ++j) Xs[j][tid] = (float)((double)Xs[j][tid] - md);
         }
         __syncthreads();
+        rotate_rows<CH / 4>(Xs, Us, k, tid >> 6, tid & 63);
         float wa = 0.f, xqx = 0.f;
         if (variant == MECUCO_FAST_HAAR) {
             for (int j = 0; j < k; ++j) wa = fmaf(Xs[j][c], Xs[j][c], wa);
@@ -353,6 +368,7 @@ adjoint_patch_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, 
             Ys[i][c] = v + cq;
         }
         __syncthreads();
+        unrotate_rows<CH / 4>(Ys, Us, k, tid >> 6, tid & 63);
         if (tid < CH && a0 + tid < m) {
             float s = 0.f;
             for (int j = 0; j < k; ++j) s += Ys[j][tid];
@@ -364,9 +380,9 @@ adjoint_patch_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, 
 }
 
 cudaError_t launch_adjoint(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, const int32_t *idx,
-                           int k, int64_t np, int variant, const float *sigma, const float *U, const float *M,
-                           const float *R, const float *Q, const float *gk, float *dG, float *dR, float *dQ, float *C,
-                           float *dMbuf, float *dX, int64_t ldd, cudaStream_t s) {
+                           int k, int64_t np, int variant, const float *rot, const float *sigma, const float *U,
+                           const float *M, const float *R, const float *Q, const float *gk, float *dG, float *dR,
+                           float *dQ, float *C, float *dMbuf, float *dX, int64_t ldd, cudaStream_t s) {
     if (np <= 0) return cudaSuccess;
     if (k > 64) return cudaErrorInvalidValue;
     const size_t smem = BW_SMEM_FLOATS * sizeof(float);
@@ -375,18 +391,18 @@ cudaError_t launch_adjoint(const void *X, mecuco_dtype dt, int64_t N, int64_t m,
     adjoint_kspace_kernel<<<(unsigned)np, 256, smem, s>>>(sigma, U, M, R, Q, gk, k, m, variant, dG, dR, dQ, C, dMbuf);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t psmem = (size_t)(2 * 64 * 33 + 2 * 64 * 64) * sizeof(float);
+    const size_t psmem = (size_t)(2 * 64 * 33 + 2 * 64 * 64 + 64 * 65) * sizeof(float);
     if (dt == MECUCO_BF16) {
         e = cudaFuncSetAttribute(adjoint_patch_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)psmem);
         if (e != cudaSuccess) return e;
-        adjoint_patch_kernel<<<(unsigned)np, 256, psmem, s>>>((const __nv_bfloat16 *)X, N, m, ld, idx, k, variant, dG,
-                                                              dR, dQ, C, dX, ldd);
+        adjoint_patch_kernel<<<(unsigned)np, 256, psmem, s>>>((const __nv_bfloat16 *)X, N, m, ld, idx, k, variant, rot,
+                                                              dG, dR, dQ, C, dX, ldd);
     } else {
         e = cudaFuncSetAttribute(adjoint_patch_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
         if (e != cudaSuccess) return e;
-        adjoint_patch_kernel<<<(unsigned)np, 256, psmem, s>>>((const float *)X, N, m, ld, idx, k, variant, dG, dR, dQ,
-                                                              C, dX, ldd);
+        adjoint_patch_kernel<<<(unsigned)np, 256, psmem, s>>>((const float *)X, N, m, ld, idx, k, variant, rot, dG, dR,
+                                                              dQ, C, dX, ldd);
     }
     return cudaGetLastError();
 }

@@ -92,4 +92,69 @@ __device__ __forceinline__ void atomic_max_u64(unsigned long long *p, unsigned l
     atomicMax(p, v);
 }
 
+// ---- rotation of a patch chunk by a per-point orthogonal k x k matrix U0 ----
+// Us[r][l] = U0[r][l] for r, l < k, zero elsewhere (all 64 x 64 entries).
+__device__ __forceinline__ void load_rotation(const float *__restrict__ u, int k, float (*Us)[65]) {
+    for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+        const int r = e >> 6, l = e & 63;
+        Us[r][l] = (r < k && l < k) ? u[r * k + l] : 0.f;
+    }
+}
+
+// In-place Z = U0^T Xs for a row-major chunk Xs[row][column] (rows >= k stay
+// zero).  256 threads: thread (l = tid & 63, column group cg = tid >> 6) forms
+// row l of Z for NC columns cg*NC.. into registers; a barrier separates the
+// reads from the writes.  Called by all threads, between barriers.
+template <int NC, int LDX>
+__device__ __forceinline__ void rotate_rows(float (*Xs)[LDX], const float (*Us)[65], int k, int cg, int l) {
+    float z[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) z[c] = 0.f;
+    for (int r = 0; r < k; ++r) {
+        const float u = Us[r][l];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) z[c] = fmaf(u, Xs[r][cg * NC + c], z[c]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < NC; ++c) Xs[l][cg * NC + c] = z[c];
+    __syncthreads();
+}
+
+// The same for a column-major chunk Xs[column][row].
+template <int NC, int LDX>
+__device__ __forceinline__ void rotate_cols(float (*Xs)[LDX], const float (*Us)[65], int k, int cg, int l) {
+    float z[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) z[c] = 0.f;
+    for (int r = 0; r < k; ++r) {
+        const float u = Us[r][l];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) z[c] = fmaf(u, Xs[cg * NC + c][r], z[c]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < NC; ++c) Xs[cg * NC + c][l] = z[c];
+    __syncthreads();
+}
+
+// In-place Y = U0 Y for a row-major chunk (the inverse rotation): thread
+// (j = tid & 63, cg = tid >> 6) forms row j for NC columns; rows >= k of Y are
+// never read.
+template <int NC, int LDX>
+__device__ __forceinline__ void unrotate_rows(float (*Ys)[LDX], const float (*Us)[65], int k, int cg, int j) {
+    float z[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) z[c] = 0.f;
+    for (int l = 0; l < k; ++l) {
+        const float u = Us[j][l];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) z[c] = fmaf(u, Ys[l][cg * NC + c], z[c]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < NC; ++c) Ys[j][cg * NC + c] = z[c];
+    __syncthreads();
+}
+
 }  // namespace mecuco

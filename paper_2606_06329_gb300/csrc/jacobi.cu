@@ -173,13 +173,17 @@ jacobi_kernel(const float *__restrict__ G, int k, int64_t np, int max_sweeps, fl
 // From FP32-accurate X (~2^-23) one step gives eigenvectors accurate to the
 // square of that, i.e. to FP64 level, and re-orthogonalises them.  delta =
 // 2^-18 max|lam| treats eigenvalues closer than the FP32 estimate can resolve
-// as a cluster (only orthogonalised).  One CTA (RT threads) per patch; results
+// as a cluster (only orthogonalised).  With rel != 0 the cluster test is
+// relative to the pair itself, |lam_i - lam_j| <= 2^-18 max(|lam_i|, |lam_j|):
+// for a Gram whose FP32 eigenpairs are accurate to a few ulps relative to
+// each eigenvalue (a nearly diagonal Gram, as in the adjoint's rotated basis),
+// where the absolute test would lump all small eigenvalues into one cluster.  One CTA (RT threads) per patch; results
 // re-sorted descending.
 // ---------------------------------------------------------------------------
 constexpr int RT = 256;
 
 __global__ void __launch_bounds__(RT)
-jacobi_refine64_kernel(const float *__restrict__ G, int k, float *__restrict__ sigma, float *__restrict__ U) {
+jacobi_refine64_kernel(const float *__restrict__ G, int k, int rel, float *__restrict__ sigma, float *__restrict__ U) {
     extern __shared__ __align__(16) unsigned char rsm[];
     const int ld = k + 1;
     double *A = reinterpret_cast<double *>(rsm);  // [k][ld]
@@ -237,7 +241,8 @@ jacobi_refine64_kernel(const float *__restrict__ G, int k, float *__restrict__ s
         const double rij = 0.5 * (Rm[i * ld + j] + Rm[j * ld + i]);
         const double sij = 0.5 * (S[i * ld + j] + S[j * ld + i]);
         double v;
-        if (i == j || fabs(lam[i] - lam[j]) <= delta) v = 0.5 * rij;
+        const double dij = rel ? 3.814697265625e-06 * fmax(fabs(lam[i]), fabs(lam[j])) : delta;
+        if (i == j || fabs(lam[i] - lam[j]) <= dij) v = 0.5 * rij;
         else v = (sij + lam[j] * rij) / (lam[j] - lam[i]);
         ev[ne] = v;
     }
@@ -276,14 +281,14 @@ cudaError_t launch_jacobi(const float *G, int k, int64_t np, int fp64, int max_s
     if (np <= 0) return cudaSuccess;
     if (k > 64) return cudaErrorInvalidValue;
     cudaError_t e;
-    if (fp64 == 1) {
-        // FP32 sweeps, then one FP64 refinement step
+    if (fp64 == 1 || fp64 == 3) {
+        // FP32 sweeps, then one FP64 refinement step (3: relative cluster test)
         e = launch_jacobi(G, k, np, 0, max_sweeps, sigma, U, ctr, s);
         if (e != cudaSuccess) return e;
         const size_t rs = refine64_smem_bytes(k);
         e = cudaFuncSetAttribute(jacobi_refine64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs);
         if (e != cudaSuccess) return e;
-        jacobi_refine64_kernel<<<(unsigned)np, RT, rs, s>>>(G, k, sigma, U);
+        jacobi_refine64_kernel<<<(unsigned)np, RT, rs, s>>>(G, k, fp64 == 3, sigma, U);
         return cudaGetLastError();
     }
     const size_t smem = jacobi_smem_bytes(k, fp64);

@@ -63,17 +63,18 @@ cudaError_t launch_knn_fallback(const void *X, mecuco_dtype dt, int64_t N, int64
 //   R   np x k       X_c 1_m
 //   Q   np x k x k   X_c diag(c) X_c^T, c_a = sum_j X_c[j,a]^2   (nullable)
 // Neighbour indices outside [0, N) are read as row 0 and raise
-// MECUCO_ERR_INVALID_ARG in the device status word.
+// MECUCO_ERR_INVALID_ARG in the device status word.  With rot (np x k x k,
+// orthogonal U0 per point, nullable) the moments are those of U0^T X_c.
 cudaError_t launch_patch_gram(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
-                              const int32_t *idx, int k, int64_t p0, int64_t np, float *G,
-                              float *R, float *Q, DevCounters *ctr, cudaStream_t s);
+                              const int32_t *idx, int k, int64_t p0, int64_t np, const float *rot,
+                              float *G, float *R, float *Q, DevCounters *ctr, cudaStream_t s);
 
 // Third moments M[j,r,t] = sum_a X_c[j,a] X_c[r,a] X_c[t,a], stored pair-major:
 // D[pair(a,b)][c] = M[a][b][c] for a <= b, every c; np x m3_pair_floats(k) floats.
 // `items` is the work-item list built by m3_build_items.
 cudaError_t launch_patch_m3(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
-                            const int32_t *idx, int k, int64_t p0, int64_t np, float *M,
-                            const int32_t *items, DevCounters *ctr, cudaStream_t s);
+                            const int32_t *idx, int k, int64_t p0, int64_t np, const float *rot,
+                            float *M, const int32_t *items, DevCounters *ctr, cudaStream_t s);
 
 __host__ __device__ inline int pair_index(int a, int b, int k) { return a * k - (a * (a - 1)) / 2 + (b - a); }
 inline int64_t m3_pair_floats(int k) { return (int64_t)k * (k + 1) / 2 * k; }
@@ -85,21 +86,24 @@ __device__ inline int64_t m3_pair_floats_d(int k) { return (int64_t)k * (k + 1) 
 int m3_items(int k);
 void m3_build_items(int k, int32_t *items /* m3_items(k) */);
 
-// BF16-mixed form: G, R, Q and the pair-major M of each patch from one
-// tensor-core GEMM per 128-pair tile (BF16 operands, FP32 accumulation).
-// pair_ab[p] = a | b << 16 for pair index p (built by moments_tc_build_pairs);
-// idx points at the chunk's first neighbour row; Q may be NULL.
+// BF16-mixed form: G, R, Q and the pair-major M of each patch from
+// tensor-core GEMMs over 128-row tiles of row products (BF16 operands, FP32
+// accumulation).  rowtab holds moments_tc_rows(k) row codes built by
+// moments_tc_build_rows; idx points at the chunk's first neighbour row; Q may
+// be NULL.
 cudaError_t launch_moments_tc(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, const int32_t *idx,
-                              int k, int64_t np, const int32_t *pair_ab, float *M, float *G, float *R, float *Q,
+                              int k, int64_t np, const int32_t *rowtab, float *M, float *G, float *R, float *Q,
                               DevCounters *ctr, cudaStream_t s);
-void moments_tc_build_pairs(int k, int32_t *pair_ab /* k(k+1)/2 */);
-size_t moments_tc_smem_bytes();
+int moments_tc_rows(int k);
+void moments_tc_build_rows(int k, int32_t *codes /* moments_tc_rows(k) */);
+size_t moments_tc_smem_bytes(int k);
 
 // ---- Step 3: k x k eigensolve -----------------------------------------------
 // Parallel-order two-sided Jacobi, one CTA per patch.  G: np x k x k.
 // Outputs sigma (np x k, descending) and U (np x k x k, column l = eigenvector).
 // fp64: 0 = FP32 sweeps; 1 = FP32 sweeps then one FP64 refinement step;
-// 2 = every sweep in FP64.
+// 2 = every sweep in FP64; 3 = as 1 with the refinement's cluster test
+// relative to each eigenvalue pair (for nearly diagonal Grams).
 cudaError_t launch_jacobi(const float *G, int k, int64_t np, int fp64, int max_sweeps,
                           float *sigma, float *U, DevCounters *ctr, cudaStream_t s);
 
@@ -114,12 +118,13 @@ cudaError_t launch_estimator(const float *sigma, const float *U, const float *M,
 
 // ---- adjoint ---------------------------------------------------------------
 // d(sum_i gk_i K_i)/dX for the points of one chunk (idx offset to the chunk),
-// accumulated into dX (row stride ldd) with atomics.  Inputs are the forward's
-// sigma/U/M/R/Q of the chunk; dG, dR, dQ (np x k x k, k, k x k), C and dMbuf
-// (np x k^3 each) are scratch.
+// accumulated into dX (row stride ldd) with atomics.  Inputs are sigma/U (the
+// eigenpairs of the rotated Gram) and M/R/Q of the rotated patch Z = U0^T X_c
+// (rot = U0 per point, np x k x k); dG, dR, dQ (np x k x k, k, k x k), C and
+// dMbuf (np x k^3 each) are scratch.
 cudaError_t launch_adjoint(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, const int32_t *idx,
-                           int k, int64_t np, int variant, const float *sigma, const float *U, const float *M,
-                           const float *R, const float *Q, const float *gk, float *dG, float *dR, float *dQ, float *C,
-                           float *dMbuf, float *dX, int64_t ldd, cudaStream_t s);
+                           int k, int64_t np, int variant, const float *rot, const float *sigma, const float *U,
+                           const float *M, const float *R, const float *Q, const float *gk, float *dG, float *dR,
+                           float *dQ, float *C, float *dMbuf, float *dX, int64_t ldd, cudaStream_t s);
 
 }  // namespace mecuco

@@ -9,6 +9,15 @@
 // c_a = sum_j X_c[j,a]^2.  Centring is per column (x_ja - mean_j x_ja), so both
 // kernels stream the patch through shared memory in column chunks, centre each
 // chunk and accumulate, reading every neighbour row once per kernel.
+//
+// Both kernels optionally take a per-point orthogonal k x k matrix U0 (row r,
+// column l) and then accumulate the moments of Z = U0^T X_c instead of X_c.
+// Every estimator term is invariant under such a rotation of the point axis
+// (tau, t_range, t_A, |G_tens|^2 and the Haar sum are sums of squares over j),
+// and with U0 the eigenvectors of a first Gram the rotated Gram is nearly
+// diagonal, so its small eigenvalues come out with small relative error in
+// FP32 (error of order eps s_max/s_min instead of eps (s_max/s_min)^2).  The
+// adjoint uses this.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -30,18 +39,20 @@ __device__ __forceinline__ int checked_row(int r, int64_t N, DevCounters *ctr) {
 // ---------------------------------------------------------------------------
 constexpr int GCH = 64;
 
-template <typename T>
+template <typename T, bool ROT>
 __global__ void __launch_bounds__(256)
 patch_gram_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, const int32_t *__restrict__ idx,
-                  int k, int64_t p0, float *__restrict__ G, float *__restrict__ R, float *__restrict__ Q,
-                  DevCounters *ctr) {
+                  int k, int64_t p0, const float *__restrict__ rot, float *__restrict__ G, float *__restrict__ R,
+                  float *__restrict__ Q, DevCounters *ctr) {
     __shared__ float Xs[64][GCH + 1];
+    __shared__ float Us[ROT ? 64 : 1][65];
     __shared__ float cw[GCH];
     __shared__ int rows[64];
     const int tid = threadIdx.x;
     const int64_t p = p0 + blockIdx.x;
     if (tid < k) rows[tid] = checked_row(idx[p * k + tid], N, ctr);
     if (tid >= k && tid < 64) rows[tid] = -1;
+    if (ROT) load_rotation(rot + (p - p0) * (int64_t)k * k, k, Us);
     const int bi = tid >> 4, bj = tid & 15;
     const bool active = (4 * bi < k) && (4 * bj < k);
     float g[4][4], qq[4][4];
@@ -60,18 +71,31 @@ patch_gram_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
         }
         __syncthreads();
         if (tid < GCH) {
-            float s = 0.f;
-            for (int j = 0; j < k; ++j) s += Xs[j][tid];
-            float mean = s / (float)k;
             float w = 0.f;
-            for (int j = 0; j < k; ++j) {
-                float v = Xs[j][tid] - mean;
-                Xs[j][tid] = v;
-                w = fmaf(v, v, w);
+            if (ROT) {
+                // centred values rounded once from FP64 (the rotated form feeds the adjoint)
+                double sd = 0.0;
+                for (int j = 0; j < k; ++j) sd += (double)Xs[j][tid];
+                const double md = sd / (double)k;
+                for (int j = 0; j < k; ++j) {
+                    const float v = (float)((double)Xs[j][tid] - md);
+                    Xs[j][tid] = v;
+                    w = fmaf(v, v, w);
+                }
+            } else {
+                float s = 0.f;
+                for (int j = 0; j < k; ++j) s += Xs[j][tid];
+                float mean = s / (float)k;
+                for (int j = 0; j < k; ++j) {
+                    float v = Xs[j][tid] - mean;
+                    Xs[j][tid] = v;
+                    w = fmaf(v, v, w);
+                }
             }
             cw[tid] = w;
         }
         __syncthreads();
+        if (ROT) rotate_rows<GCH / 4>(Xs, Us, k, tid >> 6, tid & 63);
         if (active) {
 #pragma unroll 4
             for (int c = 0; c < GCH; ++c) {
@@ -111,14 +135,21 @@ patch_gram_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
 }
 
 cudaError_t launch_patch_gram(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
-                              const int32_t *idx, int k, int64_t p0, int64_t np, float *G,
-                              float *R, float *Q, DevCounters *ctr, cudaStream_t s) {
+                              const int32_t *idx, int k, int64_t p0, int64_t np, const float *rot,
+                              float *G, float *R, float *Q, DevCounters *ctr, cudaStream_t s) {
     if (np <= 0) return cudaSuccess;
     if (k > 64) return cudaErrorInvalidValue;
-    if (dt == MECUCO_BF16)
-        patch_gram_kernel<<<(unsigned)np, 256, 0, s>>>((const __nv_bfloat16 *)X, N, m, ld, idx, k, p0, G, R, Q, ctr);
+    const bool bf = dt == MECUCO_BF16;
+    const __nv_bfloat16 *Xb = (const __nv_bfloat16 *)X;
+    const float *Xf = (const float *)X;
+    if (bf && rot)
+        patch_gram_kernel<__nv_bfloat16, true><<<(unsigned)np, 256, 0, s>>>(Xb, N, m, ld, idx, k, p0, rot, G, R, Q, ctr);
+    else if (bf)
+        patch_gram_kernel<__nv_bfloat16, false><<<(unsigned)np, 256, 0, s>>>(Xb, N, m, ld, idx, k, p0, rot, G, R, Q, ctr);
+    else if (rot)
+        patch_gram_kernel<float, true><<<(unsigned)np, 256, 0, s>>>(Xf, N, m, ld, idx, k, p0, rot, G, R, Q, ctr);
     else
-        patch_gram_kernel<<<(unsigned)np, 256, 0, s>>>((const float *)X, N, m, ld, idx, k, p0, G, R, Q, ctr);
+        patch_gram_kernel<float, false><<<(unsigned)np, 256, 0, s>>>(Xf, N, m, ld, idx, k, p0, rot, G, R, Q, ctr);
     return cudaGetLastError();
 }
 
@@ -155,18 +186,20 @@ void m3_build_items(int k, int32_t *items) {
 
 constexpr int MCH = 32;
 
-template <typename T>
+template <typename T, bool ROT>
 __global__ void __launch_bounds__(256)
 patch_m3_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, const int32_t *__restrict__ idx,
-                int k, int64_t p0, float *__restrict__ M, const int32_t *__restrict__ items, int nitems,
-                DevCounters *ctr) {
+                int k, int64_t p0, const float *__restrict__ rot, float *__restrict__ M,
+                const int32_t *__restrict__ items, int nitems, DevCounters *ctr) {
     __shared__ __align__(16) float Xs[MCH][64];
+    __shared__ float Us[ROT ? 64 : 1][65];
     __shared__ int rows[64];
     const int tid = threadIdx.x;
     const int64_t p = p0 + blockIdx.x;
     const int item = blockIdx.y * 256 + tid;
     const int kp = ((k + 7) / 8) * 8;
     if (tid < 64) rows[tid] = (tid < k) ? checked_row(idx[p * k + tid], N, ctr) : -1;
+    if (ROT) load_rotation(rot + (p - p0) * (int64_t)k * k, k, Us);
     int j = 0, rb = 0, tb = 0;
     const bool active = item < nitems;
     if (active) {
@@ -189,12 +222,20 @@ patch_m3_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, const
         }
         __syncthreads();
         if (tid < MCH) {
-            float s = 0.f;
-            for (int jj = 0; jj < k; ++jj) s += Xs[tid][jj];
-            float mean = s / (float)k;
-            for (int jj = 0; jj < k; ++jj) Xs[tid][jj] -= mean;
+            if (ROT) {
+                double sd = 0.0;
+                for (int jj = 0; jj < k; ++jj) sd += (double)Xs[tid][jj];
+                const double md = sd / (double)k;
+                for (int jj = 0; jj < k; ++jj) Xs[tid][jj] = (float)((double)Xs[tid][jj] - md);
+            } else {
+                float s = 0.f;
+                for (int jj = 0; jj < k; ++jj) s += Xs[tid][jj];
+                float mean = s / (float)k;
+                for (int jj = 0; jj < k; ++jj) Xs[tid][jj] -= mean;
+            }
         }
         __syncthreads();
+        if (ROT) rotate_cols<MCH / 4>(Xs, Us, k, tid >> 6, tid & 63);
         if (active) {
             for (int c = 0; c < MCH; ++c) {
                 const float4 *col = reinterpret_cast<const float4 *>(&Xs[c][0]);
@@ -231,16 +272,23 @@ patch_m3_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, const
 }
 
 cudaError_t launch_patch_m3(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
-                            const int32_t *idx, int k, int64_t p0, int64_t np, float *M,
-                            const int32_t *items, DevCounters *ctr, cudaStream_t s) {
+                            const int32_t *idx, int k, int64_t p0, int64_t np, const float *rot,
+                            float *M, const int32_t *items, DevCounters *ctr, cudaStream_t s) {
     if (np <= 0) return cudaSuccess;
     if (k > 64) return cudaErrorInvalidValue;
     int nitems = m3_items(k);
     dim3 grid((unsigned)np, (unsigned)((nitems + 255) / 256));  // (point, item group)
-    if (dt == MECUCO_BF16)
-        patch_m3_kernel<<<grid, 256, 0, s>>>((const __nv_bfloat16 *)X, N, m, ld, idx, k, p0, M, items, nitems, ctr);
+    const bool bf = dt == MECUCO_BF16;
+    const __nv_bfloat16 *Xb = (const __nv_bfloat16 *)X;
+    const float *Xf = (const float *)X;
+    if (bf && rot)
+        patch_m3_kernel<__nv_bfloat16, true><<<grid, 256, 0, s>>>(Xb, N, m, ld, idx, k, p0, rot, M, items, nitems, ctr);
+    else if (bf)
+        patch_m3_kernel<__nv_bfloat16, false><<<grid, 256, 0, s>>>(Xb, N, m, ld, idx, k, p0, rot, M, items, nitems, ctr);
+    else if (rot)
+        patch_m3_kernel<float, true><<<grid, 256, 0, s>>>(Xf, N, m, ld, idx, k, p0, rot, M, items, nitems, ctr);
     else
-        patch_m3_kernel<<<grid, 256, 0, s>>>((const float *)X, N, m, ld, idx, k, p0, M, items, nitems, ctr);
+        patch_m3_kernel<float, false><<<grid, 256, 0, s>>>(Xf, N, m, ld, idx, k, p0, rot, M, items, nitems, ctr);
     return cudaGetLastError();
 }
 

@@ -2,28 +2,37 @@
 // patch and produce, on the 5th-generation tensor cores, every moment the
 // estimator needs:
 //   M[a][b][t] = sum_c X_c[a,c] X_c[b,c] X_c[t,c]   (pairs a <= b, all t)
-//   G[a][b]    = sum_c X_c[a,c] X_c[b,c]             (= X_c X_c^T, eq. svd_cov)
-//   Q[a][b]    = sum_c w_c X_c[a,c] X_c[b,c],  w_c = sum_j X_c[j,c]^2 (Haar term)
-//   R[a]       = sum_c X_c[a,c]
-// as one GEMM per 128-pair tile: D = Z B^T with
-//   Z[(a,b), c] = X_c[a,c] X_c[b,c]  (rows in pair order, pair(a,b) = a k - a(a-1)/2 + b - a)
-//   B = [X_c ; 1 ; w]                  (k + 2 rows, zero-padded to N = 16 ceil((k+2)/16))
-// so D[(a,b), t] = M[a][b][t], D[(a,b), k] = G[a][b], D[(a,b), k+1] = Q[a][b].
+//   G[a][t]    = sum_c X_c[a,c] X_c[t,c]             (= X_c X_c^T, eq. svd_cov)
+//   Q[a][t]    = sum_c w_c X_c[a,c] X_c[t,c],  w_c = sum_j X_c[j,c]^2 (Haar term)
+//   R[a]       = sum_c X_c[a,c]                      (CUDA cores, while centring)
+// as GEMMs D = Z B^T with B = X_c (N = 16 ceil(k/16) rows, zero-padded) and Z
+// the row products Z[r, c] = X_c[a_r, c] y_r[c], y_r = X_c[b_r, :] (an M row),
+// the all-ones vector (a G row) or w (a Q row).
 //
-// One CTA (512 threads) per patch.  The columns of the patch are streamed in
-// 64-column chunks: the CUDA cores gather the k neighbour rows (the next
-// chunk's loads are issued before the current chunk is processed, so their
-// latency hides behind it), centre each column (x - mean over the k rows) in
-// FP32, accumulate R, form w, and write Z and B as BF16 into a 128-byte-
-// swizzled K-major operand buffer (two buffers: building chunk i+1 overlaps
-// the MMAs of chunk i); one thread issues tcgen05.mma (M=128, N, K=16) for
-// every tile of the current pass into TMEM (FP32 accumulation).  TMEM holds up
-// to TPP tiles, so the tiles are covered in passes over the columns (re-reading
-// the patch from L2).  After a pass the warps drain TMEM through shared memory
-// so each tile's 128 pair rows (contiguous in the pair-major M buffer) leave as
-// coalesced stores.  Every mbarrier wait is bounded (MECUCO_ERR_TIMEOUT, no
-// trap).
+// Row order.  The pairs a <= b are grouped in 8 x 8 blocks (a-block <= b-block;
+// a 32-row quarter of a block holds 4 values of a and 8 of b, so a warp reads
+// few distinct rows of the patch); the rows a > b that the diagonal blocks
+// leave free carry the G and Q rows.  Two blocks form a 128-row MMA tile.
+// The host builds the table of row codes once per k.
+//
+// One CTA per patch: 16 "former" warps and one MMA warp.  The columns of the
+// patch are streamed in 64-column chunks.  The formers gather the k neighbour
+// rows (the next chunk's loads are in flight while the current chunk is
+// processed), centre each column in FP32, accumulate R and w, and keep the
+// chunk as packed BF16 pairs in shared memory and as the K-major, 128-byte-
+// swizzled B operand.  For every tile of the current pass each former thread
+// forms 16 products of its tile row (HMUL2 on BF16 pairs) and writes them with
+// tcgen05.st straight into a TMEM slot holding the A operand (four slots,
+// 64 K-columns each); the MMA warp issues tcgen05.mma with A in TMEM, B in
+// shared memory and FP32 accumulators in TMEM, and releases each slot with
+// tcgen05.commit.  TMEM holds the accumulators of up to 384/N tiles, so the
+// tiles are covered in passes over the columns (the patch is re-read from L2).
+// After a pass the formers read the accumulators back (tcgen05.ld) and store
+// each row to its destination.  Every wait is bounded (MECUCO_ERR_TIMEOUT,
+// no trap); the MMA warp waits for its last MMAs before TMEM is freed.
 #include <math.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -32,16 +41,20 @@
 namespace mecuco {
 
 namespace {
-constexpr int MT_THREADS = 512;
-constexpr int MT_CH = 64;                  // columns per chunk (one 128-byte swizzle row of BF16)
-constexpr int MT_TPP = 5;                  // tiles per pass (shared-memory bound)
-constexpr int MT_TILE_BYTES = 128 * 128;   // 128 rows x 128 bytes
-constexpr int MT_BMAX_ROWS = 80;           // k <= 64 -> N <= 80
-constexpr int MT_B_BYTES = MT_BMAX_ROWS * 128;
-constexpr int MT_BUF_BYTES = MT_TPP * MT_TILE_BYTES + MT_B_BYTES;
-constexpr int MT_XS_LD = 68;               // FP32 staging row stride (floats)
-constexpr int MT_XS_FLOATS = 64 * MT_XS_LD;
+constexpr int MT_FORMERS = 512;                        // 16 warps
+constexpr int MT_THREADS = MT_FORMERS + 32;            // + the MMA warp
+constexpr int MT_CH = 64;                              // columns per chunk
+constexpr int MT_SLOTS = 4;                            // A slots in TMEM
+constexpr int MT_SLOT_COLS = MT_CH / 2;                // 32-bit TMEM columns per slot
+constexpr int MT_D_COLS = 512 - MT_SLOTS * MT_SLOT_COLS;  // accumulator columns (384)
+constexpr int MT_XS_LD = 68;                           // FP32 staging row stride (floats)
+constexpr int MT_XP_LD = 36;                           // packed BF16x2 row stride (words)
+constexpr int MT_ROW_ONES = 64, MT_ROW_W = 65, MT_ROW_ZERO = 66, MT_XP_ROWS = 67;
+constexpr int MT_B_BYTES = 64 * 128;                   // B operand: up to 64 rows x 128 bytes
+constexpr int MT_MAX_ROWS = 2304;                      // row table bound (k = 64)
 constexpr long long MT_WAIT = 1000000000LL;
+
+enum : int { ROW_NONE = 0, ROW_PAIR = 1, ROW_G = 2, ROW_Q = 3 };
 
 __device__ __forceinline__ uint32_t sw128(int row, int unit16) {
     // byte offset of 16-byte unit `unit16` (0..7) of `row` in a 128B-swizzled K-major tile
@@ -104,25 +117,58 @@ struct Unit8<float> {
 };
 }  // namespace
 
-__host__ __device__ inline int moments_tc_n(int k) { return ((k + 2 + 15) / 16) * 16; }
+__host__ __device__ inline int moments_tc_n(int k) { return k <= 16 ? 16 : ((k + 15) / 16) * 16; }
 
-size_t moments_tc_smem_bytes() {
-    return 1024 + 2 * (size_t)MT_BUF_BYTES + 2 * (size_t)MT_XS_FLOATS * sizeof(float) + 64 * sizeof(float) +
-           MT_CH * sizeof(float) + 8 * 64 * sizeof(float) + 64;
+// Rows of the row table: the 8 x 8 pair blocks, or more if their free rows
+// cannot hold the 2k G and Q rows, rounded up to whole 128-row tiles.
+int moments_tc_rows(int k) {
+    const int kb = (k + 7) / 8;
+    const int rows = std::max(kb * (kb + 1) / 2 * 64, k * (k + 1) / 2 + 2 * k);
+    return (rows + 127) / 128 * 128;
+}
+
+void moments_tc_build_rows(int k, int32_t *codes) {
+    const int kb = (k + 7) / 8;
+    const int nrows = moments_tc_rows(k);
+    auto code = [](int a, int b, int kind) { return (int32_t)(a | (b << 8) | (kind << 16)); };
+    int n = 0;
+    for (int A = 0; A < kb; ++A)
+        for (int B = A; B < kb; ++B)
+            for (int r = 0; r < 64; ++r) {
+                const int h = r / 32, L = r % 32;
+                const int a = 8 * A + 4 * h + L / 8, b = 8 * B + L % 8;
+                const bool valid = a < k && b < k && (A < B || a <= b);
+                codes[n++] = valid ? code(a, b, ROW_PAIR) : code(MT_ROW_ZERO, MT_ROW_ZERO, ROW_NONE);
+            }
+    for (; n < nrows; ++n) codes[n] = code(MT_ROW_ZERO, MT_ROW_ZERO, ROW_NONE);
+    // G and Q rows go into free slots
+    int next = 0;
+    for (int which = 0; which < 2; ++which)
+        for (int a = 0; a < k; ++a) {
+            while (((codes[next] >> 16) & 3) != ROW_NONE) ++next;
+            codes[next] = which == 0 ? code(a, MT_ROW_ONES, ROW_G) : code(a, MT_ROW_W, ROW_Q);
+        }
+}
+
+size_t moments_tc_smem_bytes(int k) {
+    return 1024 + 2 * (size_t)MT_B_BYTES + 2 * (size_t)MT_XP_ROWS * MT_XP_LD * 4 + 64 * (size_t)MT_XS_LD * 4 +
+           8 * 64 * 4 + 64 * 4 + (size_t)moments_tc_rows(k) * 4;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(MT_THREADS, 1)
 moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, const int32_t *__restrict__ idx, int k,
-                  const int32_t *__restrict__ pair_ab, float *__restrict__ M, float *__restrict__ G,
+                  const int32_t *__restrict__ rowtab, int nrows, float *__restrict__ M, float *__restrict__ G,
                   float *__restrict__ R, float *__restrict__ Q, DevCounters *ctr) {
     extern __shared__ __align__(1024) uint8_t msm_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(msm_raw) + 1023) & ~(uintptr_t)1023);
-    float *Xs0 = reinterpret_cast<float *>(base + 2 * MT_BUF_BYTES);  // two [64][MT_XS_LD] staging chunks
-    float *Rs = Xs0 + 2 * MT_XS_FLOATS;                                // [64]
-    float *Ws = Rs + 64;                                               // [MT_CH] column weights w_c
-    float *Part = Ws + MT_CH;                                          // [8][64] centring partials
-    __shared__ uint64_t mma_done[2];
+    uint8_t *Bop0 = base;                                                       // 2 x B operand
+    uint32_t *Xp0 = reinterpret_cast<uint32_t *>(base + 2 * MT_B_BYTES);        // 2 x [67][36] packed pairs
+    float *Xs = reinterpret_cast<float *>(Xp0 + 2 * MT_XP_ROWS * MT_XP_LD);     // [64][68] FP32 staging
+    float *Part = Xs + 64 * MT_XS_LD;                                           // [8][64]
+    float *Rs = Part + 8 * 64;                                                  // [64]
+    int32_t *codes = reinterpret_cast<int32_t *>(Rs + 64);                      // [nrows]
+    __shared__ uint64_t slot_full[MT_SLOTS], slot_empty[MT_SLOTS], chunk_done[2], pass_done;
     __shared__ uint32_t tmem_slot;
     __shared__ int rows[64];
     __shared__ int abort_flag, never;
@@ -130,9 +176,10 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t pt = blockIdx.x;
     const int npairs = k * (k + 1) / 2;
-    const int ntiles = (npairs + 127) / 128;
+    const int ntiles = nrows / 128;
     const int Nb = moments_tc_n(k);
-    const int tpp = min(MT_TPP, 512 / Nb);
+    const int tpp = min(ntiles, MT_D_COLS / Nb);
+    const int npass = (ntiles + tpp - 1) / tpp;
     const int nchunks = (int)((m + MT_CH - 1) / MT_CH);
     const uint32_t idesc = tc::idesc_bf16_f32(128, Nb);
     const bool vec = (ld % 8 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
@@ -146,9 +193,21 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
         rows[tid] = r;
         Rs[tid] = 0.f;
     }
+    for (int e = tid; e < nrows; e += MT_THREADS) codes[e] = __ldg(rowtab + e);
+    // constant rows of both packed buffers: ones (BF16 1.0 pairs) and zeros
+    for (int e = tid; e < 2 * MT_XP_LD; e += MT_THREADS) {
+        uint32_t *xp = Xp0 + (e / MT_XP_LD) * MT_XP_ROWS * MT_XP_LD;
+        xp[MT_ROW_ONES * MT_XP_LD + e % MT_XP_LD] = 0x3f803f80u;
+        xp[MT_ROW_ZERO * MT_XP_LD + e % MT_XP_LD] = 0u;
+    }
     if (tid == 0) {
-        tc::mbar_init(tc::smem_u32(&mma_done[0]), 1);
-        tc::mbar_init(tc::smem_u32(&mma_done[1]), 1);
+        for (int s = 0; s < MT_SLOTS; ++s) {
+            tc::mbar_init(tc::smem_u32(&slot_full[s]), MT_FORMERS / 32);
+            tc::mbar_init(tc::smem_u32(&slot_empty[s]), 1);
+        }
+        tc::mbar_init(tc::smem_u32(&chunk_done[0]), 1);
+        tc::mbar_init(tc::smem_u32(&chunk_done[1]), 1);
+        tc::mbar_init(tc::smem_u32(&pass_done), 1);
         abort_flag = (*(volatile unsigned *)&ctr->status & DEV_TIMEOUT) ? 1 : 0;
         never = 0;
         tc::fence_mbar_init();
@@ -162,205 +221,195 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
     tc::fence_after();
     const uint32_t tmem = tmem_slot;
     volatile int *abortp = &abort_flag;
-    uint32_t commits0 = 0, commits1 = 0;  // commits issued on mma_done[0] / [1] (uniform across threads)
+    auto fail = [&]() {
+        atomicOr(&ctr->status, (unsigned)DEV_TIMEOUT);
+        abort_flag = 1;
+    };
 
-    // gather unit of this thread: row gj, 8-column group gg (64 rows x 8 groups = 512 units)
-    const int gj = tid >> 3, gg = tid & 7;
-    const T *grow = X + (int64_t)rows[gj] * ld;
-    Unit8<T> pre;
-
-    for (int t0 = 0; t0 < ntiles && !*abortp; t0 += tpp) {
-        const int nt = min(tpp, ntiles - t0);
-        // prologue: chunk 0 into staging 0
-        if (gj < k) pre.load(grow, gg * 8, m, vec); else pre.zero();
-        pre.store(Xs0 + gj * MT_XS_LD + gg * 8);
-        for (int ci = 0; ci < nchunks; ++ci) {
-            const int b = ci & 1;
-            float *Xs = Xs0 + b * MT_XS_FLOATS;
-            uint8_t *ob = base + b * MT_BUF_BYTES;
-            const int64_t a0 = (int64_t)ci * MT_CH;
-            // issue the next chunk's loads now; they land while this chunk is processed
-            const bool has_next = ci + 1 < nchunks;
-            if (has_next) {
-                if (gj < k) pre.load(grow, a0 + MT_CH + gg * 8, m, vec); else pre.zero();
+    if (warp == MT_FORMERS / 32) {
+        // ================= MMA warp (lane 0 issues) =================
+        uint32_t q = 0, gc = 0;
+        for (int ps = 0; ps < npass; ++ps) {
+            const int t0 = ps * tpp, nt = min(tpp, ntiles - t0);
+            if (lane == 0) {
+                for (int ci = 0; ci < nchunks; ++ci, ++gc) {
+                    const uint32_t bsa = tc::smem_u32(Bop0 + (gc & 1) * MT_B_BYTES);
+                    for (int t = 0; t < nt; ++t, ++q) {
+                        const int s = q % MT_SLOTS;
+                        if (!*abortp &&
+                            !tc::mbar_wait(tc::smem_u32(&slot_full[s]), (q / MT_SLOTS) & 1, abortp, MT_WAIT))
+                            fail();
+                        tc::fence_after();
+                        if (!*abortp) {
+                            const uint32_t a_t = tmem + (uint32_t)(MT_D_COLS + s * MT_SLOT_COLS);
+#pragma unroll
+                            for (int kk = 0; kk < MT_CH / 16; ++kk)
+                                tc::mma_f16_ts(tmem + (uint32_t)(t * Nb), a_t + (uint32_t)(kk * 8),
+                                               tc::sdesc_sw128(bsa + kk * 32), idesc, (ci | kk) != 0);
+                        }
+                        tc::commit(tc::smem_u32(&slot_empty[s]));
+                    }
+                    tc::commit(tc::smem_u32(&chunk_done[gc & 1]));
+                }
+                tc::commit(tc::smem_u32(&pass_done));
+                // every MMA of the pass has completed before this warp moves on (and
+                // before TMEM is freed, whatever happened to the formers)
+                if (!tc::mbar_wait(tc::smem_u32(&pass_done), ps & 1, &never, MT_WAIT)) fail();
             }
-            __syncthreads();  // staging b complete
-            // ---- centre each column over the k rows: thread (column cc, row group rg)
-            // owns rows 8 rg .. 8 rg + 7; column sums and sums of squares go through
-            // shared partials (8 groups per column)
-            {
-                const int cc = tid & 63, rg = tid >> 6;
-                float v[8], s = 0.f;
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    v[e] = Xs[(rg * 8 + e) * MT_XS_LD + cc];  // rows >= k hold zeros
-                    s += v[e];
+            __syncwarp();
+            asm volatile("bar.sync 2, 544;" ::: "memory");  // the formers have drained the accumulators
+            tc::fence_after();
+        }
+    } else {
+        // ================= former warps =================
+        const int qd = warp & 3, cpart = warp >> 2;  // TMEM lane quarter, 16-column part of a chunk
+        const int trow = qd * 32 + lane;             // tile row (= TMEM lane) of this thread
+        const int gj = tid >> 3, gg = tid & 7;       // gather unit: patch row, 8-column group
+        const T *grow = X + (int64_t)rows[gj] * ld;
+        Unit8<T> pre;
+        uint32_t q = 0, gc = 0;
+        for (int ps = 0; ps < npass; ++ps) {
+            const int t0 = ps * tpp, nt = min(tpp, ntiles - t0);
+            if (gj < k) pre.load(grow, gg * 8, m, vec); else pre.zero();
+            for (int ci = 0; ci < nchunks; ++ci, ++gc) {
+                const int b = gc & 1;
+                const int64_t a0 = (int64_t)ci * MT_CH;
+                pre.store(Xs + gj * MT_XS_LD + gg * 8);
+                if (ci + 1 < nchunks) {
+                    if (gj < k) pre.load(grow, a0 + MT_CH + gg * 8, m, vec); else pre.zero();
                 }
-                Part[rg * 64 + cc] = s;
-                __syncthreads();
-                float tot = 0.f;
-#pragma unroll
-                for (int g = 0; g < 8; ++g) tot += Part[g * 64 + cc];
-                const float mean = tot / (float)k;
-                float w = 0.f, rsum[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const bool real = rg * 8 + e < k;
-                    const float x = real ? v[e] - mean : 0.f;
-                    Xs[(rg * 8 + e) * MT_XS_LD + cc] = x;
-                    w = fmaf(x, x, w);
-                    rsum[e] = x;
-                }
-                __syncthreads();  // every thread has read Part
-                Part[rg * 64 + cc] = w;
-                // row sums R (first pass only): warp-reduce each of the 8 rows over 32 columns
-                if (t0 == 0) {
+                asm volatile("bar.sync 1, 512;" ::: "memory");
+                // ---- centre: thread (column cc, row group rg) owns rows 8 rg .. 8 rg + 7
+                {
+                    const int cc = tid & 63, rg = tid >> 6;
+                    float v[8], sum = 0.f;
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
-                        const float r = warp_sum(rsum[e]);
-                        if (lane == 0 && rg * 8 + e < k) atomicAdd(&Rs[rg * 8 + e], r);
+                        v[e] = Xs[(rg * 8 + e) * MT_XS_LD + cc];
+                        sum += v[e];
+                    }
+                    Part[rg * 64 + cc] = sum;
+                    asm volatile("bar.sync 1, 512;" ::: "memory");
+                    float tot = 0.f;
+#pragma unroll
+                    for (int g = 0; g < 8; ++g) tot += Part[g * 64 + cc];
+                    const float mean = tot / (float)k;
+                    float w = 0.f;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const float x = (rg * 8 + e < k) ? v[e] - mean : 0.f;
+                        v[e] = x;
+                        Xs[(rg * 8 + e) * MT_XS_LD + cc] = x;
+                        w = fmaf(x, x, w);
+                    }
+                    asm volatile("bar.sync 1, 512;" ::: "memory");  // every thread has read Part
+                    Part[rg * 64 + cc] = w;
+                    if (ps == 0) {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const float r = warp_sum(v[e]);
+                            if (lane == 0 && rg * 8 + e < k) atomicAdd(&Rs[rg * 8 + e], r);
+                        }
                     }
                 }
-                __syncthreads();
-                if (rg == 0) {
-                    float ws = 0.f;
-#pragma unroll
-                    for (int g = 0; g < 8; ++g) ws += Part[g * 64 + cc];
-                    Ws[cc] = (a0 + cc < m) ? ws : 0.f;
+                // buffer b is free once the MMAs of the chunk that last used it completed
+                if (tid == 0 && gc >= 2) {
+                    if (!*abortp && !tc::mbar_wait(tc::smem_u32(&chunk_done[b]), ((gc >> 1) - 1) & 1, abortp, MT_WAIT))
+                        fail();
                 }
-            }
-            // operand buffer b is free once the MMAs of the chunk that last used it completed
-            const uint32_t cb = b ? commits1 : commits0;
-            if (tid == 0 && cb > 0) {
-                if (!tc::mbar_wait(tc::smem_u32(&mma_done[b]), (cb - 1) & 1, abortp, MT_WAIT)) {
-                    atomicOr(&ctr->status, (unsigned)DEV_TIMEOUT);
-                    abort_flag = 1;
-                }
-            }
-            __syncthreads();
-            // ---- B operand: rows 0..k-1 = X_c, row k = 1, row k+1 = w, rest 0
-            uint8_t *bb = ob + MT_TPP * MT_TILE_BYTES;
-            for (int u = tid; u < Nb * 8; u += MT_THREADS) {
-                const int r = u >> 3, g = u & 7;
-                float v[8];
-                if (r < k) {
+                asm volatile("bar.sync 1, 512;" ::: "memory");
+                uint32_t *Xp = Xp0 + b * MT_XP_ROWS * MT_XP_LD;
+                uint8_t *Bop = Bop0 + b * MT_B_BYTES;
+                {
+                    // unit (row r, 8-column group g): 4 packed words to Xp and the B operand
+                    const int r = tid >> 3, g = tid & 7;
                     const float4 lo = reinterpret_cast<const float4 *>(Xs + r * MT_XS_LD + g * 8)[0];
                     const float4 hi = reinterpret_cast<const float4 *>(Xs + r * MT_XS_LD + g * 8)[1];
-                    v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w;
-                    v[4] = hi.x; v[5] = hi.y; v[6] = hi.z; v[7] = hi.w;
-                } else if (r == k) {
+                    const uint4 pk = make_uint4(pack_bf16x2(lo.x, lo.y), pack_bf16x2(lo.z, lo.w),
+                                                pack_bf16x2(hi.x, hi.y), pack_bf16x2(hi.z, hi.w));
+                    *reinterpret_cast<uint4 *>(Xp + r * MT_XP_LD + g * 4) = pk;
+                    if (r < Nb) *reinterpret_cast<uint4 *>(Bop + sw128(r, g)) = pk;
+                    if (tid < 32) {
+                        float w0 = 0.f, w1 = 0.f;
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) v[e] = (a0 + g * 8 + e < m) ? 1.f : 0.f;
-                } else if (r == k + 1) {
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) v[e] = Ws[g * 8 + e];
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) v[e] = 0.f;
+                        for (int gq = 0; gq < 8; ++gq) {
+                            w0 += Part[gq * 64 + 2 * tid];
+                            w1 += Part[gq * 64 + 2 * tid + 1];
+                        }
+                        Xp[MT_ROW_W * MT_XP_LD + tid] = pack_bf16x2(w0, w1);
+                    }
                 }
-                *reinterpret_cast<uint4 *>(bb + sw128(r, g)) =
-                    make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
-                               pack_bf16x2(v[6], v[7]));
-            }
-            // ---- A operand: Z rows of this pass's tiles
-            for (int u = tid; u < nt * 128 * 8; u += MT_THREADS) {
-                const int rl = u >> 3, g = u & 7;  // row within the pass, 16-byte unit
-                const int pr = t0 * 128 + rl;
-                uint4 pk = make_uint4(0, 0, 0, 0);
-                if (pr < npairs) {
-                    const int code = __ldg(pair_ab + pr);
-                    const int pa = code & 0xffff, pb = code >> 16;
-                    const float4 *xa = reinterpret_cast<const float4 *>(Xs + pa * MT_XS_LD + g * 8);
-                    const float4 *xb = reinterpret_cast<const float4 *>(Xs + pb * MT_XS_LD + g * 8);
-                    const float4 a_lo = xa[0], a_hi = xa[1], b_lo = xb[0], b_hi = xb[1];
-                    pk = make_uint4(pack_bf16x2(a_lo.x * b_lo.x, a_lo.y * b_lo.y),
-                                    pack_bf16x2(a_lo.z * b_lo.z, a_lo.w * b_lo.w),
-                                    pack_bf16x2(a_hi.x * b_hi.x, a_hi.y * b_hi.y),
-                                    pack_bf16x2(a_hi.z * b_hi.z, a_hi.w * b_hi.w));
-                }
-                *reinterpret_cast<uint4 *>(ob + (rl >> 7) * MT_TILE_BYTES + sw128(rl & 127, g)) = pk;
-            }
-            // the next chunk's raw values go to the other staging buffer
-            if (has_next) pre.store(Xs0 + (b ^ 1) * MT_XS_FLOATS + gj * MT_XS_LD + gg * 8);
-            // make the generic-proxy stores visible to the tensor core, then issue
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            if (tid == 0 && !*abortp) {
-                tc::fence_after();
-                const uint32_t bsa = tc::smem_u32(bb);
-                for (int t = 0; t < nt; ++t) {
-                    const uint32_t asa = tc::smem_u32(ob + t * MT_TILE_BYTES);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("bar.sync 1, 512;" ::: "memory");
+                // ---- form the A operand of each tile of the pass in a TMEM slot
+                for (int t = 0; t < nt; ++t, ++q) {
+                    const int s = q % MT_SLOTS;
+                    if (q >= MT_SLOTS) {
+                        if (lane == 0 && !*abortp &&
+                            !tc::mbar_wait(tc::smem_u32(&slot_empty[s]), ((q / MT_SLOTS) - 1) & 1, abortp, MT_WAIT))
+                            fail();
+                        __syncwarp();
+                        tc::fence_after();
+                    }
+                    const int code = codes[(t0 + t) * 128 + trow];
+                    const int ra = code & 0xff, rb = (code >> 8) & 0xff;
+                    const uint4 *pa = reinterpret_cast<const uint4 *>(Xp + ra * MT_XP_LD + cpart * 8);
+                    const uint4 *pb = reinterpret_cast<const uint4 *>(Xp + rb * MT_XP_LD + cpart * 8);
+                    const uint4 a_lo = pa[0], a_hi = pa[1], b_lo = pb[0], b_hi = pb[1];
+                    uint32_t z[8];
+                    const uint32_t av[8] = {a_lo.x, a_lo.y, a_lo.z, a_lo.w, a_hi.x, a_hi.y, a_hi.z, a_hi.w};
+                    const uint32_t bv[8] = {b_lo.x, b_lo.y, b_lo.z, b_lo.w, b_hi.x, b_hi.y, b_hi.z, b_hi.w};
 #pragma unroll
-                    for (int kk = 0; kk < MT_CH / 16; ++kk)
-                        tc::mma_f16(tmem + (uint32_t)(t * Nb), tc::sdesc_sw128(asa + kk * 32),
-                                    tc::sdesc_sw128(bsa + kk * 32), idesc, (ci | kk) != 0);
+                    for (int e = 0; e < 8; ++e) {
+                        __nv_bfloat162 x = *reinterpret_cast<const __nv_bfloat162 *>(&av[e]);
+                        __nv_bfloat162 y = *reinterpret_cast<const __nv_bfloat162 *>(&bv[e]);
+                        __nv_bfloat162 pr = __hmul2(x, y);
+                        z[e] = *reinterpret_cast<uint32_t *>(&pr);
+                    }
+                    tc::tmem_st_32x32b_x8(tmem + ((uint32_t)(qd * 32) << 16) +
+                                              (uint32_t)(MT_D_COLS + s * MT_SLOT_COLS + cpart * 8),
+                                          z);
+                    tc::tmem_st_wait();
+                    tc::fence_before();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(tc::smem_u32(&slot_full[s]));
                 }
-                tc::commit(tc::smem_u32(&mma_done[b]));
             }
-            if (b) ++commits1; else ++commits0;
-        }
-        // ---- wait for the last MMAs of the pass (bounded), then drain TMEM
-        if (tid == 0) {
-            if (commits0 > 0) tc::mbar_wait(tc::smem_u32(&mma_done[0]), (commits0 - 1) & 1, &never, MT_WAIT);
-            if (commits1 > 0) tc::mbar_wait(tc::smem_u32(&mma_done[1]), (commits1 - 1) & 1, &never, MT_WAIT);
-        }
-        __syncthreads();
-        tc::fence_after();
-        // warp group wg = warp / 4 drains tiles wg, wg + 4, ... into its own staging
-        // slot (128 x k floats) in the now idle operand buffers
-        const int quarter = warp & 3, wg = warp >> 2;
-        const size_t slot_bytes = 128 * 64 * sizeof(float);
-        float *stage = reinterpret_cast<float *>(base + (size_t)wg * slot_bytes);
-        for (int tb = 0; tb < nt; tb += 4) {
-            const int t = tb + wg;
-            const bool active = t < nt;
-            const int row = quarter * 32 + lane;
-            const int pr = (t0 + t) * 128 + row;
-            const bool valid = active && pr < npairs;
-            int pa = 0, pb = 0;
-            if (valid) { const int code = __ldg(pair_ab + pr); pa = code & 0xffff; pb = code >> 16; }
-            if (active) {
+            // ---- drain the pass's accumulators: warps with cpart == t % 4 take tile t
+            if (lane == 0 && !tc::mbar_wait(tc::smem_u32(&pass_done), ps & 1, abortp, MT_WAIT)) fail();
+            __syncwarp();
+            tc::fence_after();
+            for (int t = cpart; t < nt; t += 4) {
+                const int code = codes[(t0 + t) * 128 + trow];
+                const int ra = code & 0xff, rb = (code >> 8) & 0xff, kind = (code >> 16) & 3;
+                float *dst = nullptr;
+                if (kind == ROW_PAIR) dst = M + (pt * (int64_t)npairs + pair_index(ra, rb, k)) * k;
+                else if (kind == ROW_G) dst = G + (pt * k + ra) * (int64_t)k;
+                else if (kind == ROW_Q && Q) dst = Q + (pt * k + ra) * (int64_t)k;
                 for (int c0 = 0; c0 < Nb; c0 += 16) {
                     uint32_t r16[16];
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-                        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-                        : "=r"(r16[0]), "=r"(r16[1]), "=r"(r16[2]), "=r"(r16[3]), "=r"(r16[4]), "=r"(r16[5]),
-                          "=r"(r16[6]), "=r"(r16[7]), "=r"(r16[8]), "=r"(r16[9]), "=r"(r16[10]), "=r"(r16[11]),
-                          "=r"(r16[12]), "=r"(r16[13]), "=r"(r16[14]), "=r"(r16[15])
-                        : "r"(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * Nb + c0)));
+                    tc::tmem_ld_32x32b_x16(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(t * Nb + c0), r16);
                     tc::tmem_ld_wait();
+                    if (dst) {
+                        if ((k & 3) == 0 && c0 + 16 <= k) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int col = c0 + j;
-                        const float v = __uint_as_float(r16[j]);
-                        if (col < k) stage[row * k + col] = v;
-                        else if (valid && col == k) {
-                            G[pt * k * k + pa * k + pb] = v;
-                            G[pt * k * k + pb * k + pa] = v;
-                        } else if (valid && col == k + 1 && Q) {
-                            Q[pt * k * k + pa * k + pb] = v;
-                            Q[pt * k * k + pb * k + pa] = v;
+                            for (int e = 0; e < 16; e += 4)
+                                *reinterpret_cast<float4 *>(dst + c0 + e) =
+                                    make_float4(__uint_as_float(r16[e]), __uint_as_float(r16[e + 1]),
+                                                __uint_as_float(r16[e + 2]), __uint_as_float(r16[e + 3]));
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 16; ++e)
+                                if (c0 + e < k) dst[c0 + e] = __uint_as_float(r16[e]);
                         }
                     }
                 }
             }
-            __syncthreads();
-            // coalesced copy of the staged tiles: rows [r0, min(npairs, r0 + 128)) x k floats are contiguous
-            for (int g4 = 0; g4 < 4; ++g4) {
-                const int tt = tb + g4;
-                if (tt >= nt) break;
-                const int r0 = (t0 + tt) * 128;
-                const int nf = min(128, npairs - r0) * k;
-                const float *src = reinterpret_cast<const float *>(base + (size_t)g4 * slot_bytes);
-                float *dst = M + (pt * (int64_t)npairs + r0) * k;
-                for (int e = tid; e < nf; e += MT_THREADS) dst[e] = src[e];
-            }
-            __syncthreads();
+            tc::fence_before();
+            asm volatile("bar.sync 2, 544;" ::: "memory");
         }
-        tc::fence_before();
-        __syncthreads();
     }
+    __syncthreads();
     if (tid < k) R[pt * k + tid] = Rs[tid];
     tc::fence_before();
     __syncthreads();
@@ -370,30 +419,26 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
     }
 }
 
-void moments_tc_build_pairs(int k, int32_t *pair_ab) {
-    int n = 0;
-    for (int a = 0; a < k; ++a)
-        for (int b = a; b < k; ++b) pair_ab[n++] = a | (b << 16);
-}
-
 cudaError_t launch_moments_tc(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, const int32_t *idx,
-                              int k, int64_t np, const int32_t *pair_ab, float *M, float *G, float *R, float *Q,
+                              int k, int64_t np, const int32_t *rowtab, float *M, float *G, float *R, float *Q,
                               DevCounters *ctr, cudaStream_t s) {
     if (np <= 0) return cudaSuccess;
     if (k > 64 || k < 2) return cudaErrorInvalidValue;
-    const size_t smem = moments_tc_smem_bytes();
+    const int nrows = moments_tc_rows(k);
+    if (nrows > MT_MAX_ROWS) return cudaErrorInvalidValue;
+    const size_t smem = moments_tc_smem_bytes(k);
     cudaError_t e;
     if (dt == MECUCO_BF16) {
         e = cudaFuncSetAttribute(moments_tc_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
-        moments_tc_kernel<<<(unsigned)np, MT_THREADS, smem, s>>>((const __nv_bfloat16 *)X, N, m, ld, idx, k, pair_ab,
-                                                                 M, G, R, Q, ctr);
+        moments_tc_kernel<<<(unsigned)np, MT_THREADS, smem, s>>>((const __nv_bfloat16 *)X, N, m, ld, idx, k, rowtab,
+                                                                 nrows, M, G, R, Q, ctr);
     } else {
         e = cudaFuncSetAttribute(moments_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        moments_tc_kernel<<<(unsigned)np, MT_THREADS, smem, s>>>((const float *)X, N, m, ld, idx, k, pair_ab, M, G,
-                                                                 R, Q, ctr);
+        moments_tc_kernel<<<(unsigned)np, MT_THREADS, smem, s>>>((const float *)X, N, m, ld, idx, k, rowtab, nrows, M,
+                                                                 G, R, Q, ctr);
     }
     return cudaGetLastError();
 }
