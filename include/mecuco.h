@@ -111,7 +111,8 @@ typedef enum {
     MECUCO_STAGE_JACOBI = 6,     /* k x k eigensolve */
     MECUCO_STAGE_ESTIMATOR = 7,  /* k-space Fast estimator */
     MECUCO_STAGE_ADJOINT = 8,    /* k-space adjoint + patch adjoint and scatter */
-    MECUCO_STAGE_COUNT = 9
+    MECUCO_STAGE_BASIS = 9,      /* tangent-basis expansion V_r = X_c^T U_p S^-1 */
+    MECUCO_STAGE_COUNT = 10
 } mecuco_stage;
 
 /* Counters of the last completed call (valid after the stream is synchronised). */
@@ -203,6 +204,20 @@ MECUCO_API mecuco_status mecuco_curvature_range(mecuco_t h, const void *X, mecuc
 MECUCO_API mecuco_status mecuco_curvature_backward(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m,
                                                    int64_t ld, int k, const int32_t *idx, mecuco_variant var,
                                                    const float *dkappa, float *dX_out, void *stream);
+
+/* Tangent bases of the points [row_begin, row_end) (Alg. 1 SVD_p; eq. svd_cov):
+ * the first d_out right singular vectors V_r = X_c^T U_p S^-1 of each patch,
+ * from the plain FP32 Gram and eigensolve (MECUCO_OPT_JACOBI_FP64 applies).
+ * Columns l >= p (the numerical rank rule of the estimator) are zero; column
+ * signs are fixed so that the largest-magnitude entry of U_p's column l
+ * (lowest row on ties) is positive.
+ *   X      device, N x m (ld) of dtype dt
+ *   idx    device, N x k int32 neighbour lists (required)
+ *   d_out  1 <= d_out <= min(k - 1, m)
+ *   V_out  device, (row_end - row_begin) x m x d_out floats, l fastest */
+MECUCO_API mecuco_status mecuco_tangent_basis(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m,
+                                              int64_t ld, int k, const int32_t *idx, int64_t row_begin,
+                                              int64_t row_end, int d_out, float *V_out, void *stream);
 
 /* The same computation with HOST buffers (pageable or pinned): X_host is
  * copied to the device, the path runs, kappa (and idx if idx_host_out is not

@@ -18,7 +18,8 @@ FAST_LITERAL, FAST_HAAR = 0, 1
 PREC_FP32, PREC_BF16_MIXED = 0, 1
 (OPT_KNN_MARGIN, OPT_JACOBI_FP64, OPT_JACOBI_MAX_SWEEPS, OPT_CHUNK_POINTS, OPT_KNN_QUERY_CHUNK, OPT_PROFILE,
  OPT_KNN_SPLITS) = range(7)
-STAGES = ("rownorm", "knn_search", "knn_rerank", "knn_fallback", "gram", "moments", "jacobi", "estimator", "adjoint")
+STAGES = ("rownorm", "knn_search", "knn_rerank", "knn_fallback", "gram", "moments", "jacobi", "estimator", "adjoint",
+          "basis")
 
 
 class MecucoNotBuilt(ImportError):
@@ -57,6 +58,7 @@ SIGNATURES = {
     "mecuco_curvature_range": (_st, [_p, _p, _i32, _i64, _i64, _i64, _i32, _p, _i32, _i32, _i32, _i64, _i64,
                                      _p, _p, _p, _p, _p]),
     "mecuco_curvature_backward": (_st, [_p, _p, _i32, _i64, _i64, _i64, _i32, _p, _i32, _p, _p, _p]),
+    "mecuco_tangent_basis": (_st, [_p, _p, _i32, _i64, _i64, _i64, _i32, _p, _i64, _i64, _i32, _p, _p]),
     "mecuco_curvature_host": (_st, [_p, _p, _i32, _i64, _i64, _i64, _i32, _i32, _i32, _i32, _p, _p, _p]),
     "mecuco_knn_noalloc": (_st, [_p, _i32, _i64, _i64, _i64, _i32, _i32, _p, _p, _p]),
     "mecuco_get_last_status": (_st, [_p, _p]),

@@ -137,6 +137,20 @@ class Context:
         N.check(st, "mecuco_curvature_range")
         return kappa
 
+    def mecuco_tangent_basis(self, X: torch.Tensor, k: int, idx: torch.Tensor, d_out: int, row_begin: int = 0,
+                             row_end=None) -> torch.Tensor:
+        """First d_out tangent directions V_r (m x d_out per point) of rows [row_begin, row_end)."""
+        _check_x(X, self.device)
+        n, m = X.shape
+        if idx.dtype != torch.int32 or tuple(idx.shape) != (n, k) or not idx.is_contiguous():
+            raise ValueError("idx must be a contiguous int32 (N, k) tensor")
+        re = n if row_end is None else int(row_end)
+        V = torch.empty((re - int(row_begin), m, int(d_out)), dtype=torch.float32, device=X.device)
+        st = self.lib.mecuco_tangent_basis(self.handle, _ptr(X), _dtype_code(X), n, m, X.stride(0), int(k), _ptr(idx),
+                                           int(row_begin), re, int(d_out), _ptr(V), _stream(self.device))
+        N.check(st, "mecuco_tangent_basis")
+        return V
+
     def mecuco_curvature_backward(self, X: torch.Tensor, k: int, idx: torch.Tensor, dkappa: torch.Tensor,
                                   variant: str = "literal"):
         """dX = d(sum_i dkappa_i K_i)/dX with the neighbour lists idx frozen (float32, N x m)."""

@@ -204,9 +204,6 @@ KnnPlan plan_knn(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t 
     const int64_t want = (p.tc ? 1LL : 2LL) * h->num_sms;
     p.nsplit = 1;
     if (qblocks < want) p.nsplit = (int)std::min<int64_t>((want + qblocks - 1) / qblocks, 1024 / p.kc);
-    // tensor-core search: at least 2 splits, so a wave of the persistent CTAs
-    // (one per SM) touches num_sms / 2 query tiles, which stay in L2
-    if (p.tc) p.nsplit = std::max(p.nsplit, std::min(2, 1024 / p.kc));
     if (h->knn_splits > 0) p.nsplit = std::min(h->knn_splits, 1024 / p.kc);
     while (p.nsplit > 1 && (N + p.nsplit - 1) / p.nsplit < p.kc) --p.nsplit;
     return p;
@@ -606,10 +603,13 @@ mecuco_status mecuco_curvature_backward(mecuco_t h, const void *X, mecuco_dtype 
     for (int64_t p0 = 0; p0 < N; p0 += chunk) {
         const int64_t np = std::min(chunk, N - p0);
         const int32_t *nb = idx + p0 * k;
-        // U0: eigenvectors of the plain FP32 Gram
+        // U0: eigenvectors of the plain FP32 Gram, FP64-refined so that U0 is orthogonal to
+        // FP32 rounding (a rotation that is not orthogonal acts as a perturbation of X_c,
+        // which ill-conditioned patches amplify)
         LAUNCH(h, MECUCO_STAGE_GRAM, s,
                launch_patch_gram(X, dt, N, m, ld, nb, k, 0, np, nullptr, b.G, b.R, nullptr, h->ctr, s));
-        LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(b.G, k, np, 0, h->jacobi_max_sweeps, b.sig, U0, h->ctr, s));
+        LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(b.G, k, np, 1, h->jacobi_max_sweeps, b.sig, U0, h->ctr, s));
+        ++h->launches;  // the refinement kernel
         // moments of Z = U0^T X_c and the FP64-refined eigenpairs of its Gram
         LAUNCH(h, MECUCO_STAGE_GRAM, s,
                launch_patch_gram(X, dt, N, m, ld, nb, k, 0, np, U0, b.G, b.R, need_q ? b.Q : nullptr, h->ctr, s));
@@ -621,6 +621,42 @@ mecuco_status mecuco_curvature_backward(mecuco_t h, const void *X, mecuco_dtype 
                launch_adjoint(X, dt, N, m, ld, nb, k, np, (int)var, U0, b.sig, b.U, b.M, b.R, b.Q, dkappa + p0, dG, dR,
                               dQ, Cb, dM, dX_out, m, s));
         ++h->launches;  // two kernels
+    }
+    return MECUCO_OK;
+}
+
+mecuco_status mecuco_tangent_basis(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
+                                   int k, const int32_t *idx, int64_t rb, int64_t re, int d_out, float *V_out,
+                                   void *stream) {
+    mecuco_status st = check_common(h, X, dt, N, m, ld, k, 1);  // idx is given: k <= N
+    if (st != MECUCO_OK) return st;
+    if ((st = check_range(N, rb, re)) != MECUCO_OK) return st;
+    if (!idx || !V_out || d_out < 1 || d_out > k - 1 || (int64_t)d_out > m) return MECUCO_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = begin_call(h, s)) != MECUCO_OK) return st;
+    const int64_t chunk = std::min<int64_t>(h->chunk_points > 0 ? h->chunk_points : 65536, re - rb);
+    Carver t(nullptr);
+    t.take<float>((size_t)chunk * k * k);
+    t.take<float>((size_t)chunk * k);
+    t.take<float>((size_t)chunk * k);
+    t.take<float>((size_t)chunk * k * k);
+    if ((st = ensure(h->ws, h->ws_bytes, t.off)) != MECUCO_OK) return st;
+    Carver c(h->ws);
+    float *G = c.take<float>((size_t)chunk * k * k);
+    float *R = c.take<float>((size_t)chunk * k);
+    float *sig = c.take<float>((size_t)chunk * k);
+    float *U = c.take<float>((size_t)chunk * k * k);
+    const int mode = h->jacobi_fp64 >= 0 ? h->jacobi_fp64 : 0;
+    for (int64_t p0 = rb; p0 < re; p0 += chunk) {
+        const int64_t np = std::min(chunk, re - p0);
+        const int32_t *nb = idx + p0 * k;
+        LAUNCH(h, MECUCO_STAGE_GRAM, s,
+               launch_patch_gram(X, dt, N, m, ld, nb, k, 0, np, nullptr, G, R, nullptr, h->ctr, s));
+        LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(G, k, np, mode, h->jacobi_max_sweeps, sig, U, h->ctr, s));
+        if (mode == 1 || mode == 3) ++h->launches;
+        LAUNCH(h, MECUCO_STAGE_BASIS, s,
+               launch_tangent_basis(X, dt, N, m, ld, nb, k, np, sig, U, d_out, V_out + (p0 - rb) * m * (int64_t)d_out,
+                                    h->ctr, s));
     }
     return MECUCO_OK;
 }

@@ -116,6 +116,13 @@ cudaError_t launch_estimator(const float *sigma, const float *U, const float *M,
                              float *kappa, float *lambda_out, float *s_out, DevCounters *ctr,
                              cudaStream_t s);
 
+// ---- tangent bases ------------------------------------------------------------
+// V (np x m x d_out, l fastest) = X_c^T U_p S^-1 for the points of one chunk
+// (idx offset to the chunk), sigma/U from launch_jacobi.
+cudaError_t launch_tangent_basis(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
+                                 const int32_t *idx, int k, int64_t np, const float *sigma, const float *U,
+                                 int d_out, float *V, DevCounters *ctr, cudaStream_t s);
+
 // ---- adjoint ---------------------------------------------------------------
 // d(sum_i gk_i K_i)/dX for the points of one chunk (idx offset to the chunk),
 // accumulated into dX (row stride ldd) with atomics.  Inputs are sigma/U (the

@@ -1,0 +1,72 @@
+"""Adjoint of the Fast-mode curvature (mecuco_curvature_backward and the torch
+autograd wrapper): d(sum_i K_i)/dX with the neighbour lists frozen, against
+FP64 central finite differences of the oracle (target: 1e-3 relative)."""
+import numpy as np
+import pytest
+
+from paper_2606_06329_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GRAD_TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_06329_gb300 import api, build
+    build.build()
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+def _rel(got, ref):
+    scale = np.maximum(np.abs(ref), 1e-2 * np.sqrt(np.mean(ref ** 2)))
+    return np.abs(got - ref) / scale
+
+
+def _grad_check(ctx, orc, X, k, ncoord, variant, seed):
+    n, m = X.shape
+    X64 = X.astype(np.float64)
+    idx, _ = orc.knn(X64, k)
+    Xd = torch.from_numpy(X).cuda()
+    idd = torch.from_numpy(idx).cuda()
+    dX = ctx.mecuco_curvature_backward(Xd, k, idd, torch.ones(n, device="cuda"), variant=variant)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(seed)
+    coords = np.stack([rng.integers(0, n, ncoord), rng.integers(0, m, ncoord)], axis=1)
+    h = 1e-5 * np.sqrt(np.mean(X64 ** 2))
+    fd = orc.grad_fd(X64, k, idx, coords, h, variant=orc.HAAR if variant == "haar" else orc.LITERAL)
+    got = dX.cpu().numpy()[coords[:, 0], coords[:, 1]].astype(np.float64)
+    err = _rel(got, fd)
+    print(f"grad {variant} n={n} m={m} k={k}: max rel err {err.max():.2e}, median {np.median(err):.2e}")
+    return err
+
+
+@pytest.mark.parametrize("variant", ["literal", "haar"])
+def test_backward_small_vs_finite_differences(ctx, orc, variant):
+    X = synth.mlp_decoder(n=3000, m=24, latent=4, seed=3)
+    err = _grad_check(ctx, orc, X, 8, 48, variant, seed=1)
+    assert err.max() < GRAD_TOL
+
+
+def test_backward_mlp_decoder_full_size(ctx, orc):
+    X = synth.mlp_decoder(n=50000, m=256, seed=1)
+    err = _grad_check(ctx, orc, X, 32, 64, "literal", seed=2)
+    assert err.max() < GRAD_TOL
+
+
+def test_autograd_function_matches_entry_point(ctx):
+    from paper_2606_06329_gb300 import autograd
+    X = torch.from_numpy(synth.sphere(n=1500, m=32, seed=5)).cuda().requires_grad_(True)
+    k = 10
+    idx = ctx.mecuco_knn(X.detach(), k)
+    w = torch.rand(1500, device="cuda")
+    kappa = autograd.curvature(X, idx, k)
+    (kappa * w).sum().backward()
+    ref = ctx.mecuco_curvature_backward(X.detach(), k, idx, w)
+    assert torch.allclose(X.grad, ref, rtol=1e-5, atol=1e-6 * ref.abs().max().item())
+    assert torch.allclose(kappa.detach(), ctx.mecuco_curvature(X.detach(), k, idx=idx))
