@@ -132,15 +132,24 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def _profile_traffic():
-    """DRAM bytes per launch of the distance-search kernel from the committed
-    ncu summary (profiles/knn_search_*.md), if one matches the current kernel."""
-    path = os.path.join(ROOT, "profiles", "knn_tc_traffic.json")
-    if os.path.exists(path):
-        try:
-            return json.load(open(path))
-        except Exception:
-            return None
+def _profile_traffic(N: int, nq: int):
+    """DRAM bytes per launch of the distance-search kernel, from the line
+    ``bench-traffic: kernel=knn_tc_kernel pairs=P bytes=B source_sha1=H`` of a
+    committed ncu summary under profiles/ (one capture of P query-candidate
+    pairs), scaled to this launch's nq * N pairs; None when no summary matches
+    the current kernel source."""
+    import glob
+    import hashlib
+    src = os.path.join(ROOT, "paper_2606_06329_gb300", "csrc", "knn_tc.cu")
+    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for ln in open(path):
+            if not ln.startswith("bench-traffic:"):
+                continue
+            kv = dict(tok.split("=", 1) for tok in ln.split()[1:] if "=" in tok)
+            if kv.get("kernel") != "knn_tc_kernel" or kv.get("source_sha1") != sha:
+                continue
+            return float(kv["bytes"]) * (nq * N) / float(kv["pairs"])
     return None
 
 
@@ -261,10 +270,13 @@ def run_ours(args):
             flops_per_launch = 2.0 * N * N * m / knn_n * args.steps
             ach = flops_per_launch / (knn_ms / knn_n * 1e-3) / 1e12
             pk = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-            traffic = _profile_traffic()
+            nq_launch = N / knn_n * args.steps
+            traffic = _profile_traffic(N, nq_launch)
             roof = {"kernel": "knn_tc_kernel (distance GEMM + fused candidate select)", "bound": "tensor",
                     "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                    "traffic": traffic.get("bytes_per_launch") if traffic and traffic.get("N") == N else None,
+                    "traffic": traffic,
+                    "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a smaller capture, "
+                                      "scaled by query-candidate pairs (profiles/)" if traffic else None,
                     "peak_source": f"{src} bf16_tflops_sustained (kernel timed inside a multi-second step)",
                     "algorithmic": "2*N*N*m FLOP per step (dot products of every query with every point)",
                     "share_of_step": knn_ms / elapsed_ms}
@@ -333,7 +345,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="curved_patches_1m")

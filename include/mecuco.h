@@ -96,8 +96,10 @@ typedef enum {
     MECUCO_OPT_CHUNK_POINTS = 3,     /* points per estimator chunk (0 = automatic) */
     MECUCO_OPT_KNN_QUERY_CHUNK = 4,  /* query rows per kNN launch (0 = automatic) */
     MECUCO_OPT_PROFILE = 5,          /* 1: bracket every kernel with CUDA events (mecuco_get_stage_times) */
-    MECUCO_OPT_KNN_SPLITS = 6        /* candidate-range splits of the kNN search (0 = automatic, else 1..64;
+    MECUCO_OPT_KNN_SPLITS = 6,       /* candidate-range splits of the kNN search (0 = automatic, else 1..64;
                                         capped so that splits * candidate capacity <= 1024) */
+    MECUCO_OPT_BATCH_LANES = 7       /* concurrent streams of mecuco_curvature_batched (1..32, default 8;
+                                        a batch signature tuned by mecuco_autotune_batched uses its own) */
 } mecuco_option;
 
 /* Kernel stages, for mecuco_get_stage_times. */
@@ -218,6 +220,37 @@ MECUCO_API mecuco_status mecuco_curvature_backward(mecuco_t h, const void *X, me
 MECUCO_API mecuco_status mecuco_tangent_basis(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m,
                                               int64_t ld, int k, const int32_t *idx, int64_t row_begin,
                                               int64_t row_end, int d_out, float *V_out, void *stream);
+
+/* One dataset of a batched call. */
+typedef struct {
+    const void *X;  /* device, N x m, row stride ld, of the call's dtype */
+    int64_t N, m, ld;
+    int k;          /* 2 <= k <= 64, k <= N - 1 (N with include_self) */
+    int32_t *idx;   /* device N x k: the neighbour lists are written here (NULL: kept in scratch only) */
+    float *kappa;   /* device N: the curvature of every point */
+} mecuco_dataset;
+
+/* kNN + Fast-mode curvature (Alg. 1) of many independent datasets of uneven
+ * sizes in one call, each exactly as mecuco_curvature computes it.  The
+ * datasets are spread over concurrent streams ("lanes", longest first onto the
+ * least-loaded lane; the caller's stream forks to them and joins them back),
+ * each lane with its own slice of a batch workspace.  `sets` is a host array
+ * read during the call.  A call that needs no new workspace and no new per-k
+ * table (every k already seen by this context) makes no allocation and no
+ * host synchronisation, so it can be captured into a CUDA graph; make one
+ * uncaptured call with the same datasets first. */
+MECUCO_API mecuco_status mecuco_curvature_batched(mecuco_t h, const mecuco_dataset *sets, int nsets,
+                                                  mecuco_dtype dt, int include_self, mecuco_variant var,
+                                                  mecuco_precision prec, void *stream);
+
+/* Times mecuco_curvature_batched on these datasets with 1, 2, 4, 8, 16 and 32
+ * lanes (CUDA events on `stream`, after one warm-up call), keeps the fastest
+ * for this batch signature (number of sets, total N, m and k, dtype,
+ * precision) in the context and returns it in *lanes_out.  Synchronous; the
+ * results of the last timed call are left in the datasets' outputs. */
+MECUCO_API mecuco_status mecuco_autotune_batched(mecuco_t h, const mecuco_dataset *sets, int nsets,
+                                                 mecuco_dtype dt, int include_self, mecuco_variant var,
+                                                 mecuco_precision prec, void *stream, int *lanes_out);
 
 /* The same computation with HOST buffers (pageable or pinned): X_host is
  * copied to the device, the path runs, kappa (and idx if idx_host_out is not

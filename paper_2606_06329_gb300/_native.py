@@ -17,7 +17,7 @@ F32, BF16 = 0, 1
 FAST_LITERAL, FAST_HAAR = 0, 1
 PREC_FP32, PREC_BF16_MIXED = 0, 1
 (OPT_KNN_MARGIN, OPT_JACOBI_FP64, OPT_JACOBI_MAX_SWEEPS, OPT_CHUNK_POINTS, OPT_KNN_QUERY_CHUNK, OPT_PROFILE,
- OPT_KNN_SPLITS) = range(7)
+ OPT_KNN_SPLITS, OPT_BATCH_LANES) = range(8)
 STAGES = ("rownorm", "knn_search", "knn_rerank", "knn_fallback", "gram", "moments", "jacobi", "estimator", "adjoint",
           "basis")
 
@@ -43,6 +43,11 @@ class mecuco_stats(C.Structure):
         "jacobi_not_converged", "rank_deficient", "kernel_launches")]
 
 
+class mecuco_dataset(C.Structure):
+    _fields_ = [("X", C.c_void_p), ("N", C.c_int64), ("m", C.c_int64), ("ld", C.c_int64), ("k", C.c_int),
+                ("idx", C.c_void_p), ("kappa", C.c_void_p)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -59,6 +64,9 @@ SIGNATURES = {
                                      _p, _p, _p, _p, _p]),
     "mecuco_curvature_backward": (_st, [_p, _p, _i32, _i64, _i64, _i64, _i32, _p, _i32, _p, _p, _p]),
     "mecuco_tangent_basis": (_st, [_p, _p, _i32, _i64, _i64, _i64, _i32, _p, _i64, _i64, _i32, _p, _p]),
+    "mecuco_curvature_batched": (_st, [_p, C.POINTER(mecuco_dataset), _i32, _i32, _i32, _i32, _i32, _p]),
+    "mecuco_autotune_batched": (_st, [_p, C.POINTER(mecuco_dataset), _i32, _i32, _i32, _i32, _i32, _p,
+                                      C.POINTER(C.c_int)]),
     "mecuco_curvature_host": (_st, [_p, _p, _i32, _i64, _i64, _i64, _i32, _i32, _i32, _i32, _p, _p, _p]),
     "mecuco_knn_noalloc": (_st, [_p, _i32, _i64, _i64, _i64, _i32, _i32, _p, _p, _p]),
     "mecuco_get_last_status": (_st, [_p, _p]),

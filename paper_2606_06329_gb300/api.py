@@ -137,6 +137,46 @@ class Context:
         N.check(st, "mecuco_curvature_range")
         return kappa
 
+    def _datasets(self, Xs, ks, idx_out):
+        if len(Xs) != len(ks) or not Xs:
+            raise ValueError("one k per dataset")
+        dt = _dtype_code(Xs[0])
+        arr = (N.mecuco_dataset * len(Xs))()
+        kappas = []
+        for i, (X, k) in enumerate(zip(Xs, ks)):
+            _check_x(X, self.device)
+            if _dtype_code(X) != dt:
+                raise ValueError("all datasets of a batch share one dtype")
+            n, m = X.shape
+            kap = torch.empty(n, dtype=torch.float32, device=X.device)
+            kappas.append(kap)
+            iv = idx_out[i] if idx_out is not None else None
+            if iv is not None and (iv.dtype != torch.int32 or tuple(iv.shape) != (n, int(k)) or not iv.is_contiguous()):
+                raise ValueError("idx_out[i] must be a contiguous int32 (N, k) tensor")
+            arr[i] = N.mecuco_dataset(_ptr(X), n, m, X.stride(0), int(k), _ptr(iv) if iv is not None else None,
+                                      _ptr(kap))
+        return arr, dt, kappas
+
+    def mecuco_curvature_batched(self, Xs, ks, include_self: bool = False, variant: str = "literal",
+                                 precision: str = "fp32", idx_out=None):
+        """Curvature of several datasets in one call; returns one kappa tensor per dataset
+        (neighbour lists written to idx_out[i] when given)."""
+        arr, dt, kappas = self._datasets(Xs, ks, idx_out)
+        st = self.lib.mecuco_curvature_batched(self.handle, arr, len(Xs), dt, int(bool(include_self)), _VAR[variant],
+                                               _PREC[precision], _stream(self.device))
+        N.check(st, "mecuco_curvature_batched")
+        return kappas
+
+    def mecuco_autotune_batched(self, Xs, ks, include_self: bool = False, variant: str = "literal",
+                                precision: str = "fp32") -> int:
+        """Time the batched call with 1..32 lanes; keep and return the fastest lane count."""
+        arr, dt, _ = self._datasets(Xs, ks, None)
+        lanes = C.c_int(0)
+        st = self.lib.mecuco_autotune_batched(self.handle, arr, len(Xs), dt, int(bool(include_self)), _VAR[variant],
+                                              _PREC[precision], _stream(self.device), C.byref(lanes))
+        N.check(st, "mecuco_autotune_batched")
+        return lanes.value
+
     def mecuco_tangent_basis(self, X: torch.Tensor, k: int, idx: torch.Tensor, d_out: int, row_begin: int = 0,
                              row_end=None) -> torch.Tensor:
         """First d_out tangent directions V_r (m x d_out per point) of rows [row_begin, row_end)."""

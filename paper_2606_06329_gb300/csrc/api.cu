@@ -7,7 +7,10 @@
 #include <cstddef>
 
 #include <algorithm>
+#include <map>
 #include <new>
+#include <numeric>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -58,11 +61,17 @@ struct mecuco_ctx {
     char *io = nullptr;  // device copies of the host-buffer entry point
     size_t io_bytes = 0;
     DevCounters *ctr = nullptr;
-    int32_t *m3_items = nullptr;
-    int m3_items_k = -1;
-    int32_t *pair_ab = nullptr;
-    int pair_ab_k = -1;
+    int32_t *m3_items[65] = {};  // per k: work items of the CUDA-core third-moment kernel
+    int32_t *rowtab[65] = {};    // per k: row codes of the tensor-core moment kernel
     int knn_splits = 0;
+    // batched entry point: lanes (streams) and their workspace
+    int batch_lanes = 8;
+    char *bws = nullptr;
+    size_t bws_bytes = 0;
+    cudaStream_t lane_stream[32] = {};
+    cudaEvent_t lane_event[32] = {};
+    cudaEvent_t fork_event = nullptr;
+    std::map<std::tuple<int, int64_t, int64_t, int64_t, int, int>, int> tuned_lanes;  // batch signature -> lanes
     // options
     int64_t knn_margin = 32;
     int jacobi_fp64 = -1;
@@ -231,11 +240,11 @@ void knn_scratch(Carver &c, const KnnPlan &p, int64_t N, KnnBufs *b) {
 
 // kNN of query rows [rb, re) (outputs relative to rb); scratch at ws + start,
 // the workspace already sized by the caller.
-mecuco_status run_knn(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, int k,
+mecuco_status run_knn(mecuco_t h, char *ws, const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, int k,
                       int include_self, mecuco_precision prec, int64_t rb, int64_t re, int32_t *idx_out,
                       float *dist_out, cudaStream_t s, size_t start) {
     KnnPlan p = plan_knn(h, X, dt, N, m, ld, re - rb, k, prec);
-    Carver c(h->ws, start);
+    Carver c(ws, start);
     KnnBufs b;
     knn_scratch(c, p, N, &b);
     LAUNCH(h, MECUCO_STAGE_ROWNORM, s, launch_rownorm(X, dt, N, m, ld, b.norms, s));
@@ -298,50 +307,36 @@ mecuco_status begin_call(mecuco_t h, cudaStream_t s) {
     return MECUCO_OK;
 }
 
-mecuco_status ensure_pairs(mecuco_t h, int k) {
-    if (h->pair_ab_k == k) return MECUCO_OK;
-    if (h->pair_ab) {
-        CK(cudaDeviceSynchronize());
-        cudaFree(h->pair_ab);
-        h->pair_ab = nullptr;
-        h->pair_ab_k = -1;
-    }
-    const int n = moments_tc_rows(k);
-    std::vector<int32_t> host((size_t)n);
-    moments_tc_build_rows(k, host.data());
-    if (cudaMalloc(&h->pair_ab, sizeof(int32_t) * n) != cudaSuccess) {
+// Device tables built once per k and kept for the context's lifetime (the
+// first use of a k copies synchronously; later calls, and stream capture, do not).
+mecuco_status upload_table(int32_t **slot, const std::vector<int32_t> &host) {
+    int32_t *d = nullptr;
+    if (cudaMalloc(&d, sizeof(int32_t) * std::max<size_t>(host.size(), 1)) != cudaSuccess) {
         (void)cudaGetLastError();
-        h->pair_ab = nullptr;
         return MECUCO_ERR_OOM;
     }
-    CK(cudaMemcpy(h->pair_ab, host.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
-    h->pair_ab_k = k;
+    cudaError_t e = cudaMemcpy(d, host.data(), sizeof(int32_t) * host.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(d); set_err("cudaMemcpy", e); return MECUCO_ERR_CUDA; }
+    *slot = d;
     return MECUCO_OK;
+}
+
+mecuco_status ensure_pairs(mecuco_t h, int k) {
+    if (h->rowtab[k]) return MECUCO_OK;
+    std::vector<int32_t> host((size_t)moments_tc_rows(k));
+    moments_tc_build_rows(k, host.data());
+    return upload_table(&h->rowtab[k], host);
 }
 
 mecuco_status ensure_items(mecuco_t h, int k) {
-    if (h->m3_items_k == k) return MECUCO_OK;
-    if (h->m3_items) {
-        CK(cudaDeviceSynchronize());
-        cudaFree(h->m3_items);
-        h->m3_items = nullptr;
-        h->m3_items_k = -1;
-    }
-    int n = m3_items(k);
-    std::vector<int32_t> host((size_t)n);
+    if (h->m3_items[k]) return MECUCO_OK;
+    std::vector<int32_t> host((size_t)mecuco::m3_items(k));
     m3_build_items(k, host.data());
-    if (cudaMalloc(&h->m3_items, sizeof(int32_t) * n) != cudaSuccess) {
-        (void)cudaGetLastError();
-        h->m3_items = nullptr;
-        return MECUCO_ERR_OOM;
-    }
-    CK(cudaMemcpy(h->m3_items, host.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
-    h->m3_items_k = k;
-    return MECUCO_OK;
+    return upload_table(&h->m3_items[k], host);
 }
 
 struct EstBufs {
-    float *G, *R, *Q, *M, *sig, *U;
+    float *G, *R, *Q, *M, *sig, *U, *U0;
 };
 void est_scratch(Carver &c, int64_t chunk, int k, EstBufs *b) {
     b->G = c.take<float>((size_t)chunk * k * k);
@@ -350,10 +345,11 @@ void est_scratch(Carver &c, int64_t chunk, int k, EstBufs *b) {
     b->M = c.take<float>((size_t)chunk * m3_pair_floats(k));
     b->sig = c.take<float>((size_t)chunk * k);
     b->U = c.take<float>((size_t)chunk * k * k);
+    b->U0 = c.take<float>((size_t)chunk * k * k);
 }
 
 int64_t est_chunk(mecuco_t h, int64_t nrows, int k) {
-    const int64_t per_point = m3_pair_floats(k) + 3LL * k * k + 3LL * k;
+    const int64_t per_point = m3_pair_floats(k) + 4LL * k * k + 3LL * k;
     int64_t chunk = h->chunk_points;
     if (chunk <= 0) {
         chunk = (int64_t)(((size_t)2 << 30) / (per_point * sizeof(float)));
@@ -362,59 +358,173 @@ int64_t est_chunk(mecuco_t h, int64_t nrows, int k) {
     return std::min(chunk, nrows);
 }
 
-mecuco_status run_curvature(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, int k,
-                            const int32_t *idx, int include_self, mecuco_variant var, mecuco_precision prec,
+// Workspace bytes of run_curvature for nrows query rows (idx given, or
+// computed into the front of the workspace).
+size_t curvature_bytes(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, int k,
+                       bool idx_given, int64_t nrows, mecuco_precision prec) {
+    const int64_t chunk = est_chunk(h, nrows, k);
+    const size_t idx_bytes = idx_given ? 0 : align_up((size_t)nrows * k * sizeof(int32_t), 256);
+    size_t need = idx_given ? 0 : knn_bytes(h, X, dt, N, m, ld, nrows, k, prec, idx_bytes);
+    Carver c(nullptr, idx_bytes);
+    EstBufs b;
+    est_scratch(c, chunk, k, &b);
+    return std::max(need, c.off);
+}
+
+// Curvature of query rows [rb, re): kNN (unless idx is given), then per chunk
+// moments -> eigensolve -> estimator.  Scratch at ws, sized by the caller with
+// curvature_bytes; the per-k tables must exist (ensure_items / ensure_pairs).
+mecuco_status run_curvature(mecuco_t h, char *ws, const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
+                            int k, const int32_t *idx, int include_self, mecuco_variant var, mecuco_precision prec,
                             int64_t rb, int64_t re, float *kappa_out, float *lambda_out, float *U_out,
                             float *s_out, cudaStream_t s) {
-    mecuco_status st = ensure_items(h, k);
-    if (st != MECUCO_OK) return st;
+    mecuco_status st = MECUCO_OK;
     const bool tc_moments = prec == MECUCO_PREC_BF16_MIXED;
-    if (tc_moments && (st = ensure_pairs(h, k)) != MECUCO_OK) return st;
+    if (!h->m3_items[k] || (tc_moments && !h->rowtab[k])) return MECUCO_ERR_INVALID_ARG;
     const int64_t nrows = re - rb;
     const int64_t chunk = est_chunk(h, nrows, k);
-    // workspace: [idx of the range, if computed here] then kNN scratch, reused by the estimator
     const size_t idx_bytes = idx ? 0 : align_up((size_t)nrows * k * sizeof(int32_t), 256);
-    size_t need = idx ? 0 : knn_bytes(h, X, dt, N, m, ld, nrows, k, prec, idx_bytes);
-    {
-        Carver c(nullptr, idx_bytes);
-        EstBufs b;
-        est_scratch(c, chunk, k, &b);
-        need = std::max(need, c.off);
-    }
-    st = ensure(h->ws, h->ws_bytes, need);
-    if (st != MECUCO_OK) return st;
     const int32_t *nbr = idx;
     if (!idx) {
-        int32_t *idx_buf = reinterpret_cast<int32_t *>(h->ws);
-        st = run_knn(h, X, dt, N, m, ld, k, include_self, prec, rb, re, idx_buf, nullptr, s, idx_bytes);
+        int32_t *idx_buf = reinterpret_cast<int32_t *>(ws);
+        st = run_knn(h, ws, X, dt, N, m, ld, k, include_self, prec, rb, re, idx_buf, nullptr, s, idx_bytes);
         if (st != MECUCO_OK) return st;
         nbr = idx_buf;
     }
-    Carver c(h->ws, idx_bytes);
+    Carver c(ws, idx_bytes);
     EstBufs b;
     est_scratch(c, chunk, k, &b);
     const int fp64 = h->jacobi_fp64 >= 0 ? h->jacobi_fp64 : (prec == MECUCO_PREC_BF16_MIXED ? 1 : 0);
+    const float *Qarg = var == MECUCO_FAST_HAAR ? b.Q : nullptr;
     for (int64_t p0 = 0; p0 < nrows; p0 += chunk) {
         const int64_t np = std::min(chunk, nrows - p0);
         const int32_t *nb = nbr + p0 * k;
-        float *Ud = U_out ? U_out + p0 * (int64_t)k * k : b.U;
         if (tc_moments) {
+            // BF16-mixed: moments of X_c on the tensor cores, eigenpairs of its Gram
+            float *Ud = U_out ? U_out + p0 * (int64_t)k * k : b.U;
             LAUNCH(h, MECUCO_STAGE_MOMENTS, s,
-                   launch_moments_tc(X, dt, N, m, ld, nb, k, np, h->pair_ab, b.M, b.G, b.R,
+                   launch_moments_tc(X, dt, N, m, ld, nb, k, np, h->rowtab[k], b.M, b.G, b.R,
                                      var == MECUCO_FAST_HAAR ? b.Q : nullptr, h->ctr, s));
+            LAUNCH(h, MECUCO_STAGE_JACOBI, s,
+                   launch_jacobi(b.G, k, np, fp64, h->jacobi_max_sweeps, b.sig, Ud, h->ctr, s));
+            if (fp64 == 1 || fp64 == 3) ++h->launches;  // the FP64 refinement is a second kernel
+            LAUNCH(h, MECUCO_STAGE_ESTIMATOR, s,
+                   launch_estimator(b.sig, Ud, b.M, b.R, Qarg, k, m, np, (int)var, rank_eps_gram32(m), kappa_out + p0,
+                                    lambda_out ? lambda_out + p0 * k : nullptr, s_out ? s_out + p0 * k : nullptr,
+                                    h->ctr, s));
         } else {
+            // plain FP32: moments of the rotated patch Z = U0^T X_c (U0 = FP64-refined
+            // eigenvectors of the FP32 Gram; K is invariant under the rotation and the
+            // nearly diagonal Gram of Z resolves small eigenvalues), then its eigenpairs
             LAUNCH(h, MECUCO_STAGE_GRAM, s,
-                   launch_patch_gram(X, dt, N, m, ld, nb, k, 0, np, nullptr, b.G, b.R,
-                                     var == MECUCO_FAST_HAAR ? b.Q : nullptr, h->ctr, s));
+                   launch_patch_gram(X, dt, N, m, ld, nb, k, 0, np, nullptr, b.G, b.R, nullptr, h->ctr, s));
+            LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(b.G, k, np, 1, h->jacobi_max_sweeps, b.sig, b.U0, h->ctr, s));
+            ++h->launches;
+            LAUNCH(h, MECUCO_STAGE_GRAM, s,
+                   launch_patch_gram(X, dt, N, m, ld, nb, k, 0, np, b.U0, b.G, b.R, var == MECUCO_FAST_HAAR ? b.Q : nullptr,
+                                     h->ctr, s));
             LAUNCH(h, MECUCO_STAGE_MOMENTS, s,
-                   launch_patch_m3(X, dt, N, m, ld, nb, k, 0, np, nullptr, b.M, h->m3_items, h->ctr, s));
+                   launch_patch_m3(X, dt, N, m, ld, nb, k, 0, np, b.U0, b.M, h->m3_items[k], h->ctr, s));
+            LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(b.G, k, np, fp64, h->jacobi_max_sweeps, b.sig, b.U, h->ctr, s));
+            if (fp64 == 1 || fp64 == 3) ++h->launches;
+            LAUNCH(h, MECUCO_STAGE_ESTIMATOR, s,
+                   launch_estimator(b.sig, b.U, b.M, b.R, Qarg, k, m, np, (int)var, rank_eps_rotated(k, m),
+                                    kappa_out + p0, lambda_out ? lambda_out + p0 * k : nullptr,
+                                    s_out ? s_out + p0 * k : nullptr, h->ctr, s));
+            if (U_out) LAUNCH(h, MECUCO_STAGE_JACOBI, s,
+                              launch_compose_rotation(b.U0, b.U, k, np, U_out + p0 * (int64_t)k * k, s));
         }
-        LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(b.G, k, np, fp64, h->jacobi_max_sweeps, b.sig, Ud, h->ctr, s));
-        if (fp64 == 1 || fp64 == 3) ++h->launches;  // the FP64 refinement is a second kernel
-        LAUNCH(h, MECUCO_STAGE_ESTIMATOR, s,
-               launch_estimator(b.sig, Ud, b.M, b.R, b.Q, k, m, np, (int)var, kappa_out + p0,
-                                lambda_out ? lambda_out + p0 * k : nullptr, s_out ? s_out + p0 * k : nullptr, h->ctr,
-                                s));
+    }
+    return MECUCO_OK;
+}
+
+// ---- batched entry point -----------------------------------------------------
+mecuco_status check_set(const mecuco_dataset &d, int include_self) {
+    if (!d.X || !d.kappa) return MECUCO_ERR_INVALID_ARG;
+    if (d.N < 2 || d.N >= ((int64_t)1 << 31) || d.m < 1 || d.ld < d.m) return MECUCO_ERR_INVALID_ARG;
+    if (d.k < 2 || d.k > 64 || (int64_t)d.k > d.N - (include_self ? 0 : 1)) return MECUCO_ERR_INVALID_ARG;
+    return MECUCO_OK;
+}
+
+std::tuple<int, int64_t, int64_t, int64_t, int, int> batch_signature(const mecuco_dataset *sets, int nsets,
+                                                                     mecuco_dtype dt, mecuco_precision prec) {
+    int64_t sn = 0, sm = 0, sk = 0;
+    for (int i = 0; i < nsets; ++i) { sn += sets[i].N; sm += sets[i].m; sk += sets[i].k; }
+    return std::make_tuple(nsets, sn, sm, sk, (int)dt, (int)prec);
+}
+
+mecuco_status run_batched(mecuco_t h, const mecuco_dataset *sets, int nsets, mecuco_dtype dt, int include_self,
+                          mecuco_variant var, mecuco_precision prec, cudaStream_t s, int lanes) {
+    mecuco_status st;
+    for (int i = 0; i < nsets; ++i) {
+        if ((st = ensure_items(h, sets[i].k)) != MECUCO_OK) return st;
+        if (prec == MECUCO_PREC_BF16_MIXED && (st = ensure_pairs(h, sets[i].k)) != MECUCO_OK) return st;
+    }
+    lanes = std::max(1, std::min(lanes, std::min(nsets, 32)));
+    // longest first onto the least-loaded lane (cost: kNN N^2 m + moments N k^2 m)
+    std::vector<int> order(nsets);
+    std::iota(order.begin(), order.end(), 0);
+    std::vector<double> cost(nsets);
+    for (int i = 0; i < nsets; ++i) {
+        const double N = (double)sets[i].N, m = (double)sets[i].m, k = (double)sets[i].k;
+        cost[i] = N * N * m + N * k * k * m;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<double> load(lanes, 0.0);
+    std::vector<int> lane_of(nsets);
+    std::vector<size_t> lane_bytes(lanes, 0), set_idx_bytes(nsets);
+    for (int i : order) {
+        const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        load[l] += cost[i];
+        lane_of[i] = l;
+        const mecuco_dataset &d = sets[i];
+        set_idx_bytes[i] = d.idx ? 0 : align_up((size_t)d.N * d.k * sizeof(int32_t), 256);
+        const size_t need = set_idx_bytes[i] + std::max(knn_bytes(h, d.X, dt, d.N, d.m, d.ld, d.N, d.k, prec, 0),
+                                                        curvature_bytes(h, d.X, dt, d.N, d.m, d.ld, d.k, true, d.N,
+                                                                        prec));
+        lane_bytes[l] = std::max(lane_bytes[l], align_up(need, 256));
+    }
+    std::vector<size_t> lane_off(lanes, 0);
+    size_t total = 0;
+    for (int l = 0; l < lanes; ++l) { lane_off[l] = total; total += lane_bytes[l]; }
+    if ((st = ensure(h->bws, h->bws_bytes, total)) != MECUCO_OK) return st;
+    for (int l = 0; l < lanes; ++l) {
+        if (!h->lane_stream[l]) CK(cudaStreamCreateWithFlags(&h->lane_stream[l], cudaStreamNonBlocking));
+        if (!h->lane_event[l]) CK(cudaEventCreateWithFlags(&h->lane_event[l], cudaEventDisableTiming));
+    }
+    if (!h->fork_event) CK(cudaEventCreateWithFlags(&h->fork_event, cudaEventDisableTiming));
+    CK(cudaEventRecord(h->fork_event, s));
+    for (int l = 0; l < lanes; ++l) CK(cudaStreamWaitEvent(h->lane_stream[l], h->fork_event, 0));
+    for (int i : order) {
+        const mecuco_dataset &d = sets[i];
+        cudaStream_t ls = h->lane_stream[lane_of[i]];
+        char *ws = h->bws + lane_off[lane_of[i]];
+        int32_t *idx = d.idx ? d.idx : reinterpret_cast<int32_t *>(ws);
+        const size_t ib = set_idx_bytes[i];
+        if ((st = run_knn(h, ws + ib, d.X, dt, d.N, d.m, d.ld, d.k, include_self, prec, 0, d.N, idx, nullptr, ls, 0)) !=
+            MECUCO_OK)
+            return st;
+        if ((st = run_curvature(h, ws + ib, d.X, dt, d.N, d.m, d.ld, d.k, idx, include_self, var, prec, 0, d.N,
+                                d.kappa, nullptr, nullptr, nullptr, ls)) != MECUCO_OK)
+            return st;
+    }
+    for (int l = 0; l < lanes; ++l) {
+        CK(cudaEventRecord(h->lane_event[l], h->lane_stream[l]));
+        CK(cudaStreamWaitEvent(s, h->lane_event[l], 0));
+    }
+    return MECUCO_OK;
+}
+
+mecuco_status check_batch(mecuco_t h, const mecuco_dataset *sets, int nsets, mecuco_dtype dt, int include_self,
+                          mecuco_variant var, mecuco_precision prec) {
+    if (!h || !sets || nsets < 1) return MECUCO_ERR_INVALID_ARG;
+    if (dt != MECUCO_F32 && dt != MECUCO_BF16) return MECUCO_ERR_INVALID_ARG;
+    if (include_self != 0 && include_self != 1) return MECUCO_ERR_INVALID_ARG;
+    if (var != MECUCO_FAST_LITERAL && var != MECUCO_FAST_HAAR) return MECUCO_ERR_INVALID_ARG;
+    if (prec != MECUCO_PREC_FP32 && prec != MECUCO_PREC_BF16_MIXED) return MECUCO_ERR_INVALID_ARG;
+    for (int i = 0; i < nsets; ++i) {
+        mecuco_status st = check_set(sets[i], include_self);
+        if (st != MECUCO_OK) return st;
     }
     return MECUCO_OK;
 }
@@ -478,8 +588,16 @@ mecuco_status mecuco_destroy(mecuco_t h) {
     if (h->ws) cudaFree(h->ws);
     if (h->io) cudaFree(h->io);
     if (h->ctr) cudaFree(h->ctr);
-    if (h->m3_items) cudaFree(h->m3_items);
-    if (h->pair_ab) cudaFree(h->pair_ab);
+    for (int kk = 0; kk <= 64; ++kk) {
+        if (h->m3_items[kk]) cudaFree(h->m3_items[kk]);
+        if (h->rowtab[kk]) cudaFree(h->rowtab[kk]);
+    }
+    if (h->bws) cudaFree(h->bws);
+    for (int i = 0; i < 32; ++i) {
+        if (h->lane_stream[i]) cudaStreamDestroy(h->lane_stream[i]);
+        if (h->lane_event[i]) cudaEventDestroy(h->lane_event[i]);
+    }
+    if (h->fork_event) cudaEventDestroy(h->fork_event);
     delete h;
     return MECUCO_OK;
 }
@@ -515,6 +633,10 @@ mecuco_status mecuco_set_option(mecuco_t h, mecuco_option opt, int64_t v) {
             if (v < 0 || v > 64) return MECUCO_ERR_INVALID_ARG;
             h->knn_splits = (int)v;
             break;
+        case MECUCO_OPT_BATCH_LANES:
+            if (v < 1 || v > 32) return MECUCO_ERR_INVALID_ARG;
+            h->batch_lanes = (int)v;
+            break;
         default: return MECUCO_ERR_INVALID_ARG;
     }
     return MECUCO_OK;
@@ -532,7 +654,7 @@ mecuco_status mecuco_knn_range(mecuco_t h, const void *X, mecuco_dtype dt, int64
     if ((st = begin_call(h, s)) != MECUCO_OK) return st;
     if ((st = ensure(h->ws, h->ws_bytes, knn_bytes(h, X, dt, N, m, ld, re - rb, k, prec, 0))) != MECUCO_OK)
         return st;
-    return run_knn(h, X, dt, N, m, ld, k, include_self, prec, rb, re, idx_out, dist_out, s, 0);
+    return run_knn(h, h->ws, X, dt, N, m, ld, k, include_self, prec, rb, re, idx_out, dist_out, s, 0);
 }
 
 mecuco_status mecuco_knn(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, int k,
@@ -552,8 +674,13 @@ mecuco_status mecuco_curvature_range(mecuco_t h, const void *X, mecuco_dtype dt,
     if (prec != MECUCO_PREC_FP32 && prec != MECUCO_PREC_BF16_MIXED) return MECUCO_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = begin_call(h, s)) != MECUCO_OK) return st;
-    return run_curvature(h, X, dt, N, m, ld, k, idx, include_self, var, prec, rb, re, kappa_out, lambda_out, U_out,
-                         s_out, s);
+    if ((st = ensure_items(h, k)) != MECUCO_OK) return st;
+    if (prec == MECUCO_PREC_BF16_MIXED && (st = ensure_pairs(h, k)) != MECUCO_OK) return st;
+    if ((st = ensure(h->ws, h->ws_bytes, curvature_bytes(h, X, dt, N, m, ld, k, idx != nullptr, re - rb, prec))) !=
+        MECUCO_OK)
+        return st;
+    return run_curvature(h, h->ws, X, dt, N, m, ld, k, idx, include_self, var, prec, rb, re, kappa_out, lambda_out,
+                         U_out, s_out, s);
 }
 
 mecuco_status mecuco_curvature(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, int k,
@@ -573,7 +700,7 @@ mecuco_status mecuco_curvature_backward(mecuco_t h, const void *X, mecuco_dtype 
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = begin_call(h, s)) != MECUCO_OK) return st;
     if ((st = ensure_items(h, k)) != MECUCO_OK) return st;
-    // per point: forward buffers + U0 + dG, dR, dQ + C and dM (k^3 each)
+    // per point: forward buffers (incl. U0) + dG, dR, dQ + C and dM (k^3 each)
     const int64_t per_point = m3_pair_floats(k) + 7LL * k * k + 4LL * k + 2LL * k * k * k;
     int64_t chunk = h->chunk_points > 0 ? h->chunk_points
                                          : std::max<int64_t>(256, std::min<int64_t>(65536, ((int64_t)2 << 30) /
@@ -583,7 +710,6 @@ mecuco_status mecuco_curvature_backward(mecuco_t h, const void *X, mecuco_dtype 
     EstBufs b;
     est_scratch(t, chunk, k, &b);
     t.take<float>((size_t)chunk * k * k);
-    t.take<float>((size_t)chunk * k * k);
     t.take<float>((size_t)chunk * k);
     t.take<float>((size_t)chunk * k * k);
     t.take<float>((size_t)chunk * k * k * k);
@@ -591,7 +717,7 @@ mecuco_status mecuco_curvature_backward(mecuco_t h, const void *X, mecuco_dtype 
     if ((st = ensure(h->ws, h->ws_bytes, t.off)) != MECUCO_OK) return st;
     Carver c(h->ws);
     est_scratch(c, chunk, k, &b);
-    float *U0 = c.take<float>((size_t)chunk * k * k);
+    float *U0 = b.U0;
     float *dG = c.take<float>((size_t)chunk * k * k);
     float *dR = c.take<float>((size_t)chunk * k);
     float *dQ = c.take<float>((size_t)chunk * k * k);
@@ -614,12 +740,12 @@ mecuco_status mecuco_curvature_backward(mecuco_t h, const void *X, mecuco_dtype 
         LAUNCH(h, MECUCO_STAGE_GRAM, s,
                launch_patch_gram(X, dt, N, m, ld, nb, k, 0, np, U0, b.G, b.R, need_q ? b.Q : nullptr, h->ctr, s));
         LAUNCH(h, MECUCO_STAGE_MOMENTS, s,
-               launch_patch_m3(X, dt, N, m, ld, nb, k, 0, np, U0, b.M, h->m3_items, h->ctr, s));
+               launch_patch_m3(X, dt, N, m, ld, nb, k, 0, np, U0, b.M, h->m3_items[k], h->ctr, s));
         LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(b.G, k, np, rot_mode, h->jacobi_max_sweeps, b.sig, b.U, h->ctr, s));
         if (rot_mode == 1 || rot_mode == 3) ++h->launches;  // the refinement kernel
         LAUNCH(h, MECUCO_STAGE_ADJOINT, s,
-               launch_adjoint(X, dt, N, m, ld, nb, k, np, (int)var, U0, b.sig, b.U, b.M, b.R, b.Q, dkappa + p0, dG, dR,
-                              dQ, Cb, dM, dX_out, m, s));
+               launch_adjoint(X, dt, N, m, ld, nb, k, np, (int)var, rank_eps_rotated(k, m), U0, b.sig, b.U, b.M, b.R,
+                              b.Q, dkappa + p0, dG, dR, dQ, Cb, dM, dX_out, m, s));
         ++h->launches;  // two kernels
     }
     return MECUCO_OK;
@@ -655,9 +781,58 @@ mecuco_status mecuco_tangent_basis(mecuco_t h, const void *X, mecuco_dtype dt, i
         LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(G, k, np, mode, h->jacobi_max_sweeps, sig, U, h->ctr, s));
         if (mode == 1 || mode == 3) ++h->launches;
         LAUNCH(h, MECUCO_STAGE_BASIS, s,
-               launch_tangent_basis(X, dt, N, m, ld, nb, k, np, sig, U, d_out, V_out + (p0 - rb) * m * (int64_t)d_out,
-                                    h->ctr, s));
+               launch_tangent_basis(X, dt, N, m, ld, nb, k, np, sig, U, d_out, rank_eps_gram32(m),
+                                    V_out + (p0 - rb) * m * (int64_t)d_out, h->ctr, s));
     }
+    return MECUCO_OK;
+}
+
+mecuco_status mecuco_curvature_batched(mecuco_t h, const mecuco_dataset *sets, int nsets, mecuco_dtype dt,
+                                       int include_self, mecuco_variant var, mecuco_precision prec, void *stream) {
+    mecuco_status st = check_batch(h, sets, nsets, dt, include_self, var, prec);
+    if (st != MECUCO_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = begin_call(h, s)) != MECUCO_OK) return st;
+    auto it = h->tuned_lanes.find(batch_signature(sets, nsets, dt, prec));
+    const int lanes = it != h->tuned_lanes.end() ? it->second : h->batch_lanes;
+    return run_batched(h, sets, nsets, dt, include_self, var, prec, s, lanes);
+}
+
+mecuco_status mecuco_autotune_batched(mecuco_t h, const mecuco_dataset *sets, int nsets, mecuco_dtype dt,
+                                      int include_self, mecuco_variant var, mecuco_precision prec, void *stream,
+                                      int *lanes_out) {
+    mecuco_status st = check_batch(h, sets, nsets, dt, include_self, var, prec);
+    if (st != MECUCO_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int best = 1;
+    float best_ms = 0.f;
+    const int cand[] = {32, 16, 8, 4, 2, 1};  // the largest first: it sizes the workspace once
+    bool warmed = false;
+    for (int L : cand) {
+        if (L > nsets && L != 1) continue;
+        if ((st = begin_call(h, s)) != MECUCO_OK) break;
+        if (!warmed) {
+            if ((st = run_batched(h, sets, nsets, dt, include_self, var, prec, s, L)) != MECUCO_OK) break;
+            warmed = true;
+        }
+        if (cudaEventRecord(e0, s) != cudaSuccess) { st = MECUCO_ERR_CUDA; break; }
+        if ((st = run_batched(h, sets, nsets, dt, include_self, var, prec, s, L)) != MECUCO_OK) break;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+            st = MECUCO_ERR_CUDA;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best_ms == 0.f || ms < best_ms) { best_ms = ms; best = L; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != MECUCO_OK) return st;
+    h->tuned_lanes[batch_signature(sets, nsets, dt, prec)] = best;
+    if (lanes_out) *lanes_out = best;
     return MECUCO_OK;
 }
 
@@ -683,10 +858,15 @@ mecuco_status mecuco_curvature_host(mecuco_t h, const void *X_host, mecuco_dtype
     float *kd = c.take<float>((size_t)N);
     int32_t *id = c.take<int32_t>((size_t)N * k);
     CK(cudaMemcpyAsync(Xd, X_host, xbytes, cudaMemcpyHostToDevice, s));
-    if ((st = ensure(h->ws, h->ws_bytes, knn_bytes(h, Xd, dt, N, m, ld, N, k, prec, 0))) != MECUCO_OK) return st;
-    if ((st = run_knn(h, Xd, dt, N, m, ld, k, include_self, prec, 0, N, id, nullptr, s, 0)) != MECUCO_OK) return st;
-    if ((st = run_curvature(h, Xd, dt, N, m, ld, k, id, include_self, var, prec, 0, N, kd, nullptr, nullptr, nullptr,
-                            s)) != MECUCO_OK)
+    if ((st = ensure_items(h, k)) != MECUCO_OK) return st;
+    if (prec == MECUCO_PREC_BF16_MIXED && (st = ensure_pairs(h, k)) != MECUCO_OK) return st;
+    const size_t need = std::max(knn_bytes(h, Xd, dt, N, m, ld, N, k, prec, 0),
+                                 curvature_bytes(h, Xd, dt, N, m, ld, k, true, N, prec));
+    if ((st = ensure(h->ws, h->ws_bytes, need)) != MECUCO_OK) return st;
+    if ((st = run_knn(h, h->ws, Xd, dt, N, m, ld, k, include_self, prec, 0, N, id, nullptr, s, 0)) != MECUCO_OK)
+        return st;
+    if ((st = run_curvature(h, h->ws, Xd, dt, N, m, ld, k, id, include_self, var, prec, 0, N, kd, nullptr, nullptr,
+                            nullptr, s)) != MECUCO_OK)
         return st;
     CK(cudaMemcpyAsync(kappa_host_out, kd, sizeof(float) * N, cudaMemcpyDeviceToHost, s));
     if (idx_host_out) CK(cudaMemcpyAsync(idx_host_out, id, sizeof(int32_t) * N * k, cudaMemcpyDeviceToHost, s));

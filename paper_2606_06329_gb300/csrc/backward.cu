@@ -47,7 +47,7 @@ constexpr int BW_SMEM_FLOATS = 5 * 64 * 65;
 __global__ void __launch_bounds__(256)
 adjoint_kspace_kernel(const float *__restrict__ sigma, const float *__restrict__ U, const float *__restrict__ M,
                       const float *__restrict__ R, const float *__restrict__ Q, const float *__restrict__ gk, int k,
-                      int64_t m, int variant, float *__restrict__ dG, float *__restrict__ dR, float *__restrict__ dQ,
+                      int64_t m, int variant, float rank_eps, float *__restrict__ dG, float *__restrict__ dR, float *__restrict__ dQ,
                       float *__restrict__ Cout, float *__restrict__ dMbuf) {
     extern __shared__ float bsm[];
     float(*Ws)[65] = reinterpret_cast<float(*)[65]>(bsm);             // W[r][l]
@@ -69,9 +69,8 @@ adjoint_kspace_kernel(const float *__restrict__ sigma, const float *__restrict__
         int pmax = k - 1;
         if ((int64_t)pmax > m) pmax = (int)m;
         const float s0 = fmaxf(sg[0], 0.f);
-        const float eps_rank = 8.f * sqrtf((float)m) * 5.9604644775390625e-08f;
         int rank = 0;
-        for (int l = 0; l < k; ++l) rank += (sg[l] > eps_rank * s0) && (sg[l] > 0.f);
+        for (int l = 0; l < k; ++l) rank += (sg[l] > rank_eps * s0) && (sg[l] > 0.f);
         s_p = rank < pmax ? rank : pmax;
     }
     __syncthreads();
@@ -381,15 +380,16 @@ adjoint_patch_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, 
 }
 
 cudaError_t launch_adjoint(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, const int32_t *idx,
-                           int k, int64_t np, int variant, const float *rot, const float *sigma, const float *U,
-                           const float *M, const float *R, const float *Q, const float *gk, float *dG, float *dR,
-                           float *dQ, float *C, float *dMbuf, float *dX, int64_t ldd, cudaStream_t s) {
+                           int k, int64_t np, int variant, float rank_eps, const float *rot, const float *sigma,
+                           const float *U, const float *M, const float *R, const float *Q, const float *gk, float *dG,
+                           float *dR, float *dQ, float *C, float *dMbuf, float *dX, int64_t ldd, cudaStream_t s) {
     if (np <= 0) return cudaSuccess;
     if (k > 64) return cudaErrorInvalidValue;
     const size_t smem = BW_SMEM_FLOATS * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(adjoint_kspace_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    adjoint_kspace_kernel<<<(unsigned)np, 256, smem, s>>>(sigma, U, M, R, Q, gk, k, m, variant, dG, dR, dQ, C, dMbuf);
+    adjoint_kspace_kernel<<<(unsigned)np, 256, smem, s>>>(sigma, U, M, R, Q, gk, k, m, variant, rank_eps, dG, dR, dQ, C,
+                                                          dMbuf);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t psmem = (size_t)(2 * 64 * 33 + 2 * 64 * 64 + 64 * 65) * sizeof(float);

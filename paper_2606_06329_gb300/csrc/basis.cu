@@ -22,7 +22,7 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 tangent_basis_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, const int32_t *__restrict__ idx,
                      int k, const float *__restrict__ sigma, const float *__restrict__ U, int d_out,
-                     float *__restrict__ V, DevCounters *ctr) {
+                     float rank_eps, float *__restrict__ V, DevCounters *ctr) {
     __shared__ float Xs[64][TB_CH + 1];
     __shared__ float Us[64][65];  // U[j][l] * sign_l / s_l for l < d_out (0 for l >= p)
     __shared__ float scale[64];
@@ -42,9 +42,8 @@ tangent_basis_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, 
             int pmax = k - 1;
             if ((int64_t)pmax > m) pmax = (int)m;
             const float s0 = fmaxf(sg[0], 0.f);
-            const float eps_rank = 8.f * sqrtf((float)m) * 5.9604644775390625e-08f;
             int rank = 0;
-            for (int l = 0; l < k; ++l) rank += (sg[l] > eps_rank * s0) && (sg[l] > 0.f);
+            for (int l = 0; l < k; ++l) rank += (sg[l] > rank_eps * s0) && (sg[l] > 0.f);
             const int p = rank < pmax ? rank : pmax;
             if (tid < p) {
                 float best = -1.f, sgn = 1.f;
@@ -90,15 +89,42 @@ tangent_basis_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, 
 
 cudaError_t launch_tangent_basis(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
                                  const int32_t *idx, int k, int64_t np, const float *sigma, const float *U,
-                                 int d_out, float *V, DevCounters *ctr, cudaStream_t s) {
+                                 int d_out, float rank_eps, float *V, DevCounters *ctr, cudaStream_t s) {
     if (np <= 0) return cudaSuccess;
     if (k > 64 || d_out < 1 || d_out > k) return cudaErrorInvalidValue;
     if (dt == MECUCO_BF16)
         tangent_basis_kernel<<<(unsigned)np, 256, 0, s>>>((const __nv_bfloat16 *)X, N, m, ld, idx, k, sigma, U, d_out,
-                                                          V, ctr);
+                                                          rank_eps, V, ctr);
     else
-        tangent_basis_kernel<<<(unsigned)np, 256, 0, s>>>((const float *)X, N, m, ld, idx, k, sigma, U, d_out, V,
-                                                          ctr);
+        tangent_basis_kernel<<<(unsigned)np, 256, 0, s>>>((const float *)X, N, m, ld, idx, k, sigma, U, d_out,
+                                                          rank_eps, V, ctr);
+    return cudaGetLastError();
+}
+
+// U_out = U0 V per point: one CTA (256 threads) per point.
+__global__ void __launch_bounds__(256)
+compose_rotation_kernel(const float *__restrict__ U0, const float *__restrict__ V, int k, float *__restrict__ U_out) {
+    __shared__ float A[64][65], B[64][65];
+    const int64_t pt = blockIdx.x;
+    const int kk = k * k;
+    for (int e = threadIdx.x; e < kk; e += 256) {
+        A[e / k][e % k] = U0[pt * kk + e];
+        B[e / k][e % k] = V[pt * kk + e];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kk; e += 256) {
+        const int r = e / k, l = e % k;
+        float t = 0.f;
+        for (int c = 0; c < k; ++c) t = fmaf(A[r][c], B[c][l], t);
+        U_out[pt * kk + e] = t;
+    }
+}
+
+cudaError_t launch_compose_rotation(const float *U0, const float *V, int k, int64_t np, float *U_out,
+                                    cudaStream_t s) {
+    if (np <= 0) return cudaSuccess;
+    if (k > 64) return cudaErrorInvalidValue;
+    compose_rotation_kernel<<<(unsigned)np, 256, 0, s>>>(U0, V, k, U_out);
     return cudaGetLastError();
 }
 

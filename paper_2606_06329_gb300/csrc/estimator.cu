@@ -32,8 +32,8 @@ constexpr int EST_SMEM = 3 * 64 * 65 * (int)sizeof(float);
 __global__ void __launch_bounds__(256)
 estimator_kernel(const float *__restrict__ sigma, const float *__restrict__ U, const float *__restrict__ M,
                  const float *__restrict__ R, const float *__restrict__ Q, int k, int64_t m, int variant,
-                 float *__restrict__ kappa, float *__restrict__ lambda_out, float *__restrict__ s_out,
-                 DevCounters *ctr) {
+                 float rank_eps, float *__restrict__ kappa, float *__restrict__ lambda_out,
+                 float *__restrict__ s_out, DevCounters *ctr) {
     extern __shared__ float esm[];
     float(*Ws)[65] = reinterpret_cast<float(*)[65]>(esm);            // W[r][l], zero for l >= p
     float(*Mj)[65] = reinterpret_cast<float(*)[65]>(esm + 64 * 65);
@@ -48,11 +48,10 @@ estimator_kernel(const float *__restrict__ sigma, const float *__restrict__ U, c
         int pmax = k - 1;
         if ((int64_t)pmax > m) pmax = (int)m;
         float s0 = fmaxf(sg[0], 0.f);
-        // FP32 rounding of the Gram perturbs its eigenvalues by ~sqrt(m) 2^-24 s_0;
-        // eigenvalues below 8x that scale are indistinguishable from zero here
-        const float eps_rank = 8.f * sqrtf((float)m) * 5.9604644775390625e-08f;
+        // numerical rank: eigenvalues above rank_eps * s_0 (the caller's threshold
+        // for the accuracy of the Gram it solved)
         int rank = 0;
-        for (int l = 0; l < k; ++l) rank += (sg[l] > eps_rank * s0) && (sg[l] > 0.f);
+        for (int l = 0; l < k; ++l) rank += (sg[l] > rank_eps * s0) && (sg[l] > 0.f);
         s_p = rank < pmax ? rank : pmax;
         if (s_p < pmax) atomicAdd(&ctr->rank_deficient, 1ull);
     }
@@ -183,15 +182,15 @@ estimator_kernel(const float *__restrict__ sigma, const float *__restrict__ U, c
 }
 
 cudaError_t launch_estimator(const float *sigma, const float *U, const float *M, const float *R,
-                             const float *Q, int k, int64_t m, int64_t np, int variant,
+                             const float *Q, int k, int64_t m, int64_t np, int variant, float rank_eps,
                              float *kappa, float *lambda_out, float *s_out, DevCounters *ctr,
                              cudaStream_t s) {
     if (np <= 0) return cudaSuccess;
     if (k > 64) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(estimator_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, EST_SMEM);
     if (e != cudaSuccess) return e;
-    estimator_kernel<<<(unsigned)np, 256, EST_SMEM, s>>>(sigma, U, M, R, Q, k, m, variant, kappa, lambda_out,
-                                                         s_out, ctr);
+    estimator_kernel<<<(unsigned)np, 256, EST_SMEM, s>>>(sigma, U, M, R, Q, k, m, variant, rank_eps, kappa,
+                                                         lambda_out, s_out, ctr);
     return cudaGetLastError();
 }
 

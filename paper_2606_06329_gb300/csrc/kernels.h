@@ -1,6 +1,8 @@
 // kernels.h - host launchers of the MeCuCo CUDA kernels (internal, C++ linkage).
 #pragma once
 
+#include <math.h>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -112,16 +114,33 @@ cudaError_t launch_jacobi(const float *G, int k, int64_t np, int fp64, int max_s
 // launch_patch_gram (Q only for the Haar variant).  Writes kappa (np) and,
 // when not NULL, lambda_out (np x k) and the singular values s_out (np x k).
 cudaError_t launch_estimator(const float *sigma, const float *U, const float *M, const float *R,
-                             const float *Q, int k, int64_t m, int64_t np, int variant,
+                             const float *Q, int k, int64_t m, int64_t np, int variant, float rank_eps,
                              float *kappa, float *lambda_out, float *s_out, DevCounters *ctr,
                              cudaStream_t s);
+
+// Numerical-rank thresholds (eigenvalues kept above eps * s_0):
+//  - a Gram accumulated in FP32 (or from BF16 products) carries rounding of
+//    ~sqrt(m) 2^-24 s_0, so eigenvalues below 8x that are not resolved;
+//  - the Gram of a rotated patch (U0^T X_c, nearly diagonal) resolves small
+//    eigenvalues to relative accuracy ~2^-24 s_max/s_l, so it takes the FP64
+//    oracle's k m 2^-52, floored at 2^-40 above the rotation's own noise.
+inline float rank_eps_gram32(int64_t m) { return 8.f * sqrtf((float)m) * 5.9604644775390625e-08f; }
+inline float rank_eps_rotated(int k, int64_t m) {
+    const double e = (double)k * (double)m * 2.220446049250313e-16;
+    return (float)(e > 9.094947017729282e-13 ? e : 9.094947017729282e-13);
+}
+
+// U_out (np x k x k) = U0 V per point (the eigenvectors of a rotated Gram back
+// in the patch's own basis).
+cudaError_t launch_compose_rotation(const float *U0, const float *V, int k, int64_t np, float *U_out,
+                                    cudaStream_t s);
 
 // ---- tangent bases ------------------------------------------------------------
 // V (np x m x d_out, l fastest) = X_c^T U_p S^-1 for the points of one chunk
 // (idx offset to the chunk), sigma/U from launch_jacobi.
 cudaError_t launch_tangent_basis(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
                                  const int32_t *idx, int k, int64_t np, const float *sigma, const float *U,
-                                 int d_out, float *V, DevCounters *ctr, cudaStream_t s);
+                                 int d_out, float rank_eps, float *V, DevCounters *ctr, cudaStream_t s);
 
 // ---- adjoint ---------------------------------------------------------------
 // d(sum_i gk_i K_i)/dX for the points of one chunk (idx offset to the chunk),
@@ -130,8 +149,8 @@ cudaError_t launch_tangent_basis(const void *X, mecuco_dtype dt, int64_t N, int6
 // (rot = U0 per point, np x k x k); dG, dR, dQ (np x k x k, k, k x k), C and
 // dMbuf (np x k^3 each) are scratch.
 cudaError_t launch_adjoint(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, const int32_t *idx,
-                           int k, int64_t np, int variant, const float *rot, const float *sigma, const float *U,
-                           const float *M, const float *R, const float *Q, const float *gk, float *dG, float *dR,
-                           float *dQ, float *C, float *dMbuf, float *dX, int64_t ldd, cudaStream_t s);
+                           int k, int64_t np, int variant, float rank_eps, const float *rot, const float *sigma,
+                           const float *U, const float *M, const float *R, const float *Q, const float *gk, float *dG,
+                           float *dR, float *dQ, float *C, float *dMbuf, float *dX, int64_t ldd, cudaStream_t s);
 
 }  // namespace mecuco

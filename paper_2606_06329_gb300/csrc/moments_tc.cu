@@ -15,21 +15,24 @@
 // leave free carry the G and Q rows.  Two blocks form a 128-row MMA tile.
 // The host builds the table of row codes once per k.
 //
-// One CTA per patch: 16 "former" warps and one MMA warp.  The columns of the
-// patch are streamed in 64-column chunks.  The formers gather the k neighbour
-// rows (the next chunk's loads are in flight while the current chunk is
-// processed), centre each column in FP32, accumulate R and w, and keep the
-// chunk as packed BF16 pairs in shared memory and as the K-major, 128-byte-
-// swizzled B operand.  For every tile of the current pass each former thread
-// forms 16 products of its tile row (HMUL2 on BF16 pairs) and writes them with
-// tcgen05.st straight into a TMEM slot holding the A operand (four slots,
-// 64 K-columns each); the MMA warp issues tcgen05.mma with A in TMEM, B in
-// shared memory and FP32 accumulators in TMEM, and releases each slot with
-// tcgen05.commit.  TMEM holds the accumulators of up to 384/N tiles, so the
-// tiles are covered in passes over the columns (the patch is re-read from L2).
-// After a pass the formers read the accumulators back (tcgen05.ld) and store
-// each row to its destination.  Every wait is bounded (MECUCO_ERR_TIMEOUT,
-// no trap); the MMA warp waits for its last MMAs before TMEM is freed.
+// One CTA per patch, three warp roles connected by mbarriers:
+//   8 producer warps  gather the k neighbour rows of the next 64-column chunk
+//                     (loads in flight while the current chunk is processed),
+//                     centre each column in FP32, accumulate R and w, and
+//                     write the chunk as packed BF16 pairs and as the K-major,
+//                     128-byte-swizzled B operand (two buffers);
+//   8 former warps    for every tile of the current pass, each thread forms
+//                     32 products of its tile row (HMUL2 on BF16 pairs) and
+//                     writes them with tcgen05.st straight into a TMEM slot
+//                     holding the A operand (four slots of 64 K-columns);
+//   1 MMA warp        issues tcgen05.mma with A in TMEM, B in shared memory and
+//                     FP32 accumulators in TMEM, and releases each slot and
+//                     chunk buffer with tcgen05.commit.
+// TMEM holds the accumulators of up to 384/N tiles, so the tiles are covered
+// in passes over the columns (the patch is re-read from L2).  After a pass the
+// formers read the accumulators back (tcgen05.ld) and store each row to its
+// destination.  Every wait is bounded (MECUCO_ERR_TIMEOUT, no trap); the MMA
+// warp waits for its last MMAs before TMEM is freed.
 #include <math.h>
 
 #include <algorithm>
@@ -41,8 +44,9 @@
 namespace mecuco {
 
 namespace {
-constexpr int MT_FORMERS = 512;                        // 16 warps
-constexpr int MT_THREADS = MT_FORMERS + 32;            // + the MMA warp
+constexpr int MT_PRODUCER_WARPS = 8;                  // gather, centre, pack
+constexpr int MT_FORMER_WARPS = 8;                     // row products into TMEM, drain
+constexpr int MT_THREADS = (MT_PRODUCER_WARPS + MT_FORMER_WARPS + 1) * 32;  // + the MMA warp
 constexpr int MT_CH = 64;                              // columns per chunk
 constexpr int MT_SLOTS = 4;                            // A slots in TMEM
 constexpr int MT_SLOT_COLS = MT_CH / 2;                // 32-bit TMEM columns per slot
@@ -152,7 +156,7 @@ void moments_tc_build_rows(int k, int32_t *codes) {
 
 size_t moments_tc_smem_bytes(int k) {
     return 1024 + 2 * (size_t)MT_B_BYTES + 2 * (size_t)MT_XP_ROWS * MT_XP_LD * 4 + 64 * (size_t)MT_XS_LD * 4 +
-           8 * 64 * 4 + 64 * 4 + (size_t)moments_tc_rows(k) * 4;
+           4 * 64 * 4 + (size_t)moments_tc_rows(k) * 4;
 }
 
 template <typename T>
@@ -165,10 +169,10 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
     uint8_t *Bop0 = base;                                                       // 2 x B operand
     uint32_t *Xp0 = reinterpret_cast<uint32_t *>(base + 2 * MT_B_BYTES);        // 2 x [67][36] packed pairs
     float *Xs = reinterpret_cast<float *>(Xp0 + 2 * MT_XP_ROWS * MT_XP_LD);     // [64][68] FP32 staging
-    float *Part = Xs + 64 * MT_XS_LD;                                           // [8][64]
-    float *Rs = Part + 8 * 64;                                                  // [64]
-    int32_t *codes = reinterpret_cast<int32_t *>(Rs + 64);                      // [nrows]
-    __shared__ uint64_t slot_full[MT_SLOTS], slot_empty[MT_SLOTS], chunk_done[2], pass_done;
+    float *Part = Xs + 64 * MT_XS_LD;                                           // [4][64] column partials
+    int32_t *codes = reinterpret_cast<int32_t *>(Part + 4 * 64);                // [nrows]
+    __shared__ uint64_t slot_full[MT_SLOTS], slot_empty[MT_SLOTS];
+    __shared__ uint64_t chunk_ready[2], formers_done[2], chunk_done[2], pass_done, d_free;
     __shared__ uint32_t tmem_slot;
     __shared__ int rows[64];
     __shared__ int abort_flag, never;
@@ -191,7 +195,6 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
             if (r < 0 || (int64_t)r >= N) { atomicOr(&ctr->status, (unsigned)DEV_INVALID); r = 0; }
         }
         rows[tid] = r;
-        Rs[tid] = 0.f;
     }
     for (int e = tid; e < nrows; e += MT_THREADS) codes[e] = __ldg(rowtab + e);
     // constant rows of both packed buffers: ones (BF16 1.0 pairs) and zeros
@@ -202,12 +205,16 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
     }
     if (tid == 0) {
         for (int s = 0; s < MT_SLOTS; ++s) {
-            tc::mbar_init(tc::smem_u32(&slot_full[s]), MT_FORMERS / 32);
+            tc::mbar_init(tc::smem_u32(&slot_full[s]), MT_FORMER_WARPS);
             tc::mbar_init(tc::smem_u32(&slot_empty[s]), 1);
         }
-        tc::mbar_init(tc::smem_u32(&chunk_done[0]), 1);
-        tc::mbar_init(tc::smem_u32(&chunk_done[1]), 1);
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(tc::smem_u32(&chunk_ready[b]), 1);
+            tc::mbar_init(tc::smem_u32(&formers_done[b]), MT_FORMER_WARPS);
+            tc::mbar_init(tc::smem_u32(&chunk_done[b]), 1);
+        }
         tc::mbar_init(tc::smem_u32(&pass_done), 1);
+        tc::mbar_init(tc::smem_u32(&d_free), MT_FORMER_WARPS);
         abort_flag = (*(volatile unsigned *)&ctr->status & DEV_TIMEOUT) ? 1 : 0;
         never = 0;
         tc::fence_mbar_init();
@@ -225,161 +232,149 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
         atomicOr(&ctr->status, (unsigned)DEV_TIMEOUT);
         abort_flag = 1;
     };
+    auto wait = [&](uint64_t *bar, uint32_t parity) {
+        if (!*abortp && !tc::mbar_wait(tc::smem_u32(bar), parity, abortp, MT_WAIT)) fail();
+    };
 
-    if (warp == MT_FORMERS / 32) {
-        // ================= MMA warp (lane 0 issues) =================
-        uint32_t q = 0, gc = 0;
-        for (int ps = 0; ps < npass; ++ps) {
-            const int t0 = ps * tpp, nt = min(tpp, ntiles - t0);
-            if (lane == 0) {
-                for (int ci = 0; ci < nchunks; ++ci, ++gc) {
-                    const uint32_t bsa = tc::smem_u32(Bop0 + (gc & 1) * MT_B_BYTES);
-                    for (int t = 0; t < nt; ++t, ++q) {
-                        const int s = q % MT_SLOTS;
-                        if (!*abortp &&
-                            !tc::mbar_wait(tc::smem_u32(&slot_full[s]), (q / MT_SLOTS) & 1, abortp, MT_WAIT))
-                            fail();
-                        tc::fence_after();
-                        if (!*abortp) {
-                            const uint32_t a_t = tmem + (uint32_t)(MT_D_COLS + s * MT_SLOT_COLS);
+    if (warp < MT_PRODUCER_WARPS) {
+        // ================= producers: gather, centre, pack =================
+        const int ptid = tid;                                  // 0 .. 255
+        const int gr0 = ptid >> 3, gg = ptid & 7;              // gather units (row gr0 / gr0 + 32, group gg)
+        const T *grow0 = X + (int64_t)rows[gr0] * ld;
+        const T *grow1 = X + (int64_t)rows[gr0 + 32] * ld;
+        const bool live0 = gr0 < k, live1 = gr0 + 32 < k;
+        const int cc = ptid & 63, rg = ptid >> 6;              // centring: column cc, rows 16 rg .. 16 rg + 15
+        const float inv_k = 1.f / (float)k;
+        float racc[16];
 #pragma unroll
-                            for (int kk = 0; kk < MT_CH / 16; ++kk)
-                                tc::mma_f16_ts(tmem + (uint32_t)(t * Nb), a_t + (uint32_t)(kk * 8),
-                                               tc::sdesc_sw128(bsa + kk * 32), idesc, (ci | kk) != 0);
-                        }
-                        tc::commit(tc::smem_u32(&slot_empty[s]));
-                    }
-                    tc::commit(tc::smem_u32(&chunk_done[gc & 1]));
-                }
-                tc::commit(tc::smem_u32(&pass_done));
-                // every MMA of the pass has completed before this warp moves on (and
-                // before TMEM is freed, whatever happened to the formers)
-                if (!tc::mbar_wait(tc::smem_u32(&pass_done), ps & 1, &never, MT_WAIT)) fail();
-            }
-            __syncwarp();
-            asm volatile("bar.sync 2, 544;" ::: "memory");  // the formers have drained the accumulators
-            tc::fence_after();
-        }
-    } else {
-        // ================= former warps =================
-        const int qd = warp & 3, cpart = warp >> 2;  // TMEM lane quarter, 16-column part of a chunk
-        const int trow = qd * 32 + lane;             // tile row (= TMEM lane) of this thread
-        const int gj = tid >> 3, gg = tid & 7;       // gather unit: patch row, 8-column group
-        const T *grow = X + (int64_t)rows[gj] * ld;
-        Unit8<T> pre;
-        uint32_t q = 0, gc = 0;
+        for (int e = 0; e < 16; ++e) racc[e] = 0.f;
+        Unit8<T> pre0, pre1;
+        if (live0) pre0.load(grow0, gg * 8, m, vec); else pre0.zero();
+        if (live1) pre1.load(grow1, gg * 8, m, vec); else pre1.zero();
+        uint32_t gc = 0;
         for (int ps = 0; ps < npass; ++ps) {
-            const int t0 = ps * tpp, nt = min(tpp, ntiles - t0);
-            if (gj < k) pre.load(grow, gg * 8, m, vec); else pre.zero();
             for (int ci = 0; ci < nchunks; ++ci, ++gc) {
                 const int b = gc & 1;
-                const int64_t a0 = (int64_t)ci * MT_CH;
-                pre.store(Xs + gj * MT_XS_LD + gg * 8);
-                if (ci + 1 < nchunks) {
-                    if (gj < k) pre.load(grow, a0 + MT_CH + gg * 8, m, vec); else pre.zero();
+                const uint32_t use = gc >> 1;
+                pre0.store(Xs + gr0 * MT_XS_LD + gg * 8);
+                pre1.store(Xs + (gr0 + 32) * MT_XS_LD + gg * 8);
+                // next chunk (wrapping into the next pass) is loaded while this one is processed
+                const bool more = ci + 1 < nchunks || ps + 1 < npass;
+                if (more) {
+                    const int64_t an = (ci + 1 < nchunks ? (int64_t)(ci + 1) * MT_CH : 0) + gg * 8;
+                    if (live0) pre0.load(grow0, an, m, vec); else pre0.zero();
+                    if (live1) pre1.load(grow1, an, m, vec); else pre1.zero();
                 }
-                asm volatile("bar.sync 1, 512;" ::: "memory");
-                // ---- centre: thread (column cc, row group rg) owns rows 8 rg .. 8 rg + 7
-                {
-                    const int cc = tid & 63, rg = tid >> 6;
-                    float v[8], sum = 0.f;
+                asm volatile("bar.sync 1, 256;" ::: "memory");
+                float v[16], sum = 0.f;
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        v[e] = Xs[(rg * 8 + e) * MT_XS_LD + cc];
-                        sum += v[e];
-                    }
-                    Part[rg * 64 + cc] = sum;
-                    asm volatile("bar.sync 1, 512;" ::: "memory");
-                    float tot = 0.f;
-#pragma unroll
-                    for (int g = 0; g < 8; ++g) tot += Part[g * 64 + cc];
-                    const float mean = tot / (float)k;
-                    float w = 0.f;
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const float x = (rg * 8 + e < k) ? v[e] - mean : 0.f;
-                        v[e] = x;
-                        Xs[(rg * 8 + e) * MT_XS_LD + cc] = x;
-                        w = fmaf(x, x, w);
-                    }
-                    asm volatile("bar.sync 1, 512;" ::: "memory");  // every thread has read Part
-                    Part[rg * 64 + cc] = w;
-                    if (ps == 0) {
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            const float r = warp_sum(v[e]);
-                            if (lane == 0 && rg * 8 + e < k) atomicAdd(&Rs[rg * 8 + e], r);
-                        }
-                    }
+                for (int e = 0; e < 16; ++e) {
+                    v[e] = Xs[(rg * 16 + e) * MT_XS_LD + cc];
+                    sum += v[e];
                 }
-                // buffer b is free once the MMAs of the chunk that last used it completed
-                if (tid == 0 && gc >= 2) {
-                    if (!*abortp && !tc::mbar_wait(tc::smem_u32(&chunk_done[b]), ((gc >> 1) - 1) & 1, abortp, MT_WAIT))
-                        fail();
+                Part[rg * 64 + cc] = sum;
+                asm volatile("bar.sync 1, 256;" ::: "memory");
+                const float mean = (Part[cc] + Part[64 + cc] + Part[128 + cc] + Part[192 + cc]) * inv_k;
+                float w = 0.f;
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const float x = (rg * 16 + e < k) ? v[e] - mean : 0.f;
+                    Xs[(rg * 16 + e) * MT_XS_LD + cc] = x;
+                    w = fmaf(x, x, w);
+                    if (ps == 0) racc[e] += x;
                 }
-                asm volatile("bar.sync 1, 512;" ::: "memory");
+                asm volatile("bar.sync 1, 256;" ::: "memory");  // every thread has read Part
+                Part[rg * 64 + cc] = w;
+                // buffer b is free once the formers and the MMAs of its previous chunk are done with it
+                if (ptid == 0 && use >= 1) {
+                    wait(&formers_done[b], (use - 1) & 1);
+                    wait(&chunk_done[b], (use - 1) & 1);
+                }
+                asm volatile("bar.sync 1, 256;" ::: "memory");
                 uint32_t *Xp = Xp0 + b * MT_XP_ROWS * MT_XP_LD;
                 uint8_t *Bop = Bop0 + b * MT_B_BYTES;
-                {
-                    // unit (row r, 8-column group g): 4 packed words to Xp and the B operand
-                    const int r = tid >> 3, g = tid & 7;
-                    const float4 lo = reinterpret_cast<const float4 *>(Xs + r * MT_XS_LD + g * 8)[0];
-                    const float4 hi = reinterpret_cast<const float4 *>(Xs + r * MT_XS_LD + g * 8)[1];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int r = gr0 + 32 * h;
+                    const float4 lo = reinterpret_cast<const float4 *>(Xs + r * MT_XS_LD + gg * 8)[0];
+                    const float4 hi = reinterpret_cast<const float4 *>(Xs + r * MT_XS_LD + gg * 8)[1];
                     const uint4 pk = make_uint4(pack_bf16x2(lo.x, lo.y), pack_bf16x2(lo.z, lo.w),
                                                 pack_bf16x2(hi.x, hi.y), pack_bf16x2(hi.z, hi.w));
-                    *reinterpret_cast<uint4 *>(Xp + r * MT_XP_LD + g * 4) = pk;
-                    if (r < Nb) *reinterpret_cast<uint4 *>(Bop + sw128(r, g)) = pk;
-                    if (tid < 32) {
-                        float w0 = 0.f, w1 = 0.f;
-#pragma unroll
-                        for (int gq = 0; gq < 8; ++gq) {
-                            w0 += Part[gq * 64 + 2 * tid];
-                            w1 += Part[gq * 64 + 2 * tid + 1];
-                        }
-                        Xp[MT_ROW_W * MT_XP_LD + tid] = pack_bf16x2(w0, w1);
-                    }
+                    *reinterpret_cast<uint4 *>(Xp + r * MT_XP_LD + gg * 4) = pk;
+                    if (r < Nb) *reinterpret_cast<uint4 *>(Bop + sw128(r, gg)) = pk;
+                }
+                if (ptid < 32) {
+                    const int c0 = 2 * ptid;
+                    const float w0 = Part[c0] + Part[64 + c0] + Part[128 + c0] + Part[192 + c0];
+                    const float w1 = Part[c0 + 1] + Part[65 + c0] + Part[129 + c0] + Part[193 + c0];
+                    Xp[MT_ROW_W * MT_XP_LD + ptid] = pack_bf16x2(w0, w1);
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                asm volatile("bar.sync 1, 512;" ::: "memory");
-                // ---- form the A operand of each tile of the pass in a TMEM slot
+                asm volatile("bar.sync 1, 256;" ::: "memory");
+                if (ptid == 0) tc::mbar_arrive(tc::smem_u32(&chunk_ready[b]));
+            }
+        }
+        // R = X_c 1: per-thread partial sums of pass 0, reduced over the 64 column threads
+#pragma unroll
+        for (int e = 0; e < 16; ++e) Xs[(rg * 16 + e) * MT_XS_LD + cc] = racc[e];
+        asm volatile("bar.sync 1, 256;" ::: "memory");
+        if (ptid < k) {
+            float r = 0.f;
+            for (int c = 0; c < 64; ++c) r += Xs[ptid * MT_XS_LD + c];
+            R[pt * k + ptid] = r;
+        }
+    } else if (warp < MT_PRODUCER_WARPS + MT_FORMER_WARPS) {
+        // ================= formers: row products into TMEM; drain =================
+        const int qd = warp & 3, half = (warp - MT_PRODUCER_WARPS) >> 2;  // TMEM lane quarter, K half
+        const int trow = qd * 32 + lane;
+        uint32_t q = 0, gc = 0;
+        for (int ps = 0; ps < npass; ++ps) {
+            const int t0 = ps * tpp, nt = min(tpp, ntiles - t0);
+            for (int ci = 0; ci < nchunks; ++ci, ++gc) {
+                const int b = gc & 1;
+                if (lane == 0) wait(&chunk_ready[b], (gc >> 1) & 1);
+                __syncwarp();
+                const uint32_t *Xp = Xp0 + b * MT_XP_ROWS * MT_XP_LD;
                 for (int t = 0; t < nt; ++t, ++q) {
                     const int s = q % MT_SLOTS;
                     if (q >= MT_SLOTS) {
-                        if (lane == 0 && !*abortp &&
-                            !tc::mbar_wait(tc::smem_u32(&slot_empty[s]), ((q / MT_SLOTS) - 1) & 1, abortp, MT_WAIT))
-                            fail();
+                        if (lane == 0) wait(&slot_empty[s], ((q / MT_SLOTS) - 1) & 1);
                         __syncwarp();
                         tc::fence_after();
                     }
                     const int code = codes[(t0 + t) * 128 + trow];
-                    const int ra = code & 0xff, rb = (code >> 8) & 0xff;
-                    const uint4 *pa = reinterpret_cast<const uint4 *>(Xp + ra * MT_XP_LD + cpart * 8);
-                    const uint4 *pb = reinterpret_cast<const uint4 *>(Xp + rb * MT_XP_LD + cpart * 8);
-                    const uint4 a_lo = pa[0], a_hi = pa[1], b_lo = pb[0], b_hi = pb[1];
-                    uint32_t z[8];
-                    const uint32_t av[8] = {a_lo.x, a_lo.y, a_lo.z, a_lo.w, a_hi.x, a_hi.y, a_hi.z, a_hi.w};
-                    const uint32_t bv[8] = {b_lo.x, b_lo.y, b_lo.z, b_lo.w, b_hi.x, b_hi.y, b_hi.z, b_hi.w};
+                    const uint4 *pa = reinterpret_cast<const uint4 *>(Xp + (code & 0xff) * MT_XP_LD + half * 16);
+                    const uint4 *pb = reinterpret_cast<const uint4 *>(Xp + ((code >> 8) & 0xff) * MT_XP_LD + half * 16);
+                    uint32_t z[16];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        __nv_bfloat162 x = *reinterpret_cast<const __nv_bfloat162 *>(&av[e]);
-                        __nv_bfloat162 y = *reinterpret_cast<const __nv_bfloat162 *>(&bv[e]);
-                        __nv_bfloat162 pr = __hmul2(x, y);
-                        z[e] = *reinterpret_cast<uint32_t *>(&pr);
+                    for (int e4 = 0; e4 < 4; ++e4) {
+                        const uint4 av = pa[e4], bv = pb[e4];
+                        const uint32_t aw[4] = {av.x, av.y, av.z, av.w};
+                        const uint32_t bw[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            __nv_bfloat162 x = *reinterpret_cast<const __nv_bfloat162 *>(&aw[e]);
+                            __nv_bfloat162 y = *reinterpret_cast<const __nv_bfloat162 *>(&bw[e]);
+                            __nv_bfloat162 pr = __hmul2(x, y);
+                            z[e4 * 4 + e] = *reinterpret_cast<uint32_t *>(&pr);
+                        }
                     }
-                    tc::tmem_st_32x32b_x8(tmem + ((uint32_t)(qd * 32) << 16) +
-                                              (uint32_t)(MT_D_COLS + s * MT_SLOT_COLS + cpart * 8),
-                                          z);
+                    tc::tmem_st_32x32b_x16(tmem + ((uint32_t)(qd * 32) << 16) +
+                                               (uint32_t)(MT_D_COLS + s * MT_SLOT_COLS + half * 16),
+                                           z);
                     tc::tmem_st_wait();
                     tc::fence_before();
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(tc::smem_u32(&slot_full[s]));
                 }
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(tc::smem_u32(&formers_done[b]));
             }
-            // ---- drain the pass's accumulators: warps with cpart == t % 4 take tile t
-            if (lane == 0 && !tc::mbar_wait(tc::smem_u32(&pass_done), ps & 1, abortp, MT_WAIT)) fail();
+            // ---- drain the pass's accumulators: this warp takes tiles half, half + 2, ...
+            if (lane == 0) wait(&pass_done, ps & 1);
             __syncwarp();
             tc::fence_after();
-            for (int t = cpart; t < nt; t += 4) {
+            for (int t = half; t < nt; t += 2) {
                 const int code = codes[(t0 + t) * 128 + trow];
                 const int ra = code & 0xff, rb = (code >> 8) & 0xff, kind = (code >> 16) & 3;
                 float *dst = nullptr;
@@ -406,11 +401,43 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
                 }
             }
             tc::fence_before();
-            asm volatile("bar.sync 2, 544;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(tc::smem_u32(&d_free));
         }
+    } else {
+        // ================= MMA warp (lane 0 issues) =================
+        if (lane == 0) {
+            uint32_t q = 0, gc = 0;
+            for (int ps = 0; ps < npass; ++ps) {
+                const int nt = min(tpp, ntiles - ps * tpp);
+                if (ps > 0) {
+                    wait(&d_free, (ps - 1) & 1);  // the formers have drained the previous pass
+                    tc::fence_after();
+                }
+                for (int ci = 0; ci < nchunks; ++ci, ++gc) {
+                    const uint32_t bsa = tc::smem_u32(Bop0 + (gc & 1) * MT_B_BYTES);
+                    for (int t = 0; t < nt; ++t, ++q) {
+                        const int s = q % MT_SLOTS;
+                        wait(&slot_full[s], (q / MT_SLOTS) & 1);
+                        tc::fence_after();
+                        if (!*abortp) {
+                            const uint32_t a_t = tmem + (uint32_t)(MT_D_COLS + s * MT_SLOT_COLS);
+#pragma unroll
+                            for (int kk = 0; kk < MT_CH / 16; ++kk)
+                                tc::mma_f16_ts(tmem + (uint32_t)(t * Nb), a_t + (uint32_t)(kk * 8),
+                                               tc::sdesc_sw128(bsa + kk * 32), idesc, (ci | kk) != 0);
+                        }
+                        tc::commit(tc::smem_u32(&slot_empty[s]));
+                    }
+                    tc::commit(tc::smem_u32(&chunk_done[gc & 1]));
+                }
+                tc::commit(tc::smem_u32(&pass_done));
+            }
+            // every MMA has completed before TMEM is freed, whatever happened elsewhere
+            if (!tc::mbar_wait(tc::smem_u32(&pass_done), (npass - 1) & 1, &never, MT_WAIT)) fail();
+        }
+        __syncwarp();
     }
-    __syncthreads();
-    if (tid < k) R[pt * k + tid] = Rs[tid];
     tc::fence_before();
     __syncthreads();
     if (warp == 0) {
