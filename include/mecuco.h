@@ -98,8 +98,11 @@ typedef enum {
     MECUCO_OPT_PROFILE = 5,          /* 1: bracket every kernel with CUDA events (mecuco_get_stage_times) */
     MECUCO_OPT_KNN_SPLITS = 6,       /* candidate-range splits of the kNN search (0 = automatic, else 1..64;
                                         capped so that splits * candidate capacity <= 1024) */
-    MECUCO_OPT_BATCH_LANES = 7       /* concurrent streams of mecuco_curvature_batched (1..32, default 8;
+    MECUCO_OPT_BATCH_LANES = 7,      /* concurrent streams of mecuco_curvature_batched (1..32, default 8;
                                         a batch signature tuned by mecuco_autotune_batched uses its own) */
+    MECUCO_OPT_TC_SLOTS = 8          /* TMEM slots for the row-product operand of the tensor-core moment
+                                        kernel (2..8, default 4; more slots leave fewer accumulator tiles
+                                        per pass over the patch) */
 } mecuco_option;
 
 /* Kernel stages, for mecuco_get_stage_times. */

@@ -64,6 +64,7 @@ struct mecuco_ctx {
     int32_t *m3_items[65] = {};  // per k: work items of the CUDA-core third-moment kernel
     int32_t *rowtab[65] = {};    // per k: row codes of the tensor-core moment kernel
     int knn_splits = 0;
+    int tc_slots = 4;
     // batched entry point: lanes (streams) and their workspace
     int batch_lanes = 8;
     char *bws = nullptr;
@@ -190,6 +191,8 @@ int candidate_capacity(mecuco_t h, int k) {
 
 struct KnnPlan {
     int kc, nsplit;
+    int lists;      // candidate lists per query row (splits x the tensor-core kernel's column halves)
+    int kcl;        // capacity of each list
     int64_t qchunk;
     bool tc;        // candidate search on the tensor cores (BF16 operands)
     bool bf16_copy; // the tensor-core path needs a BF16 copy of X
@@ -213,8 +216,15 @@ KnnPlan plan_knn(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t 
     const int64_t want = (p.tc ? 1LL : 2LL) * h->num_sms;
     p.nsplit = 1;
     if (qblocks < want) p.nsplit = (int)std::min<int64_t>((want + qblocks - 1) / qblocks, 1024 / p.kc);
-    if (h->knn_splits > 0) p.nsplit = std::min(h->knn_splits, 1024 / p.kc);
+    // tensor-core search: each split leaves knn_tc_halves() lists per row, each of
+    // capacity >= k (<= 64, the shared-memory budget next to three stages)
+    const int halves = p.tc ? knn_tc_halves() : 1;
+    p.kcl = p.tc ? std::min(p.kc, 64) : p.kc;
+    const int cap = 1024 / (halves * p.kcl);
+    if (p.nsplit > cap) p.nsplit = cap;
+    if (h->knn_splits > 0) p.nsplit = std::min(h->knn_splits, cap);
     while (p.nsplit > 1 && (N + p.nsplit - 1) / p.nsplit < p.kc) --p.nsplit;
+    p.lists = p.nsplit * halves;
     return p;
 }
 
@@ -222,20 +232,15 @@ struct KnnBufs {
     float *norms, *cand_d;
     int32_t *cand_i, *flags;
     void *xb;
-    float *merged_d;    // merged lists (tensor-core path with nsplit > 1)
-    int32_t *merged_i;
 };
 
 // Scratch of run_knn, carved after `start`.
 void knn_scratch(Carver &c, const KnnPlan &p, int64_t N, KnnBufs *b) {
     b->norms = c.take<float>((size_t)N);
-    b->cand_d = c.take<float>((size_t)p.qchunk * p.nsplit * p.kc);
-    b->cand_i = c.take<int32_t>((size_t)p.qchunk * p.nsplit * p.kc);
+    b->cand_d = c.take<float>((size_t)p.qchunk * p.lists * p.kcl);
+    b->cand_i = c.take<int32_t>((size_t)p.qchunk * p.lists * p.kcl);
     b->flags = c.take<int32_t>((size_t)p.qchunk);
     b->xb = p.bf16_copy ? (void *)c.take<uint16_t>((size_t)N * p.ldb) : nullptr;
-    const bool merge = p.tc && p.nsplit > 1 && !p.bf16_copy;
-    b->merged_d = merge ? c.take<float>((size_t)p.qchunk * p.kc) : nullptr;
-    b->merged_i = merge ? c.take<int32_t>((size_t)p.qchunk * p.kc) : nullptr;
 }
 
 // kNN of query rows [rb, re) (outputs relative to rb); scratch at ws + start,
@@ -258,31 +263,21 @@ mecuco_status run_knn(mecuco_t h, char *ws, const void *X, mecuco_dtype dt, int6
         int64_t nq = std::min(p.qchunk, re - q0);
         int32_t *io = idx_out + (q0 - rb) * k;
         float *dout = dist_out ? dist_out + (q0 - rb) * k : nullptr;
-        const float *rd = b.cand_d;
-        const int32_t *ri = b.cand_i;
-        int rsplit = p.nsplit;
         if (p.tc) {
             LAUNCH(h, MECUCO_STAGE_KNN_SEARCH, s,
-                   launch_knn_tc(Xb, N, m, p.ldb, b.norms, q0, nq, p.kc, p.nsplit, include_self, b.cand_d, b.cand_i,
-                                 h->ctr, s));
-            // BF16 storage: merge the split lists down to kc before the re-rank.  A
-            // BF16 copy of FP32 data perturbs d~ more, so its rows keep the whole
-            // nsplit * kc pool for the certification margin.
-            if (b.merged_d) {
-                LAUNCH(h, MECUCO_STAGE_KNN_RERANK, s,
-                       launch_knn_merge(b.cand_d, b.cand_i, nq, p.kc, p.nsplit, b.merged_d, b.merged_i, s));
-                rd = b.merged_d;
-                ri = b.merged_i;
-                rsplit = 1;
-            }
+                   launch_knn_tc(Xb, N, m, p.ldb, b.norms, q0, nq, p.kcl, p.nsplit, include_self, b.cand_d,
+                                 b.cand_i, h->ctr, s));
         } else {
             LAUNCH(h, MECUCO_STAGE_KNN_SEARCH, s,
                    launch_knn_simt(X, dt, N, m, ld, b.norms, q0, nq, p.kc, p.nsplit, include_self, b.cand_d,
                                    b.cand_i, s));
         }
+        // every row's lists go to the exact re-rank together: a point that a list
+        // rejected has d~ >= that list's maximum, so the smallest list maximum
+        // bounds every candidate left out
         LAUNCH(h, MECUCO_STAGE_KNN_RERANK, s,
-               launch_knn_rerank(X, dt, N, m, ld, b.norms, q0, nq, p.kc, rsplit, k, rd, ri, io, dout, b.flags, h->ctr,
-                                 s));
+               launch_knn_rerank(X, dt, N, m, ld, b.norms, q0, nq, p.kcl, p.lists, k, b.cand_d, b.cand_i, io, dout,
+                                 b.flags, h->ctr, s));
         LAUNCH(h, MECUCO_STAGE_KNN_FALLBACK, s,
                launch_knn_fallback(X, dt, N, m, ld, q0, nq, k, include_self, b.flags, io, dout, h->ctr, s));
     }
@@ -404,7 +399,7 @@ mecuco_status run_curvature(mecuco_t h, char *ws, const void *X, mecuco_dtype dt
             float *Ud = U_out ? U_out + p0 * (int64_t)k * k : b.U;
             LAUNCH(h, MECUCO_STAGE_MOMENTS, s,
                    launch_moments_tc(X, dt, N, m, ld, nb, k, np, h->rowtab[k], b.M, b.G, b.R,
-                                     var == MECUCO_FAST_HAAR ? b.Q : nullptr, h->ctr, s));
+                                     var == MECUCO_FAST_HAAR ? b.Q : nullptr, h->tc_slots, h->ctr, s));
             LAUNCH(h, MECUCO_STAGE_JACOBI, s,
                    launch_jacobi(b.G, k, np, fp64, h->jacobi_max_sweeps, b.sig, Ud, h->ctr, s));
             if (fp64 == 1 || fp64 == 3) ++h->launches;  // the FP64 refinement is a second kernel
@@ -632,6 +627,10 @@ mecuco_status mecuco_set_option(mecuco_t h, mecuco_option opt, int64_t v) {
         case MECUCO_OPT_KNN_SPLITS:
             if (v < 0 || v > 64) return MECUCO_ERR_INVALID_ARG;
             h->knn_splits = (int)v;
+            break;
+        case MECUCO_OPT_TC_SLOTS:
+            if (v < 2 || v > 8) return MECUCO_ERR_INVALID_ARG;
+            h->tc_slots = (int)v;
             break;
         case MECUCO_OPT_BATCH_LANES:
             if (v < 1 || v > 32) return MECUCO_ERR_INVALID_ARG;

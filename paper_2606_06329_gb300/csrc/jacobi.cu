@@ -171,7 +171,10 @@ jacobi_kernel(const float *__restrict__ G, int k, int64_t np, int max_sweeps, fl
 //   E_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i)  if |lam_i - lam_j| > delta,
 //   E_ij = R_ij / 2 otherwise (and on the diagonal),   X' = X + X E.
 // From FP32-accurate X (~2^-23) one step gives eigenvectors accurate to the
-// square of that, i.e. to FP64 level, and re-orthogonalises them.  delta =
+// square of that, i.e. to FP64 level, and re-orthogonalises them.  The
+// products X^T X and X^T A X are symmetric (upper triangles only), and the
+// correction X E, of relative size ~2^-23, is formed in FP32: 2k^3 FP64 FMA per
+// patch.  delta =
 // 2^-18 max|lam| treats eigenvalues closer than the FP32 estimate can resolve
 // as a cluster (only orthogonalised).  With rel != 0 the cluster test is
 // relative to the pair itself, |lam_i - lam_j| <= 2^-18 max(|lam_i|, |lam_j|):
@@ -204,21 +207,26 @@ jacobi_refine64_kernel(const float *__restrict__ G, int k, int rel, float *__res
         X[r * ld + c] = (double)u[e];
     }
     __syncthreads();
-    // T = A X ; Rm = I - X^T X
+    // T = A X (every entry)
     for (int e = tid; e < kk; e += RT) {
         const int r = e / k, c = e % k;
-        double t = 0.0, q = 0.0;
-        for (int j = 0; j < k; ++j) {
-            t = fma(A[r * ld + j], X[j * ld + c], t);
-            q = fma(X[j * ld + r], X[j * ld + c], q);
-        }
+        double t = 0.0;
+        for (int j = 0; j < k; ++j) t = fma(A[r * ld + j], X[j * ld + c], t);
         T[r * ld + c] = t;
+    }
+    // Rm = I - X^T X (upper triangle: both products are symmetric)
+    for (int e = tid; e < kk; e += RT) {
+        const int r = e / k, c = e % k;
+        if (c < r) continue;
+        double q = 0.0;
+        for (int j = 0; j < k; ++j) q = fma(X[j * ld + r], X[j * ld + c], q);
         Rm[r * ld + c] = (r == c ? 1.0 : 0.0) - q;
     }
     __syncthreads();
-    // S = X^T T
+    // S = X^T T (upper triangle)
     for (int e = tid; e < kk; e += RT) {
         const int r = e / k, c = e % k;
+        if (c < r) continue;
         double t = 0.0;
         for (int j = 0; j < k; ++j) t = fma(X[j * ld + r], T[j * ld + c], t);
         S[r * ld + c] = t;
@@ -233,29 +241,30 @@ jacobi_refine64_kernel(const float *__restrict__ G, int k, int rel, float *__res
     }
     __syncthreads();
     const double delta = 3.814697265625e-06 * s_lmax;  // 2^-18 max|lam|
-    // E (in place of Rm): needs the old R_ij and R_ji, read before any write
-    double ev[(64 * 64 + RT - 1) / RT];
-    int ne = 0;
-    for (int e = tid; e < kk; e += RT, ++ne) {
+    // E (FP32: |E| ~ the FP32 eigenvector error, so X E rounded in FP32 is far below
+    // FP64-level error in X + X E); X as FP32 (exact: it came from FP32)
+    float *Ef = reinterpret_cast<float *>(T);       // [k][ld]
+    float *Xf = Ef + (size_t)k * ld;                 // [k][ld]
+    __syncthreads();
+    for (int e = tid; e < kk; e += RT) {
         const int i = e / k, j = e % k;
-        const double rij = 0.5 * (Rm[i * ld + j] + Rm[j * ld + i]);
-        const double sij = 0.5 * (S[i * ld + j] + S[j * ld + i]);
+        const int a = i < j ? i : j, b = i < j ? j : i;
+        const double rij = Rm[a * ld + b];
+        const double sij = S[a * ld + b];
         double v;
         const double dij = rel ? 3.814697265625e-06 * fmax(fabs(lam[i]), fabs(lam[j])) : delta;
         if (i == j || fabs(lam[i] - lam[j]) <= dij) v = 0.5 * rij;
         else v = (sij + lam[j] * rij) / (lam[j] - lam[i]);
-        ev[ne] = v;
+        Ef[i * ld + j] = (float)v;
+        Xf[i * ld + j] = (float)X[i * ld + j];
     }
     __syncthreads();
-    ne = 0;
-    for (int e = tid; e < kk; e += RT, ++ne) Rm[(e / k) * ld + (e % k)] = ev[ne];
-    __syncthreads();
-    // X' = X + X E
+    // X' = X + X E (FP32), into X (as double) for the write-back
     for (int e = tid; e < kk; e += RT) {
         const int r = e / k, c = e % k;
-        double t = X[r * ld + c];
-        for (int j = 0; j < k; ++j) t = fma(X[r * ld + j], Rm[j * ld + c], t);
-        T[r * ld + c] = t;
+        float t = 0.f;
+        for (int j = 0; j < k; ++j) t = fmaf(Xf[r * ld + j], Ef[j * ld + c], t);
+        X[r * ld + c] = (double)Xf[r * ld + c] + (double)t;
     }
     __syncthreads();
     // write back, columns re-sorted by lam descending
@@ -264,7 +273,7 @@ jacobi_refine64_kernel(const float *__restrict__ G, int k, int rel, float *__res
         int rank = 0;
         for (int j = 0; j < k; ++j) rank += (lam[j] > lam[i]) || (lam[j] == lam[i] && j < i);
         sg[rank] = (float)lam[i];
-        for (int r = 0; r < k; ++r) u[r * k + rank] = (float)T[r * ld + i];
+        for (int r = 0; r < k; ++r) u[r * k + rank] = (float)X[r * ld + i];
     }
 }
 

@@ -29,17 +29,17 @@ cudaError_t launch_knn_simt(const void *X, mecuco_dtype dt, int64_t N, int64_t m
                             int include_self, float *cand_d, int32_t *cand_i, cudaStream_t s);
 
 // Candidate search, BF16 operands on the tensor cores (tcgen05, TMEM accumulators,
-// TMA-fed shared memory), same output contract as launch_knn_simt.  Xb is BF16
-// row-major with ldb % 8 == 0 and a 16-byte aligned base (X itself when it is
-// stored that way, else a copy made by launch_to_bf16).  kc <= 128.
+// TMA-fed shared memory): the output contract of launch_knn_simt with
+// knn_tc_halves() lists of capacity kc per row and split.  Xb is BF16 row-major
+// with ldb % 8 == 0 and a 16-byte aligned base (X itself when it is stored that
+// way, else a copy made by launch_to_bf16).  kc <= 64.
 cudaError_t launch_knn_tc(const void *Xb, int64_t N, int64_t m, int64_t ldb, const float *norms,
                           int64_t q0, int64_t nq, int kc, int nsplit, int include_self,
                           float *cand_d, int32_t *cand_i, DevCounters *ctr, cudaStream_t s);
 size_t knn_tc_smem_bytes(int kc);
-// Merge nsplit per-split lists (layout of launch_knn_simt) into one list of the
-// kc smallest per query (out: nq x kc); certification carries over.
-cudaError_t launch_knn_merge(const float *in_d, const int32_t *in_i, int64_t nq, int kc, int nsplit, float *out_d,
-                             int32_t *out_i, cudaStream_t s);
+// Candidate lists the tensor-core search leaves per row and split (the epilogue's
+// column halves); list h of row r, split s starts at ((r nsplit + s) halves + h) kc.
+int knn_tc_halves();
 // BF16 copy of X (round to nearest even) with leading dimension ldb >= m.
 cudaError_t launch_to_bf16(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, void *Y,
                            int64_t ldb, cudaStream_t s);
@@ -90,12 +90,12 @@ void m3_build_items(int k, int32_t *items /* m3_items(k) */);
 
 // BF16-mixed form: G, R, Q and the pair-major M of each patch from
 // tensor-core GEMMs over 128-row tiles of row products (BF16 operands, FP32
-// accumulation).  rowtab holds moments_tc_rows(k) row codes built by
+// accumulation), nslots TMEM slots for the A operand.  rowtab holds moments_tc_rows(k) row codes built by
 // moments_tc_build_rows; idx points at the chunk's first neighbour row; Q may
 // be NULL.
 cudaError_t launch_moments_tc(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, const int32_t *idx,
                               int k, int64_t np, const int32_t *rowtab, float *M, float *G, float *R, float *Q,
-                              DevCounters *ctr, cudaStream_t s);
+                              int nslots, DevCounters *ctr, cudaStream_t s);
 int moments_tc_rows(int k);
 void moments_tc_build_rows(int k, int32_t *codes /* moments_tc_rows(k) */);
 size_t moments_tc_smem_bytes(int k);

@@ -13,10 +13,13 @@
 //               and issues tcgen05.mma (M=128, N=256, K=16) from one lane,
 //               committing each stage back to the producer and each finished
 //               tile to the epilogue.
-//   warps 2-5   epilogue: drain one accumulator (thread = query row) while the
-//               MMA fills the other; d~ = |x|^2 + |y|^2 - 2 x.y; values below
-//               the row's admission threshold enter its kc-slot candidate list
-//               (distances in shared memory, indices straight to global).
+//   warps 2-9   epilogue: drain one accumulator while the MMA fills the other;
+//               the two warps of a TMEM lane quarter take one query row per
+//               thread and half of the tile's 256 columns each, every (row,
+//               half) with its own kc-slot candidate list (distances in shared
+//               memory as a max-heap, indices straight to global), so a row leaves with
+//               TC_HALVES lists per candidate split; d~ = |x|^2 + |y|^2 - 2 x.y;
+//               values below a list's admission threshold enter it.
 // Every mbarrier wait is bounded; a timeout sets MECUCO_ERR_TIMEOUT in the
 // device status word, raises a CTA-wide abort flag, drains the copies and MMAs
 // already in flight (also bounded), frees TMEM and returns.
@@ -37,35 +40,59 @@ constexpr int NSTAGE = 3;
 constexpr int A_BYTES = TBM * TBK * 2;   // 16 KB
 constexpr int B_BYTES = TBN * TBK * 2;   // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int TC_THREADS = 192;
+constexpr int TC_THREADS = 320;  // TMA warp, MMA warp, 8 epilogue warps
+constexpr int TC_HALVES = 2;     // epilogue warps per TMEM lane quarter (column halves)
 constexpr long long WAIT_LIMIT = 1000000000LL;  // ~0.5 s of SM clock per wait
 constexpr uint32_t IDESC = tc::idesc_bf16_f32(TBM, TBN);
 
 struct ListState {
     float thr;  // admission threshold: the largest distance held once the list is full
-    int cnt;    // slots in use
-    int slot;   // slot holding thr
+    int cnt;    // entries in use
 };
 
-// Rare path of the drain: put (d, c) into the row's kc-slot list (distances in
-// shared memory at Ld[slot * TBM + row], indices to global at out[slot]); once
-// the list is full each admission replaces the current maximum.
-__device__ __noinline__ ListState list_insert(ListState st, float d, int c, float *Ld, int32_t *out, int row, int kc) {
-    int s = st.cnt < kc ? st.cnt : st.slot;
-    Ld[s * TBM + row] = d;
-    out[s] = c;
+// Rare path of the drain: the row's list is a binary max-heap of kc distances
+// in shared memory (position p at Ld[p * TBM + row]); Ls[p * TBM + row] is the
+// slot of the global index array out[] that holds the entry's candidate, so
+// entries move inside the heap without touching global memory.  Filling appends
+// and sifts up; once full, a candidate below the root replaces it and sifts
+// down (O(log kc) instead of a scan for the new maximum).
+__device__ __noinline__ ListState list_insert(ListState st, float d, int c, float *Ld, uint8_t *Ls, int32_t *out,
+                                              int row, int kc) {
     if (st.cnt < kc) {
+        int pos = st.cnt;
+        while (pos > 0) {
+            const int par = (pos - 1) >> 1;
+            const float pd = Ld[par * TBM + row];
+            if (pd >= d) break;
+            Ld[pos * TBM + row] = pd;
+            Ls[pos * TBM + row] = Ls[par * TBM + row];
+            pos = par;
+        }
+        Ld[pos * TBM + row] = d;
+        Ls[pos * TBM + row] = (uint8_t)st.cnt;
+        out[st.cnt] = c;
         ++st.cnt;
-        if (st.cnt < kc) return st;
+        if (st.cnt == kc) st.thr = Ld[row];
+        return st;
     }
-    float mx = -INFINITY;
-    int sl = 0;
-    for (int s2 = 0; s2 < kc; ++s2) {
-        float v = Ld[s2 * TBM + row];
-        if (v > mx) { mx = v; sl = s2; }
+    const uint8_t slot = Ls[row];
+    out[slot] = c;
+    int pos = 0;
+    for (;;) {
+        const int l = 2 * pos + 1;
+        if (l >= kc) break;
+        const float dl = Ld[l * TBM + row];
+        const float dr = l + 1 < kc ? Ld[(l + 1) * TBM + row] : -INFINITY;
+        const int ch = dr > dl ? l + 1 : l;
+        const float dc = dr > dl ? dr : dl;
+        if (dc <= d) break;
+        Ld[pos * TBM + row] = dc;
+        Ls[pos * TBM + row] = Ls[ch * TBM + row];
+        pos = ch;
     }
-    st.thr = mx;
-    st.slot = sl;
+    Ld[pos * TBM + row] = d;
+    Ls[pos * TBM + row] = slot;
+    st.thr = Ld[row];
     return st;
 }
 
@@ -93,8 +120,9 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
     // 1024-byte aligned stage ring, then candidate distances [kc][TBM], then barriers
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tsm_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *stages = base;
-    float *Ld = reinterpret_cast<float *>(base + NSTAGE * STAGE_BYTES);
-    TcShared *sh = reinterpret_cast<TcShared *>(Ld + (size_t)kc * TBM);
+    float *Ld0 = reinterpret_cast<float *>(base + NSTAGE * STAGE_BYTES);  // [TC_HALVES][kc][TBM] heaps
+    uint8_t *Ls0 = reinterpret_cast<uint8_t *>(Ld0 + (size_t)TC_HALVES * kc * TBM);  // [TC_HALVES][kc][TBM]
+    TcShared *sh = reinterpret_cast<TcShared *>(Ls0 + (size_t)TC_HALVES * kc * TBM);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t qend = q0 + nq;
@@ -111,7 +139,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
         }
         for (int a = 0; a < 2; ++a) {
             tc::mbar_init(tc::smem_u32(&sh->tfull[a]), 1);
-            tc::mbar_init(tc::smem_u32(&sh->tempty[a]), 4 * 32);
+            tc::mbar_init(tc::smem_u32(&sh->tempty[a]), 4 * TC_HALVES * 32);
         }
         // circuit breaker: once any CTA of this launch timed out, later CTAs skip
         // the work (their lists come out empty) instead of timing out one by one
@@ -217,7 +245,10 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
     } else {
         // ------------------------------ epilogue ---------------------------------
         const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
+        const int half = (warp - 2) >> 2;  // columns [128 half, 128 half + 128) of each tile
         const int row = quarter * 32 + lane;
+        float *Ld = Ld0 + (size_t)half * kc * TBM;
+        uint8_t *Ls = Ls0 + (size_t)half * kc * TBM;
         int t = 0;  // tiles drained so far by this CTA (all items)
         for (int64_t item = blockIdx.x; item < nitems && !*abort_flag; item += gridDim.x) {
             const int split = (int)(item % nsplit);
@@ -227,8 +258,9 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
             const int64_t gq = qb + row;
             const bool valid_row = gq < qend;
             const float qn = valid_row ? norms[gq] : 0.f;
-            const int64_t out_base = valid_row ? ((gq - q0) * nsplit + split) * (int64_t)kc : 0;
-            ListState st{valid_row ? INFINITY : -INFINITY, 0, 0};
+            const int64_t out_base =
+                valid_row ? (((gq - q0) * nsplit + split) * TC_HALVES + half) * (int64_t)kc : 0;
+            ListState st{valid_row ? INFINITY : -INFINITY, 0};
             int32_t *out_i = cand_i + out_base;
             for (int tt = 0; tt < ntiles && !*abort_flag; ++tt, ++t) {
                 const int acc = t & 1;
@@ -242,7 +274,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
                 const bool masked = (c0 + TBN > cend) || (!include_self && gq >= c0 && gq < c0 + TBN);
                 const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * TBN);
 #pragma unroll 1
-                for (int ch = 0; ch < TBN / 32; ++ch) {
+                for (int ch = half * (TBN / 32 / TC_HALVES); ch < (half + 1) * (TBN / 32 / TC_HALVES); ++ch) {
                     uint32_t r[32];
                     tc::tmem_ld_32x32b_x32(taddr + ch * 32, r);
                     tc::tmem_ld_wait();
@@ -254,17 +286,17 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
                         const float cn = (c < N) ? __ldg(cnp + j) : 0.f;
                         float d = fmaf(-2.f, __uint_as_float(r[j]), qn + cn);
                         if (masked && (c >= cend || (!include_self && c == gq))) d = INFINITY;
-                        if (d < st.thr) st = list_insert(st, d, (int)c, Ld, out_i, row, kc);
+                        if (d < st.thr) st = list_insert(st, d, (int)c, Ld, Ls, out_i, row, kc);
                     }
                 }
                 tc::fence_before();
                 tc::mbar_arrive(tc::smem_u32(&sh->tempty[acc]));
             }
             if (valid_row) {
-                for (int s2 = 0; s2 < kc; ++s2) {
-                    const bool used = s2 < st.cnt;
-                    cand_d[out_base + s2] = used ? Ld[s2 * TBM + row] : INFINITY;
-                    if (!used) out_i[s2] = -1;
+                for (int p = 0; p < st.cnt; ++p) cand_d[out_base + Ls[p * TBM + row]] = Ld[p * TBM + row];
+                for (int s2 = st.cnt; s2 < kc; ++s2) {
+                    cand_d[out_base + s2] = INFINITY;
+                    out_i[s2] = -1;
                 }
             }
         }
@@ -306,14 +338,17 @@ bool make_map(CUtensorMap *map, const void *Xb, int64_t N, int64_t m, int64_t ld
 }  // namespace
 
 size_t knn_tc_smem_bytes(int kc) {
-    return 1024 + (size_t)NSTAGE * STAGE_BYTES + (size_t)kc * TBM * sizeof(float) + sizeof(TcShared) + 64;
+    return 1024 + (size_t)NSTAGE * STAGE_BYTES + (size_t)TC_HALVES * kc * TBM * (sizeof(float) + 1) + sizeof(TcShared) +
+           64;
 }
+
+int knn_tc_halves() { return TC_HALVES; }
 
 cudaError_t launch_knn_tc(const void *Xb, int64_t N, int64_t m, int64_t ldb, const float *norms, int64_t q0,
                           int64_t nq, int kc, int nsplit, int include_self, float *cand_d, int32_t *cand_i,
                           DevCounters *ctr, cudaStream_t s) {
     if (nq <= 0) return cudaSuccess;
-    if ((reinterpret_cast<uintptr_t>(Xb) & 15) || (ldb % 8) != 0) return cudaErrorInvalidValue;
+    if ((reinterpret_cast<uintptr_t>(Xb) & 15) || (ldb % 8) != 0 || kc > 64) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
     if (!make_map(&ma, Xb, N, m, ldb, TBM) || !make_map(&mb, Xb, N, m, ldb, TBN)) return cudaErrorInvalidValue;
     const size_t smem = knn_tc_smem_bytes(kc);
@@ -328,61 +363,6 @@ cudaError_t launch_knn_tc(const void *Xb, int64_t N, int64_t m, int64_t ldb, con
     dim3 grid((unsigned)(items < sms ? items : sms));  // persistent: one CTA per SM
     knn_tc_kernel<<<grid, TC_THREADS, smem, s>>>(ma, mb, N, m, norms, q0, nq, kc, nsplit, include_self, cand_d,
                                                   cand_i, ctr);
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Merge of the per-split candidate lists of each query into one list of the kc
-// smallest approximate distances (ties to the lower index).  Every point left
-// out keeps d~ >= the merged list's maximum (a point rejected by split s has
-// d~ >= that split's maximum, which bounds the union's kc-th smallest from
-// above), so the re-rank's certification applies to the merged list unchanged.
-// One warp per query; rank counting over the nsplit * kc entries.
-// ---------------------------------------------------------------------------
-constexpr int MG_WARPS = 4;
-
-__global__ void __launch_bounds__(MG_WARPS * 32)
-knn_merge_kernel(const float *__restrict__ in_d, const int32_t *__restrict__ in_i, int64_t nq, int kc, int nsplit,
-                 float *__restrict__ out_d, int32_t *__restrict__ out_i) {
-    extern __shared__ float mgs[];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int L = kc * nsplit;
-    float *d = mgs + (size_t)w * L * 2;
-    int *ix = reinterpret_cast<int *>(d + L);
-    const int64_t q = (int64_t)blockIdx.x * MG_WARPS + w;
-    if (q >= nq) return;
-    for (int c = lane; c < L; c += 32) {
-        d[c] = in_d[q * L + c];
-        ix[c] = in_i[q * L + c];
-    }
-    __syncwarp();
-    float *od = out_d + q * kc;
-    int32_t *oi = out_i + q * kc;
-    for (int c = lane; c < kc; c += 32) { od[c] = INFINITY; oi[c] = -1; }
-    __syncwarp();
-    for (int c = lane; c < L; c += 32) {
-        const int j = ix[c];
-        if (j < 0) continue;
-        const float dc = d[c];
-        int rank = 0;
-        for (int o = 0; o < L; ++o) {
-            const int jo = ix[o];
-            if (jo < 0) continue;
-            const float dd = d[o];
-            rank += (dd < dc) || (dd == dc && jo < j);
-        }
-        if (rank < kc) { od[rank] = dc; oi[rank] = j; }
-    }
-}
-
-cudaError_t launch_knn_merge(const float *in_d, const int32_t *in_i, int64_t nq, int kc, int nsplit, float *out_d,
-                             int32_t *out_i, cudaStream_t s) {
-    if (nq <= 0) return cudaSuccess;
-    const size_t smem = (size_t)MG_WARPS * kc * nsplit * 2 * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(knn_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    knn_merge_kernel<<<(unsigned)((nq + MG_WARPS - 1) / MG_WARPS), MG_WARPS * 32, smem, s>>>(in_d, in_i, nq, kc, nsplit,
-                                                                                             out_d, out_i);
     return cudaGetLastError();
 }
 

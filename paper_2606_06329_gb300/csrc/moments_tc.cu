@@ -24,11 +24,11 @@
 //   8 former warps    for every tile of the current pass, each thread forms
 //                     32 products of its tile row (HMUL2 on BF16 pairs) and
 //                     writes them with tcgen05.st straight into a TMEM slot
-//                     holding the A operand (four slots of 64 K-columns);
+//                     holding the A operand (2..8 slots of 64 K-columns);
 //   1 MMA warp        issues tcgen05.mma with A in TMEM, B in shared memory and
 //                     FP32 accumulators in TMEM, and releases each slot and
 //                     chunk buffer with tcgen05.commit.
-// TMEM holds the accumulators of up to 384/N tiles, so the tiles are covered
+// TMEM holds the accumulators of up to (512 - 32 slots)/N tiles, so the tiles are covered
 // in passes over the columns (the patch is re-read from L2).  After a pass the
 // formers read the accumulators back (tcgen05.ld) and store each row to its
 // destination.  Every wait is bounded (MECUCO_ERR_TIMEOUT, no trap); the MMA
@@ -48,9 +48,9 @@ constexpr int MT_PRODUCER_WARPS = 8;                  // gather, centre, pack
 constexpr int MT_FORMER_WARPS = 8;                     // row products into TMEM, drain
 constexpr int MT_THREADS = (MT_PRODUCER_WARPS + MT_FORMER_WARPS + 1) * 32;  // + the MMA warp
 constexpr int MT_CH = 64;                              // columns per chunk
-constexpr int MT_SLOTS = 4;                            // A slots in TMEM
+constexpr int MT_MAX_SLOTS = 8;                        // A slots in TMEM (runtime count, 2..8)
 constexpr int MT_SLOT_COLS = MT_CH / 2;                // 32-bit TMEM columns per slot
-constexpr int MT_D_COLS = 512 - MT_SLOTS * MT_SLOT_COLS;  // accumulator columns (384)
+constexpr int MT_GROUP = 1;                            // tiles a former writes per store wait
 constexpr int MT_XS_LD = 68;                           // FP32 staging row stride (floats)
 constexpr int MT_XP_LD = 36;                           // packed BF16x2 row stride (words)
 constexpr int MT_ROW_ONES = 64, MT_ROW_W = 65, MT_ROW_ZERO = 66, MT_XP_ROWS = 67;
@@ -163,7 +163,7 @@ template <typename T>
 __global__ void __launch_bounds__(MT_THREADS, 1)
 moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, const int32_t *__restrict__ idx, int k,
                   const int32_t *__restrict__ rowtab, int nrows, float *__restrict__ M, float *__restrict__ G,
-                  float *__restrict__ R, float *__restrict__ Q, DevCounters *ctr) {
+                  float *__restrict__ R, float *__restrict__ Q, int nslots, DevCounters *ctr) {
     extern __shared__ __align__(1024) uint8_t msm_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(msm_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *Bop0 = base;                                                       // 2 x B operand
@@ -171,7 +171,7 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
     float *Xs = reinterpret_cast<float *>(Xp0 + 2 * MT_XP_ROWS * MT_XP_LD);     // [64][68] FP32 staging
     float *Part = Xs + 64 * MT_XS_LD;                                           // [4][64] column partials
     int32_t *codes = reinterpret_cast<int32_t *>(Part + 4 * 64);                // [nrows]
-    __shared__ uint64_t slot_full[MT_SLOTS], slot_empty[MT_SLOTS];
+    __shared__ uint64_t slot_full[MT_MAX_SLOTS], slot_empty[MT_MAX_SLOTS];
     __shared__ uint64_t chunk_ready[2], formers_done[2], chunk_done[2], pass_done, d_free;
     __shared__ uint32_t tmem_slot;
     __shared__ int rows[64];
@@ -182,7 +182,8 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
     const int npairs = k * (k + 1) / 2;
     const int ntiles = nrows / 128;
     const int Nb = moments_tc_n(k);
-    const int tpp = min(ntiles, MT_D_COLS / Nb);
+    const int dcols = 512 - nslots * MT_SLOT_COLS;  // accumulator columns; the A slots follow
+    const int tpp = min(ntiles, dcols / Nb);
     const int npass = (ntiles + tpp - 1) / tpp;
     const int nchunks = (int)((m + MT_CH - 1) / MT_CH);
     const uint32_t idesc = tc::idesc_bf16_f32(128, Nb);
@@ -204,7 +205,7 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
         xp[MT_ROW_ZERO * MT_XP_LD + e % MT_XP_LD] = 0u;
     }
     if (tid == 0) {
-        for (int s = 0; s < MT_SLOTS; ++s) {
+        for (int s = 0; s < nslots; ++s) {
             tc::mbar_init(tc::smem_u32(&slot_full[s]), MT_FORMER_WARPS);
             tc::mbar_init(tc::smem_u32(&slot_empty[s]), 1);
         }
@@ -335,37 +336,46 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
                 if (lane == 0) wait(&chunk_ready[b], (gc >> 1) & 1);
                 __syncwarp();
                 const uint32_t *Xp = Xp0 + b * MT_XP_ROWS * MT_XP_LD;
-                for (int t = 0; t < nt; ++t, ++q) {
-                    const int s = q % MT_SLOTS;
-                    if (q >= MT_SLOTS) {
-                        if (lane == 0) wait(&slot_empty[s], ((q / MT_SLOTS) - 1) & 1);
-                        __syncwarp();
-                        tc::fence_after();
+                // tiles in groups of MT_GROUP: their stores are issued back to back and
+                // completed with one wait, so the store latency is paid once per group
+                for (int t = 0; t < nt; t += MT_GROUP) {
+                    const int cnt = min(MT_GROUP, nt - t);
+                    for (int u = 0; u < cnt; ++u) {
+                        const uint32_t qq = q + u;
+                        if (qq >= (uint32_t)nslots && lane == 0)
+                            wait(&slot_empty[qq % nslots], ((qq / nslots) - 1) & 1);
                     }
-                    const int code = codes[(t0 + t) * 128 + trow];
-                    const uint4 *pa = reinterpret_cast<const uint4 *>(Xp + (code & 0xff) * MT_XP_LD + half * 16);
-                    const uint4 *pb = reinterpret_cast<const uint4 *>(Xp + ((code >> 8) & 0xff) * MT_XP_LD + half * 16);
-                    uint32_t z[16];
+                    __syncwarp();
+                    tc::fence_after();
+                    for (int u = 0; u < cnt; ++u) {
+                        const int code = codes[(t0 + t + u) * 128 + trow];
+                        const uint4 *pa = reinterpret_cast<const uint4 *>(Xp + (code & 0xff) * MT_XP_LD + half * 16);
+                        const uint4 *pb =
+                            reinterpret_cast<const uint4 *>(Xp + ((code >> 8) & 0xff) * MT_XP_LD + half * 16);
+                        uint32_t z[16];
 #pragma unroll
-                    for (int e4 = 0; e4 < 4; ++e4) {
-                        const uint4 av = pa[e4], bv = pb[e4];
-                        const uint32_t aw[4] = {av.x, av.y, av.z, av.w};
-                        const uint32_t bw[4] = {bv.x, bv.y, bv.z, bv.w};
+                        for (int e4 = 0; e4 < 4; ++e4) {
+                            const uint4 av = pa[e4], bv = pb[e4];
+                            const uint32_t aw[4] = {av.x, av.y, av.z, av.w};
+                            const uint32_t bw[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            __nv_bfloat162 x = *reinterpret_cast<const __nv_bfloat162 *>(&aw[e]);
-                            __nv_bfloat162 y = *reinterpret_cast<const __nv_bfloat162 *>(&bw[e]);
-                            __nv_bfloat162 pr = __hmul2(x, y);
-                            z[e4 * 4 + e] = *reinterpret_cast<uint32_t *>(&pr);
+                            for (int e = 0; e < 4; ++e) {
+                                __nv_bfloat162 x = *reinterpret_cast<const __nv_bfloat162 *>(&aw[e]);
+                                __nv_bfloat162 y = *reinterpret_cast<const __nv_bfloat162 *>(&bw[e]);
+                                __nv_bfloat162 pr = __hmul2(x, y);
+                                z[e4 * 4 + e] = *reinterpret_cast<uint32_t *>(&pr);
+                            }
                         }
+                        tc::tmem_st_32x32b_x16(tmem + ((uint32_t)(qd * 32) << 16) +
+                                                   (uint32_t)(dcols + ((q + u) % nslots) * MT_SLOT_COLS + half * 16),
+                                               z);
                     }
-                    tc::tmem_st_32x32b_x16(tmem + ((uint32_t)(qd * 32) << 16) +
-                                               (uint32_t)(MT_D_COLS + s * MT_SLOT_COLS + half * 16),
-                                           z);
                     tc::tmem_st_wait();
                     tc::fence_before();
                     __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(tc::smem_u32(&slot_full[s]));
+                    if (lane == 0)
+                        for (int u = 0; u < cnt; ++u) tc::mbar_arrive(tc::smem_u32(&slot_full[(q + u) % nslots]));
+                    q += cnt;
                 }
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(tc::smem_u32(&formers_done[b]));
@@ -417,11 +427,11 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
                 for (int ci = 0; ci < nchunks; ++ci, ++gc) {
                     const uint32_t bsa = tc::smem_u32(Bop0 + (gc & 1) * MT_B_BYTES);
                     for (int t = 0; t < nt; ++t, ++q) {
-                        const int s = q % MT_SLOTS;
-                        wait(&slot_full[s], (q / MT_SLOTS) & 1);
+                        const int s = q % nslots;
+                        wait(&slot_full[s], (q / nslots) & 1);
                         tc::fence_after();
                         if (!*abortp) {
-                            const uint32_t a_t = tmem + (uint32_t)(MT_D_COLS + s * MT_SLOT_COLS);
+                            const uint32_t a_t = tmem + (uint32_t)(dcols + s * MT_SLOT_COLS);
 #pragma unroll
                             for (int kk = 0; kk < MT_CH / 16; ++kk)
                                 tc::mma_f16_ts(tmem + (uint32_t)(t * Nb), a_t + (uint32_t)(kk * 8),
@@ -448,9 +458,11 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
 
 cudaError_t launch_moments_tc(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, const int32_t *idx,
                               int k, int64_t np, const int32_t *rowtab, float *M, float *G, float *R, float *Q,
-                              DevCounters *ctr, cudaStream_t s) {
+                              int nslots, DevCounters *ctr, cudaStream_t s) {
     if (np <= 0) return cudaSuccess;
     if (k > 64 || k < 2) return cudaErrorInvalidValue;
+    if (nslots < 2 || nslots > MT_MAX_SLOTS || (512 - nslots * MT_SLOT_COLS) < moments_tc_n(k))
+        return cudaErrorInvalidValue;
     const int nrows = moments_tc_rows(k);
     if (nrows > MT_MAX_ROWS) return cudaErrorInvalidValue;
     const size_t smem = moments_tc_smem_bytes(k);
@@ -460,12 +472,12 @@ cudaError_t launch_moments_tc(const void *X, mecuco_dtype dt, int64_t N, int64_t
                                  (int)smem);
         if (e != cudaSuccess) return e;
         moments_tc_kernel<<<(unsigned)np, MT_THREADS, smem, s>>>((const __nv_bfloat16 *)X, N, m, ld, idx, k, rowtab,
-                                                                 nrows, M, G, R, Q, ctr);
+                                                                 nrows, M, G, R, Q, nslots, ctr);
     } else {
         e = cudaFuncSetAttribute(moments_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         moments_tc_kernel<<<(unsigned)np, MT_THREADS, smem, s>>>((const float *)X, N, m, ld, idx, k, rowtab, nrows, M,
-                                                                 G, R, Q, ctr);
+                                                                 G, R, Q, nslots, ctr);
     }
     return cudaGetLastError();
 }
