@@ -117,7 +117,8 @@ typedef enum {
     MECUCO_STAGE_ESTIMATOR = 7,  /* k-space Fast estimator */
     MECUCO_STAGE_ADJOINT = 8,    /* k-space adjoint + patch adjoint and scatter */
     MECUCO_STAGE_BASIS = 9,      /* tangent-basis expansion V_r = X_c^T U_p S^-1 */
-    MECUCO_STAGE_COUNT = 10
+    MECUCO_STAGE_EXACT = 10,     /* Exact mode: m x m covariance and K from its eigenbasis */
+    MECUCO_STAGE_COUNT = 11
 } mecuco_stage;
 
 /* Counters of the last completed call (valid after the stream is synchronised). */
@@ -223,6 +224,22 @@ MECUCO_API mecuco_status mecuco_curvature_backward(mecuco_t h, const void *X, me
 MECUCO_API mecuco_status mecuco_tangent_basis(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m,
                                               int64_t ld, int k, const int32_t *idx, int64_t row_begin,
                                               int64_t row_end, int d_out, float *V_out, void *stream);
+
+/* Exact mode (Theorem 1; eq. exact_curv) for the points [row_begin, row_end):
+ * Sigma = X_c^T X_c / (k - 1) (m x m), Sigma = W diag(v) W^T (FP32 Jacobi
+ * sweeps + FP64 refinement, v descending), C = W^T W^{o2} and
+ * K = | 1/2 v^T (C^{o2} 1) + 1/2 sum v |.  The paper's automatic mode uses it
+ * for m < 50.  Requires m <= 64.  When m > k - 1, Sigma has a null space and K
+ * depends on the eigenbasis returned for it (the identity sums over every
+ * column of W); W_out exposes that basis.
+ *   idx      device N x k neighbour lists, or NULL to compute them (prec)
+ *   kappa_out device, (row_end - row_begin) floats
+ *   v_out    device, (row_end - row_begin) x m floats, or NULL
+ *   W_out    device, (row_end - row_begin) x m x m floats (row i, column s), or NULL */
+MECUCO_API mecuco_status mecuco_curvature_exact(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m,
+                                                int64_t ld, int k, const int32_t *idx, int include_self,
+                                                mecuco_precision prec, int64_t row_begin, int64_t row_end,
+                                                float *kappa_out, float *v_out, float *W_out, void *stream);
 
 /* One dataset of a batched call. */
 typedef struct {

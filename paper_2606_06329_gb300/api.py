@@ -137,6 +137,34 @@ class Context:
         N.check(st, "mecuco_curvature_range")
         return kappa
 
+    def mecuco_curvature_exact(self, X: torch.Tensor, k: int, idx=None, include_self: bool = False,
+                               precision: str = "fp32", row_begin: int = 0, row_end=None, return_basis: bool = False):
+        """Exact-mode (Theorem 1) curvature of rows [row_begin, row_end); with return_basis also the
+        covariance eigenvalues v (rows x m) and eigenvectors W (rows x m x m) it used."""
+        _check_x(X, self.device)
+        n, m = X.shape
+        re = n if row_end is None else int(row_end)
+        rows = re - int(row_begin)
+        if idx is not None and (idx.dtype != torch.int32 or tuple(idx.shape) != (n, k) or not idx.is_contiguous()):
+            raise ValueError("idx must be a contiguous int32 (N, k) tensor")
+        kap = torch.empty(rows, dtype=torch.float32, device=X.device)
+        v = torch.empty((rows, m), dtype=torch.float32, device=X.device) if return_basis else None
+        W = torch.empty((rows, m, m), dtype=torch.float32, device=X.device) if return_basis else None
+        st = self.lib.mecuco_curvature_exact(self.handle, _ptr(X), _dtype_code(X), n, m, X.stride(0), int(k),
+                                             _ptr(idx) if idx is not None else None, int(bool(include_self)),
+                                             _PREC[precision], int(row_begin), re, _ptr(kap),
+                                             _ptr(v) if v is not None else None, _ptr(W) if W is not None else None,
+                                             _stream(self.device))
+        N.check(st, "mecuco_curvature_exact")
+        return (kap, v, W) if return_basis else kap
+
+    def curvature_auto(self, X: torch.Tensor, k: int, idx=None, **kw):
+        """The paper's automatic mode: Exact (Theorem 1) for m < 50, Fast otherwise."""
+        if X.shape[1] < 50:
+            return self.mecuco_curvature_exact(X, k, idx=idx, include_self=kw.get("include_self", False),
+                                               precision=kw.get("precision", "fp32"))
+        return self.mecuco_curvature(X, k, idx=idx, **kw)
+
     def _datasets(self, Xs, ks, idx_out):
         if len(Xs) != len(ks) or not Xs:
             raise ValueError("one k per dataset")

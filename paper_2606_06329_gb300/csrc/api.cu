@@ -786,6 +786,52 @@ mecuco_status mecuco_tangent_basis(mecuco_t h, const void *X, mecuco_dtype dt, i
     return MECUCO_OK;
 }
 
+mecuco_status mecuco_curvature_exact(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
+                                     int k, const int32_t *idx, int include_self, mecuco_precision prec, int64_t rb,
+                                     int64_t re, float *kappa_out, float *v_out, float *W_out, void *stream) {
+    mecuco_status st = check_common(h, X, dt, N, m, ld, k, include_self);
+    if (st != MECUCO_OK) return st;
+    if ((st = check_range(N, rb, re)) != MECUCO_OK) return st;
+    if (!kappa_out || m > 64) return MECUCO_ERR_INVALID_ARG;
+    if (prec != MECUCO_PREC_FP32 && prec != MECUCO_PREC_BF16_MIXED) return MECUCO_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = begin_call(h, s)) != MECUCO_OK) return st;
+    const int64_t nrows = re - rb;
+    const int64_t chunk = std::min<int64_t>(h->chunk_points > 0 ? h->chunk_points : 65536, nrows);
+    const size_t idx_bytes = idx ? 0 : align_up((size_t)nrows * k * sizeof(int32_t), 256);
+    Carver t(nullptr, idx_bytes);
+    t.take<float>((size_t)chunk * m * m);
+    t.take<float>((size_t)chunk * m);
+    t.take<float>((size_t)chunk * m * m);
+    size_t need = t.off;
+    if (!idx) need = std::max(need, knn_bytes(h, X, dt, N, m, ld, nrows, k, prec, idx_bytes));
+    if ((st = ensure(h->ws, h->ws_bytes, need)) != MECUCO_OK) return st;
+    const int32_t *nbr = idx ? idx + rb * k : nullptr;
+    if (!idx) {
+        int32_t *idx_buf = reinterpret_cast<int32_t *>(h->ws);
+        if ((st = run_knn(h, h->ws, X, dt, N, m, ld, k, include_self, prec, rb, re, idx_buf, nullptr, s,
+                          idx_bytes)) != MECUCO_OK)
+            return st;
+        nbr = idx_buf;
+    }
+    Carver c(h->ws, idx_bytes);
+    float *S = c.take<float>((size_t)chunk * m * m);
+    float *vb = c.take<float>((size_t)chunk * m);
+    float *Wb = c.take<float>((size_t)chunk * m * m);
+    const int mode = h->jacobi_fp64 >= 0 ? h->jacobi_fp64 : 1;
+    const int mm = (int)m;
+    for (int64_t p0 = 0; p0 < nrows; p0 += chunk) {
+        const int64_t np = std::min(chunk, nrows - p0);
+        float *vd = v_out ? v_out + p0 * m : vb;
+        float *Wd = W_out ? W_out + p0 * m * m : Wb;
+        LAUNCH(h, MECUCO_STAGE_EXACT, s, launch_exact_cov(X, dt, N, m, ld, nbr + p0 * k, k, np, S, h->ctr, s));
+        LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(S, mm, np, mode, h->jacobi_max_sweeps, vd, Wd, h->ctr, s));
+        if (mode == 1 || mode == 3) ++h->launches;
+        LAUNCH(h, MECUCO_STAGE_EXACT, s, launch_exact_kappa(vd, Wd, mm, np, kappa_out + p0, s));
+    }
+    return MECUCO_OK;
+}
+
 mecuco_status mecuco_curvature_batched(mecuco_t h, const mecuco_dataset *sets, int nsets, mecuco_dtype dt,
                                        int include_self, mecuco_variant var, mecuco_precision prec, void *stream) {
     mecuco_status st = check_batch(h, sets, nsets, dt, include_self, var, prec);

@@ -135,6 +135,13 @@ inline float rank_eps_rotated(int k, int64_t m) {
 cudaError_t launch_compose_rotation(const float *U0, const float *V, int k, int64_t np, float *U_out,
                                     cudaStream_t s);
 
+// ---- Exact mode ---------------------------------------------------------------
+// S (np x m x m) = X_c^T X_c / (k - 1) of each point's patch (m <= 64); then
+// kappa (np) from the eigenpairs (v np x m descending, W np x m x m) of S.
+cudaError_t launch_exact_cov(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, const int32_t *idx,
+                             int k, int64_t np, float *S, DevCounters *ctr, cudaStream_t s);
+cudaError_t launch_exact_kappa(const float *v, const float *W, int m, int64_t np, float *kappa, cudaStream_t s);
+
 // ---- tangent bases ------------------------------------------------------------
 // V (np x m x d_out, l fastest) = X_c^T U_p S^-1 for the points of one chunk
 // (idx offset to the chunk), sigma/U from launch_jacobi.
