@@ -118,7 +118,8 @@ typedef enum {
     MECUCO_STAGE_ADJOINT = 8,    /* k-space adjoint + patch adjoint and scatter */
     MECUCO_STAGE_BASIS = 9,      /* tangent-basis expansion V_r = X_c^T U_p S^-1 */
     MECUCO_STAGE_EXACT = 10,     /* Exact mode: m x m covariance and K from its eigenbasis */
-    MECUCO_STAGE_COUNT = 11
+    MECUCO_STAGE_FIDELITY = 11,  /* agreement metrics: sorts, ranks, sums */
+    MECUCO_STAGE_COUNT = 12
 } mecuco_stage;
 
 /* Counters of the last completed call (valid after the stream is synchronised). */
@@ -240,6 +241,33 @@ MECUCO_API mecuco_status mecuco_curvature_exact(mecuco_t h, const void *X, mecuc
                                                 int64_t ld, int k, const int32_t *idx, int include_self,
                                                 mecuco_precision prec, int64_t row_begin, int64_t row_end,
                                                 float *kappa_out, float *v_out, float *W_out, void *stream);
+
+/* Theorem 1 (eq. exact_curv) evaluated on caller-supplied eigenpairs of each
+ * point's covariance: C = W^T W^{o2} and K = |1/2 sum_s v_s sum_l C_sl^2 + 1/2 sum_s v_s|.
+ * With the range eigenvectors fixed and the null-space columns of W drawn from
+ * the Haar measure, the mean of K over draws is what eq. gnull_exp's
+ * expectation (the Fast mode's null-space term) stands for.
+ *   v        device, np x m floats (eigenvalues; any order matching W's columns)
+ *   W        device, np x m x m floats, row-major, column s = eigenvector s
+ *   kappa    device, np floats (written)
+ * 1 <= m <= 64; no workspace. */
+MECUCO_API mecuco_status mecuco_exact_kappa(mecuco_t h, const float *v, const float *W, int64_t m, int64_t np,
+                                            float *kappa, void *stream);
+
+/* The paper's agreement metrics between a reference curvature vector and
+ * another (the curvature-fidelity experiments): mean absolute error, Spearman's
+ * rank correlation rho_S (Pearson correlation of average ranks) and
+ * Chatterjee's xi with the pairs ordered by the reference (ties by index) in
+ * the form that allows ties, 1 - n sum |r_{i+1} - r_i| / (2 sum l_i (n - l_i)).
+ * With normalize != 0 each vector is first min-max normalised to [0, 1] (the
+ * normalisation experiments); rho_S and xi do not change under it.
+ *   kappa_ref, kappa  device, n floats (2 <= n < 2^31)
+ *   metrics_out       device, 3 doubles: MAE, rho_S, xi */
+MECUCO_API mecuco_status mecuco_fidelity(mecuco_t h, const float *kappa_ref, const float *kappa, int64_t n,
+                                         int normalize, double *metrics_out, void *stream);
+
+/* y = (x - min x) / (max x - min x), 0 where max = min; x, y device, n floats. */
+MECUCO_API mecuco_status mecuco_minmax_normalize(mecuco_t h, const float *x, int64_t n, float *y, void *stream);
 
 /* One dataset of a batched call. */
 typedef struct {

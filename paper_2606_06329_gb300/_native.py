@@ -19,7 +19,7 @@ PREC_FP32, PREC_BF16_MIXED = 0, 1
 (OPT_KNN_MARGIN, OPT_JACOBI_FP64, OPT_JACOBI_MAX_SWEEPS, OPT_CHUNK_POINTS, OPT_KNN_QUERY_CHUNK, OPT_PROFILE,
  OPT_KNN_SPLITS, OPT_BATCH_LANES, OPT_TC_SLOTS) = range(9)
 STAGES = ("rownorm", "knn_search", "knn_rerank", "knn_fallback", "gram", "moments", "jacobi", "estimator", "adjoint",
-          "basis", "exact")
+          "basis", "exact", "fidelity")
 
 
 class MecucoNotBuilt(ImportError):
@@ -66,6 +66,9 @@ SIGNATURES = {
     "mecuco_tangent_basis": (_st, [_p, _p, _i32, _i64, _i64, _i64, _i32, _p, _i64, _i64, _i32, _p, _p]),
     "mecuco_curvature_exact": (_st, [_p, _p, _i32, _i64, _i64, _i64, _i32, _p, _i32, _i32, _i64, _i64, _p, _p, _p,
                                      _p]),
+    "mecuco_exact_kappa": (_st, [_p, _p, _p, _i64, _i64, _p, _p]),
+    "mecuco_fidelity": (_st, [_p, _p, _p, _i64, _i32, _p, _p]),
+    "mecuco_minmax_normalize": (_st, [_p, _p, _i64, _p, _p]),
     "mecuco_curvature_batched": (_st, [_p, C.POINTER(mecuco_dataset), _i32, _i32, _i32, _i32, _i32, _p]),
     "mecuco_autotune_batched": (_st, [_p, C.POINTER(mecuco_dataset), _i32, _i32, _i32, _i32, _i32, _p,
                                       C.POINTER(C.c_int)]),

@@ -158,6 +158,39 @@ class Context:
         N.check(st, "mecuco_curvature_exact")
         return (kap, v, W) if return_basis else kap
 
+    def mecuco_exact_kappa(self, v: torch.Tensor, W: torch.Tensor) -> torch.Tensor:
+        """Theorem 1 on supplied eigenpairs: v (np, m), W (np, m, m), column s = eigenvector s."""
+        dev = f"cuda:{self.device}"
+        v = v.to(device=dev, dtype=torch.float32).contiguous()
+        W = W.to(device=dev, dtype=torch.float32).contiguous()
+        if v.dim() != 2 or W.shape != (v.shape[0], v.shape[1], v.shape[1]):
+            raise ValueError("v must be (np, m) and W (np, m, m)")
+        kappa = torch.empty(v.shape[0], dtype=torch.float32, device=dev)
+        st = self.lib.mecuco_exact_kappa(self.handle, _ptr(v), _ptr(W), v.shape[1], v.shape[0], _ptr(kappa),
+                                         _stream(self.device))
+        N.check(st, "mecuco_exact_kappa")
+        return kappa
+
+    def mecuco_fidelity(self, kappa_ref: torch.Tensor, kappa: torch.Tensor, normalize: bool = False):
+        """(MAE, Spearman rho_S, Chatterjee xi) of kappa against kappa_ref."""
+        a = kappa_ref.to(device=f"cuda:{self.device}", dtype=torch.float32).contiguous()
+        b = kappa.to(device=f"cuda:{self.device}", dtype=torch.float32).contiguous()
+        if a.numel() != b.numel():
+            raise ValueError("the two vectors differ in length")
+        out = torch.empty(3, dtype=torch.float64, device=a.device)
+        st = self.lib.mecuco_fidelity(self.handle, _ptr(a), _ptr(b), a.numel(), int(bool(normalize)), _ptr(out),
+                                      _stream(self.device))
+        N.check(st, "mecuco_fidelity")
+        mae, rho, xi = out.cpu().tolist()
+        return mae, rho, xi
+
+    def mecuco_minmax_normalize(self, x: torch.Tensor) -> torch.Tensor:
+        x = x.to(dtype=torch.float32).contiguous()
+        y = torch.empty_like(x)
+        st = self.lib.mecuco_minmax_normalize(self.handle, _ptr(x), x.numel(), _ptr(y), _stream(self.device))
+        N.check(st, "mecuco_minmax_normalize")
+        return y
+
     def curvature_auto(self, X: torch.Tensor, k: int, idx=None, **kw):
         """The paper's automatic mode: Exact (Theorem 1) for m < 50, Fast otherwise."""
         if X.shape[1] < 50:

@@ -832,6 +832,38 @@ mecuco_status mecuco_curvature_exact(mecuco_t h, const void *X, mecuco_dtype dt,
     return MECUCO_OK;
 }
 
+mecuco_status mecuco_exact_kappa(mecuco_t h, const float *v, const float *W, int64_t m, int64_t np, float *kappa,
+                                 void *stream) {
+    if (!h || !v || !W || !kappa || m < 1 || m > 64 || np < 0 || np >= ((int64_t)1 << 31))
+        return MECUCO_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    mecuco_status st;
+    if ((st = begin_call(h, s)) != MECUCO_OK) return st;
+    LAUNCH(h, MECUCO_STAGE_EXACT, s, launch_exact_kappa(v, W, (int)m, np, kappa, s));
+    return MECUCO_OK;
+}
+
+mecuco_status mecuco_fidelity(mecuco_t h, const float *kappa_ref, const float *kappa, int64_t n, int normalize,
+                              double *metrics_out, void *stream) {
+    if (!h || !kappa_ref || !kappa || !metrics_out || n < 2 || n >= ((int64_t)1 << 31)) return MECUCO_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    mecuco_status st;
+    if ((st = begin_call(h, s)) != MECUCO_OK) return st;
+    if ((st = ensure(h->ws, h->ws_bytes, fidelity_scratch_bytes(n))) != MECUCO_OK) return st;
+    LAUNCH(h, MECUCO_STAGE_FIDELITY, s, launch_fidelity(kappa_ref, kappa, n, normalize != 0, h->ws, metrics_out, s));
+    return MECUCO_OK;
+}
+
+mecuco_status mecuco_minmax_normalize(mecuco_t h, const float *x, int64_t n, float *y, void *stream) {
+    if (!h || !x || !y || n < 1) return MECUCO_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    mecuco_status st;
+    if ((st = begin_call(h, s)) != MECUCO_OK) return st;
+    if ((st = ensure(h->ws, h->ws_bytes, 8192)) != MECUCO_OK) return st;
+    LAUNCH(h, MECUCO_STAGE_FIDELITY, s, launch_minmax_normalize(x, n, y, h->ws, s));
+    return MECUCO_OK;
+}
+
 mecuco_status mecuco_curvature_batched(mecuco_t h, const mecuco_dataset *sets, int nsets, mecuco_dtype dt,
                                        int include_self, mecuco_variant var, mecuco_precision prec, void *stream) {
     mecuco_status st = check_batch(h, sets, nsets, dt, include_self, var, prec);

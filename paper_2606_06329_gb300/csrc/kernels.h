@@ -142,6 +142,16 @@ cudaError_t launch_exact_cov(const void *X, mecuco_dtype dt, int64_t N, int64_t 
                              int k, int64_t np, float *S, DevCounters *ctr, cudaStream_t s);
 cudaError_t launch_exact_kappa(const float *v, const float *W, int m, int64_t np, float *kappa, cudaStream_t s);
 
+// ---- agreement metrics ----------------------------------------------------------
+// out[0..2] (device) = MAE, Spearman rho_S, Chatterjee xi between a (reference)
+// and b, after min-max normalisation of each when normalize != 0; scratch of
+// fidelity_scratch_bytes(n).  launch_minmax_normalize: y = (x - min) / (max - min)
+// with 8 KB of scratch.
+size_t fidelity_scratch_bytes(int64_t n);
+cudaError_t launch_fidelity(const float *a, const float *b, int64_t n, int normalize, void *scratch, double *out,
+                            cudaStream_t s);
+cudaError_t launch_minmax_normalize(const float *x, int64_t n, float *y, void *scratch, cudaStream_t s);
+
 // ---- tangent bases ------------------------------------------------------------
 // V (np x m x d_out, l fastest) = X_c^T U_p S^-1 for the points of one chunk
 // (idx offset to the chunk), sigma/U from launch_jacobi.
