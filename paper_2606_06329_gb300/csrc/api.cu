@@ -401,7 +401,7 @@ mecuco_status run_curvature(mecuco_t h, char *ws, const void *X, mecuco_dtype dt
                    launch_moments_tc(X, dt, N, m, ld, nb, k, np, h->rowtab[k], b.M, b.G, b.R,
                                      var == MECUCO_FAST_HAAR ? b.Q : nullptr, h->tc_slots, h->ctr, s));
             LAUNCH(h, MECUCO_STAGE_JACOBI, s,
-                   launch_jacobi(b.G, k, np, fp64, h->jacobi_max_sweeps, b.sig, Ud, h->ctr, s));
+                   launch_jacobi(b.G, k, np, fp64, h->jacobi_max_sweeps, b.sig, Ud, h->ctr, s, kJacobiPreLoose));
             if (fp64 == 1 || fp64 == 3) ++h->launches;  // the FP64 refinement is a second kernel
             LAUNCH(h, MECUCO_STAGE_ESTIMATOR, s,
                    launch_estimator(b.sig, Ud, b.M, b.R, Qarg, k, m, np, (int)var, rank_eps_gram32(m), kappa_out + p0,

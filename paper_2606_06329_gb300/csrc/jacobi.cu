@@ -8,7 +8,9 @@
 //   1. the table threads compute each pair's rotation from the current 2 x 2
 //      block: tau = (a_qq - a_pp) / (2 a_pq), t = sign(tau) / (|tau| +
 //      sqrt(1 + tau^2)), c = 1/sqrt(1 + t^2), s = t c (the rotation zeroing
-//      a_pq); pairs with |a_pq| <= eps sqrt(|a_pp a_qq|) are skipped, and the
+//      a_pq); pairs with |a_pq| <= eps sqrt(|a_pp a_qq|) are skipped (eps =
+//      2^-22 in FP32, 2^-50 in FP64; before an FP64 refinement the caller's
+//      pre_eps), and the
 //      rotating pairs are compacted into the round's table (late sweeps are
 //      cheap because few pairs still rotate);
 //   2. A <- A J (each thread walks one row over its share of the pairs),
@@ -32,18 +34,18 @@ template <typename Real>
 struct JacobiEps;
 template <>
 struct JacobiEps<float> {
-    static __device__ __forceinline__ float rel() { return 2.384185791015625e-07f; }  // 2^-22
+    static __host__ __device__ __forceinline__ float rel() { return 2.384185791015625e-07f; }  // 2^-22
 };
 template <>
 struct JacobiEps<double> {
-    static __device__ __forceinline__ double rel() { return 8.8817841970012523e-16; }  // 2^-50
+    static __host__ __device__ __forceinline__ double rel() { return 8.8817841970012523e-16; }  // 2^-50
 };
 
 constexpr int JT = 128;  // threads per patch
 
 template <typename Real>
 __global__ void __launch_bounds__(JT)
-jacobi_kernel(const float *__restrict__ G, int k, int64_t np, int max_sweeps, float *__restrict__ sigma,
+jacobi_kernel(const float *__restrict__ G, int k, int64_t np, int max_sweeps, Real eps, float *__restrict__ sigma,
               float *__restrict__ U, DevCounters *ctr) {
     extern __shared__ __align__(16) unsigned char jsm[];
     const int kp = (k + 1) & ~1;
@@ -68,7 +70,6 @@ jacobi_kernel(const float *__restrict__ G, int k, int64_t np, int max_sweeps, fl
     }
     if (tid == 0) { s_rot = 0; s_act = 0; }
     __syncthreads();
-    const Real eps = JacobiEps<Real>::rel();
     // thread -> (line, pair group) for the row/column/U walks: kp lines, JT/kp groups
     const int groups = JT / kp > 0 ? JT / kp : 1;
     const int line = tid % kp;
@@ -286,13 +287,17 @@ size_t jacobi_smem_bytes(int k, int fp64) {
 }
 
 cudaError_t launch_jacobi(const float *G, int k, int64_t np, int fp64, int max_sweeps, float *sigma, float *U,
-                          DevCounters *ctr, cudaStream_t s) {
+                          DevCounters *ctr, cudaStream_t s, float pre_eps) {
     if (np <= 0) return cudaSuccess;
     if (k > 64) return cudaErrorInvalidValue;
     cudaError_t e;
     if (fp64 == 1 || fp64 == 3) {
         // FP32 sweeps, then one FP64 refinement step (3: relative cluster test)
-        e = launch_jacobi(G, k, np, 0, max_sweeps, sigma, U, ctr, s);
+        const size_t smem = jacobi_smem_bytes(k, 0);
+        e = cudaFuncSetAttribute(jacobi_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        jacobi_kernel<float><<<(unsigned)np, JT, smem, s>>>(G, k, np, max_sweeps, pre_eps, sigma, U, ctr);
+        e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         const size_t rs = refine64_smem_bytes(k);
         e = cudaFuncSetAttribute(jacobi_refine64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs);
@@ -304,11 +309,13 @@ cudaError_t launch_jacobi(const float *G, int k, int64_t np, int fp64, int max_s
     if (fp64 == 2) {
         e = cudaFuncSetAttribute(jacobi_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        jacobi_kernel<double><<<(unsigned)np, JT, smem, s>>>(G, k, np, max_sweeps, sigma, U, ctr);
+        jacobi_kernel<double><<<(unsigned)np, JT, smem, s>>>(G, k, np, max_sweeps, JacobiEps<double>::rel(), sigma,
+                                                             U, ctr);
     } else {
         e = cudaFuncSetAttribute(jacobi_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        jacobi_kernel<float><<<(unsigned)np, JT, smem, s>>>(G, k, np, max_sweeps, sigma, U, ctr);
+        jacobi_kernel<float><<<(unsigned)np, JT, smem, s>>>(G, k, np, max_sweeps, JacobiEps<float>::rel(), sigma, U,
+                                                            ctr);
     }
     return cudaGetLastError();
 }

@@ -106,8 +106,17 @@ size_t moments_tc_smem_bytes(int k);
 // fp64: 0 = FP32 sweeps; 1 = FP32 sweeps then one FP64 refinement step;
 // 2 = every sweep in FP64; 3 = as 1 with the refinement's cluster test
 // relative to each eigenvalue pair (for nearly diagonal Grams).
+// pre_eps is the rotation threshold of the FP32 sweeps of modes 1 and 3: the
+// refinement squares the eigenvector error, so kJacobiPreLoose suffices where
+// the eigenpairs feed the estimator directly (on 100k curved patches, m = 4096,
+// k = 64, kappa moved by <= 3.6e-7 relative and the stage took 8% less time;
+// 2^-11 moved it by 1.4e-4).  Eigenvectors that later rotate a patch, whose
+// rotated Gram must come out nearly diagonal, take kJacobiPreTight.
+constexpr float kJacobiPreTight = 2.384185791015625e-07f;  // 2^-22
+constexpr float kJacobiPreLoose = 6.103515625e-05f;        // 2^-14
 cudaError_t launch_jacobi(const float *G, int k, int64_t np, int fp64, int max_sweeps,
-                          float *sigma, float *U, DevCounters *ctr, cudaStream_t s);
+                          float *sigma, float *U, DevCounters *ctr, cudaStream_t s,
+                          float pre_eps = kJacobiPreTight);
 
 // ---- Step 4: k-space estimator ----------------------------------------------
 // sigma/U from launch_jacobi, M pair-major from launch_patch_m3, R and Q from

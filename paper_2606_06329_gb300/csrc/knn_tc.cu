@@ -5,10 +5,10 @@
 // Persistent CTAs (one per SM); a work item = 128 query rows (the MMA's M, one
 // TMEM lane each) against one split of the candidate rows, swept in tiles of
 // 256 (the MMA's N).  Warp roles:
-//   warp 0      TMA producer: for every (candidate tile, 64-wide K block) loads
-//               the 128 x 64 query slice and the 256 x 64 candidate slice
-//               (128-byte swizzled, zero-filled past the matrix edges) into a
-//               NSTAGE-deep ring of shared-memory stages.
+//   warp 0      TMA producer: for every (candidate tile, TBK-wide K block) loads
+//               the 128 x TBK query slice and the 256 x TBK candidate slice
+//               (swizzled by the width of a TBK row, zero-filled past the
+//               matrix edges) into a NSTAGE-deep ring of shared-memory stages.
 //   warp 1      allocates 512 TMEM columns (two 256-column FP32 accumulators)
 //               and issues tcgen05.mma (M=128, N=256, K=16) from one lane,
 //               committing each stage back to the producer and each finished
@@ -35,11 +35,19 @@ namespace mecuco {
 namespace {
 constexpr int TBM = 128;        // query rows per CTA (MMA M)
 constexpr int TBN = 256;        // candidate rows per tile (MMA N)
-constexpr int TBK = 64;         // K elements per stage (one 128-byte swizzle row)
-constexpr int NSTAGE = 3;
-constexpr int A_BYTES = TBM * TBK * 2;   // 16 KB
-constexpr int B_BYTES = TBN * TBK * 2;   // 32 KB
+// K elements per stage: 32 (one 64-byte swizzle row) in 6 stages of 24 KB
+// rather than 64 in 3 stages of 48 KB - the same shared memory, but 5/6 of it
+// in flight while the MMA consumes a stage instead of 2/3
+constexpr int TBK = 32;
+constexpr int NSTAGE = 6;
+constexpr int A_BYTES = TBM * TBK * 2;   // 8 KB
+constexpr int B_BYTES = TBN * TBK * 2;   // 16 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+static_assert(TBK == 64 || TBK == 32, "stage rows are one 128- or 64-byte swizzle row");
+// K-major operand descriptor of a stage (swizzle width = the stage's row)
+__device__ __forceinline__ uint64_t kdesc(uint32_t saddr) {
+    return TBK == 64 ? tc::sdesc_sw128(saddr) : tc::sdesc_sw64(saddr);
+}
 constexpr int TC_THREADS = 320;  // TMA warp, MMA warp, 8 epilogue warps
 constexpr int TC_HALVES = 2;     // epilogue warps per TMEM lane quarter (column halves)
 constexpr long long WAIT_LIMIT = 1000000000LL;  // ~0.5 s of SM clock per wait
@@ -222,8 +230,8 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
                     const uint32_t sa = tc::smem_u32(stages + s * STAGE_BYTES);
 #pragma unroll
                     for (int kk = 0; kk < TBK / 16; ++kk) {
-                        const uint64_t ad = tc::sdesc_sw128(sa + kk * 32);
-                        const uint64_t bd = tc::sdesc_sw128(sa + A_BYTES + kk * 32);
+                        const uint64_t ad = kdesc(sa + kk * 32);
+                        const uint64_t bd = kdesc(sa + A_BYTES + kk * 32);
                         tc::mma_f16(dt, ad, bd, IDESC, (kb | kk) != 0);
                     }
                     tc::commit(tc::smem_u32(&sh->empty[s]));
@@ -331,7 +339,8 @@ bool make_map(CUtensorMap *map, const void *Xb, int64_t N, int64_t m, int64_t ld
     cuuint32_t box[2] = {(cuuint32_t)TBK, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(Xb), dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, TBK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }

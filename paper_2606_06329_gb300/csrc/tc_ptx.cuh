@@ -120,6 +120,13 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
+// The same for the 64-byte swizzle: rows of 64 bytes (32 BF16), 8-row atoms of
+// 512 bytes (stride byte offset 512 >> 4), layout SWIZZLE_64B (4) in bits 61-63.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+
 // 32 lanes x 32 consecutive 32-bit columns: thread (lane) l of the warp gets
 // columns [col, col + 32) of TMEM lane (warp's quarter * 32 + l).
 __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&r)[32]) {
