@@ -80,15 +80,17 @@ typedef enum { MECUCO_FAST_LITERAL = 0, MECUCO_FAST_HAAR = 1 } mecuco_variant;
  *               accumulation and an FP32 exact re-rank of the candidates;
  *               patch moments (G, R, Q, third moments) from BF16 operands on
  *               the tensor cores with FP32 accumulation; Jacobi sweeps in FP32
- *               followed by an FP64 refinement of the eigenpairs (FP64
- *               products and eigenvector accumulation).  (the chosen form) */
+ *               followed by one refinement step of the eigenpairs whose
+ *               products are carried beyond FP32 (two-term FP32, ~2^-48
+ *               relative).  (the chosen form) */
 typedef enum { MECUCO_PREC_FP32 = 0, MECUCO_PREC_BF16_MIXED = 1 } mecuco_precision;
 
 /* Tunable options (mecuco_set_option).  Values are int64. */
 typedef enum {
     MECUCO_OPT_KNN_MARGIN = 0,       /* extra candidates kept per row before the exact re-rank (default 32) */
     MECUCO_OPT_JACOBI_FP64 = 1,      /* -1: by precision (default: 0 for FP32, 1 for BF16_MIXED);
-                                        0: FP32 sweeps; 1: FP32 sweeps + one FP64 refinement step;
+                                        0: FP32 sweeps; 1: FP32 sweeps + one refinement step in
+                                        two-term FP32 (FP64-class products);
                                         2: every sweep in FP64; 3: as 1, eigenvalue clusters judged
                                         relative to each pair.  The adjoint's rotated Gram uses 3
                                         unless this option is set */
@@ -199,7 +201,7 @@ MECUCO_API mecuco_status mecuco_curvature_range(mecuco_t h, const void *X, mecuc
  * and eigenpairs are recomputed (nothing is kept from the forward call) in
  * FP32 on a rotated copy of the patch (U0^T X_c, U0 the eigenvectors of a
  * first Gram, which leaves K unchanged and keeps the small eigenvalues
- * accurate), with FP64 refinement of the eigenpairs; the per-point adjoint
+ * accurate), with refined eigenpairs (two-term FP32); the per-point adjoint
  * runs in k-space (through the derivative of the symmetric eigendecomposition,
  * which is unbounded for coinciding eigenvalues) and is scattered onto the
  * neighbour rows with atomic adds (summation order, hence the last bits, vary
@@ -228,7 +230,7 @@ MECUCO_API mecuco_status mecuco_tangent_basis(mecuco_t h, const void *X, mecuco_
 
 /* Exact mode (Theorem 1; eq. exact_curv) for the points [row_begin, row_end):
  * Sigma = X_c^T X_c / (k - 1) (m x m), Sigma = W diag(v) W^T (FP32 Jacobi
- * sweeps + FP64 refinement, v descending), C = W^T W^{o2} and
+ * sweeps + refinement step, v descending), C = W^T W^{o2} and
  * K = | 1/2 v^T (C^{o2} 1) + 1/2 sum v |.  The paper's automatic mode uses it
  * for m < 50.  Requires m <= 64.  When m > k - 1, Sigma has a null space and K
  * depends on the eigenbasis returned for it (the identity sums over every

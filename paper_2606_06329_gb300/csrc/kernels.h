@@ -103,7 +103,8 @@ size_t moments_tc_smem_bytes(int k);
 // ---- Step 3: k x k eigensolve -----------------------------------------------
 // Parallel-order two-sided Jacobi, one CTA per patch.  G: np x k x k.
 // Outputs sigma (np x k, descending) and U (np x k x k, column l = eigenvector).
-// fp64: 0 = FP32 sweeps; 1 = FP32 sweeps then one FP64 refinement step;
+// fp64: 0 = FP32 sweeps; 1 = FP32 sweeps then one refinement step (products
+// in two-term FP32, ~2^-48 relative);
 // 2 = every sweep in FP64; 3 = as 1 with the refinement's cluster test
 // relative to each eigenvalue pair (for nearly diagonal Grams).
 // pre_eps is the rotation threshold of the FP32 sweeps of modes 1 and 3: the
