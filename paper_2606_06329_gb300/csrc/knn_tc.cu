@@ -169,8 +169,13 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
     if (warp == 0) {
         // ------------------------------ TMA producer ----------------------------
         if (lane == 0) {
+            // one thread issues every load: stage index and phase are running
+            // counters, so the loop carries no division
             int it = 0;
+            uint32_t s = 0, ph = 0;
             bool ok = true;
+            const uint32_t st0 = tc::smem_u32(stages), full0 = tc::smem_u32(&sh->full[0]),
+                           empty0 = tc::smem_u32(&sh->empty[0]);
             for (int64_t item = blockIdx.x; item < nitems && ok && !*abort_flag; item += gridDim.x) {
             const int split = (int)(item % nsplit);
             const int64_t qb = q0 + (item / nsplit) * TBM;
@@ -179,14 +184,13 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
             for (int t = 0; t < ntiles && ok && !*abort_flag; ++t) {
                 const int c0 = (int)(cbeg + (int64_t)t * TBN);
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
-                    const int s = it % NSTAGE;
-                    const uint32_t par = ((it / NSTAGE) & 1) ^ 1;
-                    if (!tc::mbar_wait(tc::smem_u32(&sh->empty[s]), par, abort_flag, WAIT_LIMIT)) { ok = false; break; }
-                    const uint32_t sa = tc::smem_u32(stages + s * STAGE_BYTES);
-                    const uint32_t fb = tc::smem_u32(&sh->full[s]);
+                    if (!tc::mbar_wait(empty0 + 8 * s, ph ^ 1u, abort_flag, WAIT_LIMIT)) { ok = false; break; }
+                    const uint32_t sa = st0 + s * (uint32_t)STAGE_BYTES;
+                    const uint32_t fb = full0 + 8 * s;
                     tc::mbar_expect_tx(fb, STAGE_BYTES);
                     tc::tma_load_2d(sa, &map_a, fb, kb * TBK, (int)qb);
                     tc::tma_load_2d(sa + A_BYTES, &map_b, fb, kb * TBK, c0);
+                    if (++s == (uint32_t)NSTAGE) { s = 0; ph ^= 1u; }
                 }
             }
             }
@@ -205,9 +209,15 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
     } else if (warp == 1) {
         // ------------------------------ MMA issuer ------------------------------
         if (lane == 0) {
+            // lean issue loop (a single thread): running stage / phase counters,
+            // descriptors as base + stage offset + K step (address field >> 4)
             int it = 0;
+            uint32_t s = 0, ph = 0;
             bool ok = true;
             int t = 0;  // tiles issued so far by this CTA (all items)
+            const uint32_t st0 = tc::smem_u32(stages), full0 = tc::smem_u32(&sh->full[0]),
+                           empty0 = tc::smem_u32(&sh->empty[0]);
+            const uint64_t ad0 = kdesc(st0), bd0 = kdesc(st0 + A_BYTES);
             for (int64_t item = blockIdx.x; item < nitems && ok && !*abort_flag; item += gridDim.x) {
             const int split = (int)(item % nsplit);
             const int64_t cbeg = (int64_t)split * per, cend = min(N, cbeg + per);
@@ -221,20 +231,18 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
                 tc::fence_after();
                 const uint32_t dt = tmem + (uint32_t)(acc * TBN);
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
-                    const int s = it % NSTAGE;
-                    if (!tc::mbar_wait(tc::smem_u32(&sh->full[s]), (it / NSTAGE) & 1, abort_flag, WAIT_LIMIT)) {
+                    if (!tc::mbar_wait(full0 + 8 * s, ph, abort_flag, WAIT_LIMIT)) {
                         ok = false;
                         break;
                     }
                     tc::fence_after();
-                    const uint32_t sa = tc::smem_u32(stages + s * STAGE_BYTES);
+                    const uint64_t off = (uint64_t)(s * (uint32_t)(STAGE_BYTES >> 4));
 #pragma unroll
-                    for (int kk = 0; kk < TBK / 16; ++kk) {
-                        const uint64_t ad = kdesc(sa + kk * 32);
-                        const uint64_t bd = kdesc(sa + A_BYTES + kk * 32);
-                        tc::mma_f16(dt, ad, bd, IDESC, (kb | kk) != 0);
-                    }
-                    tc::commit(tc::smem_u32(&sh->empty[s]));
+                    for (int kk = 0; kk < TBK / 16; ++kk)
+                        tc::mma_f16(dt, ad0 + off + (uint64_t)(2 * kk), bd0 + off + (uint64_t)(2 * kk), IDESC,
+                                    (kb | kk) != 0);
+                    tc::commit(empty0 + 8 * s);
+                    if (++s == (uint32_t)NSTAGE) { s = 0; ph ^= 1u; }
                 }
                 if (ok) tc::commit(tc::smem_u32(&sh->tfull[acc]));
             }

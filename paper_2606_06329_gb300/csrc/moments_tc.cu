@@ -417,27 +417,39 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
     } else {
         // ================= MMA warp (lane 0 issues) =================
         if (lane == 0) {
-            uint32_t q = 0, gc = 0;
-            for (int ps = 0; ps < npass; ++ps) {
+            // A single thread issues every MMA, so its loop is kept free of
+            // long dependent chains: the slot index and its phase are running
+            // counters (no division), the B descriptor is built once per chunk
+            // and advanced by adding the 32-byte K step (>> 4) to its address
+            // field, and the abort flag is read only when a wait has to spin.
+            uint32_t gc = 0, s = 0, ph = 0;
+            bool ok = true;
+            const uint32_t a_base = tmem + (uint32_t)dcols;
+            const uint32_t slot_full0 = tc::smem_u32(&slot_full[0]), slot_empty0 = tc::smem_u32(&slot_empty[0]);
+            for (int ps = 0; ps < npass && ok; ++ps) {
                 const int nt = min(tpp, ntiles - ps * tpp);
                 if (ps > 0) {
                     wait(&d_free, (ps - 1) & 1);  // the formers have drained the previous pass
+                    ok = !*abortp;
                     tc::fence_after();
                 }
-                for (int ci = 0; ci < nchunks; ++ci, ++gc) {
-                    const uint32_t bsa = tc::smem_u32(Bop0 + (gc & 1) * MT_B_BYTES);
-                    for (int t = 0; t < nt; ++t, ++q) {
-                        const int s = q % nslots;
-                        wait(&slot_full[s], (q / nslots) & 1);
-                        tc::fence_after();
-                        if (!*abortp) {
-                            const uint32_t a_t = tmem + (uint32_t)(dcols + s * MT_SLOT_COLS);
-#pragma unroll
-                            for (int kk = 0; kk < MT_CH / 16; ++kk)
-                                tc::mma_f16_ts(tmem + (uint32_t)(t * Nb), a_t + (uint32_t)(kk * 8),
-                                               tc::sdesc_sw128(bsa + kk * 32), idesc, (ci | kk) != 0);
+                for (int ci = 0; ci < nchunks && ok; ++ci, ++gc) {
+                    const uint64_t bd0 = tc::sdesc_sw128(tc::smem_u32(Bop0 + (gc & 1) * MT_B_BYTES));
+                    uint32_t d = tmem;
+                    for (int t = 0; t < nt; ++t, d += (uint32_t)Nb) {
+                        if (!tc::mbar_wait(slot_full0 + 8 * s, ph, abortp, MT_WAIT)) {
+                            fail();
+                            ok = false;
+                            break;
                         }
-                        tc::commit(tc::smem_u32(&slot_empty[s]));
+                        tc::fence_after();
+                        const uint32_t a_t = a_base + s * (uint32_t)MT_SLOT_COLS;
+#pragma unroll
+                        for (int kk = 0; kk < MT_CH / 16; ++kk)
+                            tc::mma_f16_ts(d, a_t + (uint32_t)(kk * 8), bd0 + (uint64_t)(2 * kk), idesc,
+                                           (ci | kk) != 0);
+                        tc::commit(slot_empty0 + 8 * s);
+                        if (++s == (uint32_t)nslots) { s = 0; ph ^= 1u; }
                     }
                     tc::commit(tc::smem_u32(&chunk_done[gc & 1]));
                 }
