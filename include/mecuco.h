@@ -244,6 +244,25 @@ MECUCO_API mecuco_status mecuco_curvature_exact(mecuco_t h, const void *X, mecuc
                                                 mecuco_precision prec, int64_t row_begin, int64_t row_end,
                                                 float *kappa_out, float *v_out, float *W_out, void *stream);
 
+/* Fast mode with the truncated SVD replaced by a randomised low-rank
+ * approximation (the paper's future work, Sec. Conclusions), following the
+ * range finder of Halko, Martinsson & Tropp (2011, Alg. 4.3/4.4) on each
+ * patch's Gram G = X_c X_c^T: Y = G Omega, power_iters times Q = orth(Y),
+ * Y = G Q; Q = orth(Y); B = Q^T G Q = V_B diag(sigma_B) V_B^T; U = Q V_B.  The
+ * estimator (Alg. 1 Fast branch) then uses the r = rank largest eigenpairs,
+ * i.e. p = r and a null space of dimension m - r.  Results differ from
+ * mecuco_curvature unless rank = k - 1 and the sketch spans G's range.
+ *   omega        device, k x sketch_cols floats row-major: one Gaussian test
+ *                matrix for every point (drawn by the caller, independent of X)
+ *   rank         1 <= rank <= min(k - 1, m);  rank <= sketch_cols <= k
+ *   power_iters  0..16
+ * Other arguments as for mecuco_curvature; neighbours computed when idx is NULL. */
+MECUCO_API mecuco_status mecuco_curvature_rsvd(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m,
+                                               int64_t ld, int k, const int32_t *idx, int include_self,
+                                               mecuco_variant variant, mecuco_precision prec, int rank,
+                                               int sketch_cols, int power_iters, const float *omega,
+                                               float *kappa_out, void *stream);
+
 /* Theorem 1 (eq. exact_curv) evaluated on caller-supplied eigenpairs of each
  * point's covariance: C = W^T W^{o2} and K = |1/2 sum_s v_s sum_l C_sl^2 + 1/2 sum_s v_s|.
  * With the range eigenvectors fixed and the null-space columns of W drawn from

@@ -66,6 +66,8 @@ SIGNATURES = {
     "mecuco_tangent_basis": (_st, [_p, _p, _i32, _i64, _i64, _i64, _i32, _p, _i64, _i64, _i32, _p, _p]),
     "mecuco_curvature_exact": (_st, [_p, _p, _i32, _i64, _i64, _i64, _i32, _p, _i32, _i32, _i64, _i64, _p, _p, _p,
                                      _p]),
+    "mecuco_curvature_rsvd": (_st, [_p, _p, _i32, _i64, _i64, _i64, _i32, _p, _i32, _i32, _i32, _i32, _i32, _i32, _p,
+                                    _p, _p]),
     "mecuco_exact_kappa": (_st, [_p, _p, _p, _i64, _i64, _p, _p]),
     "mecuco_fidelity": (_st, [_p, _p, _p, _i64, _i32, _p, _p]),
     "mecuco_minmax_normalize": (_st, [_p, _p, _i64, _p, _p]),

@@ -158,6 +158,32 @@ class Context:
         N.check(st, "mecuco_curvature_exact")
         return (kap, v, W) if return_basis else kap
 
+    def mecuco_curvature_rsvd(self, X: torch.Tensor, k: int, rank: int, sketch_cols: int | None = None,
+                              power_iters: int = 2, omega: torch.Tensor | None = None, seed: int = 0,
+                              idx: torch.Tensor | None = None, include_self: bool = False, variant: str = "literal",
+                              precision: str = "fp32") -> torch.Tensor:
+        """Fast-mode curvature with a randomised rank-`rank` SVD of each patch.  omega is the
+        k x sketch_cols Gaussian test matrix (default: rank + min(8, k - rank) columns drawn
+        from numpy's default_rng(seed))."""
+        _check_x(X, self.device)
+        n, m = X.shape
+        if idx is not None and (idx.dtype != torch.int32 or tuple(idx.shape) != (n, k) or not idx.is_contiguous()):
+            raise ValueError("idx must be a contiguous int32 (N, k) tensor")
+        if omega is None:
+            import numpy as np
+            cols = sketch_cols if sketch_cols is not None else rank + min(8, k - rank)
+            omega = torch.from_numpy(np.random.default_rng(seed).standard_normal((k, cols)).astype(np.float32))
+        omega = omega.to(device=X.device, dtype=torch.float32).contiguous()
+        if omega.dim() != 2 or omega.shape[0] != k:
+            raise ValueError("omega must be (k, sketch_cols)")
+        kappa = torch.empty(n, dtype=torch.float32, device=X.device)
+        st = self.lib.mecuco_curvature_rsvd(self.handle, _ptr(X), _dtype_code(X), n, m, X.stride(0), int(k),
+                                            _ptr(idx), int(bool(include_self)), _VAR[variant], _PREC[precision],
+                                            int(rank), int(omega.shape[1]), int(power_iters), _ptr(omega),
+                                            _ptr(kappa), _stream(self.device))
+        N.check(st, "mecuco_curvature_rsvd")
+        return kappa
+
     def mecuco_exact_kappa(self, v: torch.Tensor, W: torch.Tensor) -> torch.Tensor:
         """Theorem 1 on supplied eigenpairs: v (np, m), W (np, m, m), column s = eigenvector s."""
         dev = f"cuda:{self.device}"

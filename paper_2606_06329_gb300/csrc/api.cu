@@ -65,6 +65,11 @@ struct mecuco_ctx {
     int32_t *rowtab[65] = {};    // per k: row codes of the tensor-core moment kernel
     int knn_splits = 0;
     int tc_slots = 4;
+    // randomised low-rank SVD (mecuco_curvature_rsvd), set for the duration of a call
+    struct {
+        int rank = 0, cols = 0, power = 0;
+        const float *omega = nullptr;
+    } rsvd;
     // batched entry point: lanes (streams) and their workspace
     int batch_lanes = 8;
     char *bws = nullptr;
@@ -332,8 +337,9 @@ mecuco_status ensure_items(mecuco_t h, int k) {
 
 struct EstBufs {
     float *G, *R, *Q, *M, *sig, *U, *U0;
+    float *rQ, *rB, *rsig, *rV;  // randomised SVD: range basis, projected Gram and its eigenpairs
 };
-void est_scratch(Carver &c, int64_t chunk, int k, EstBufs *b) {
+void est_scratch(Carver &c, int64_t chunk, int k, EstBufs *b, int rsvd_cols = 0) {
     b->G = c.take<float>((size_t)chunk * k * k);
     b->R = c.take<float>((size_t)chunk * k);
     b->Q = c.take<float>((size_t)chunk * k * k);
@@ -341,6 +347,11 @@ void est_scratch(Carver &c, int64_t chunk, int k, EstBufs *b) {
     b->sig = c.take<float>((size_t)chunk * k);
     b->U = c.take<float>((size_t)chunk * k * k);
     b->U0 = c.take<float>((size_t)chunk * k * k);
+    const int l = rsvd_cols;
+    b->rQ = l ? c.take<float>((size_t)chunk * k * l) : nullptr;
+    b->rB = l ? c.take<float>((size_t)chunk * l * l) : nullptr;
+    b->rsig = l ? c.take<float>((size_t)chunk * l) : nullptr;
+    b->rV = l ? c.take<float>((size_t)chunk * l * l) : nullptr;
 }
 
 int64_t est_chunk(mecuco_t h, int64_t nrows, int k) {
@@ -362,7 +373,7 @@ size_t curvature_bytes(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, in
     size_t need = idx_given ? 0 : knn_bytes(h, X, dt, N, m, ld, nrows, k, prec, idx_bytes);
     Carver c(nullptr, idx_bytes);
     EstBufs b;
-    est_scratch(c, chunk, k, &b);
+    est_scratch(c, chunk, k, &b, h->rsvd.cols);
     return std::max(need, c.off);
 }
 
@@ -388,13 +399,40 @@ mecuco_status run_curvature(mecuco_t h, char *ws, const void *X, mecuco_dtype dt
     }
     Carver c(ws, idx_bytes);
     EstBufs b;
-    est_scratch(c, chunk, k, &b);
+    est_scratch(c, chunk, k, &b, h->rsvd.cols);
     const int fp64 = h->jacobi_fp64 >= 0 ? h->jacobi_fp64 : (prec == MECUCO_PREC_BF16_MIXED ? 1 : 0);
     const float *Qarg = var == MECUCO_FAST_HAAR ? b.Q : nullptr;
     for (int64_t p0 = 0; p0 < nrows; p0 += chunk) {
         const int64_t np = std::min(chunk, nrows - p0);
         const int32_t *nb = nbr + p0 * k;
-        if (tc_moments) {
+        if (h->rsvd.cols) {
+            // randomised low-rank SVD: moments of X_c (unrotated), the range finder
+            // on its Gram, the projected Gram's eigenpairs, U = Q V_B (rank r)
+            float *Ud = U_out ? U_out + p0 * (int64_t)k * k : b.U;
+            const int l = h->rsvd.cols;
+            if (tc_moments) {
+                LAUNCH(h, MECUCO_STAGE_MOMENTS, s,
+                       launch_moments_tc(X, dt, N, m, ld, nb, k, np, h->rowtab[k], b.M, b.G, b.R,
+                                         var == MECUCO_FAST_HAAR ? b.Q : nullptr, h->tc_slots, h->ctr, s));
+            } else {
+                LAUNCH(h, MECUCO_STAGE_GRAM, s,
+                       launch_patch_gram(X, dt, N, m, ld, nb, k, 0, np, nullptr, b.G, b.R,
+                                         var == MECUCO_FAST_HAAR ? b.Q : nullptr, h->ctr, s));
+                LAUNCH(h, MECUCO_STAGE_MOMENTS, s,
+                       launch_patch_m3(X, dt, N, m, ld, nb, k, 0, np, nullptr, b.M, h->m3_items[k], h->ctr, s));
+            }
+            LAUNCH(h, MECUCO_STAGE_JACOBI, s,
+                   launch_rsvd_range(b.G, k, np, h->rsvd.omega, l, h->rsvd.power, b.rQ, b.rB, s));
+            LAUNCH(h, MECUCO_STAGE_JACOBI, s,
+                   launch_jacobi(b.rB, l, np, 1, h->jacobi_max_sweeps, b.rsig, b.rV, h->ctr, s));
+            ++h->launches;
+            LAUNCH(h, MECUCO_STAGE_JACOBI, s,
+                   launch_rsvd_compose(b.rQ, b.rsig, b.rV, k, l, h->rsvd.rank, np, b.sig, Ud, s));
+            LAUNCH(h, MECUCO_STAGE_ESTIMATOR, s,
+                   launch_estimator(b.sig, Ud, b.M, b.R, Qarg, k, m, np, (int)var, rank_eps_gram32(m), kappa_out + p0,
+                                    lambda_out ? lambda_out + p0 * k : nullptr, s_out ? s_out + p0 * k : nullptr,
+                                    h->ctr, s, b.G));
+        } else if (tc_moments) {
             // BF16-mixed: moments of X_c on the tensor cores, eigenpairs of its Gram
             float *Ud = U_out ? U_out + p0 * (int64_t)k * k : b.U;
             LAUNCH(h, MECUCO_STAGE_MOMENTS, s,
@@ -687,6 +725,35 @@ mecuco_status mecuco_curvature(mecuco_t h, const void *X, mecuco_dtype dt, int64
                                float *kappa_out, float *lambda_out, float *U_out, float *s_out, void *stream) {
     return mecuco_curvature_range(h, X, dt, N, m, ld, k, idx, include_self, var, prec, 0, N, kappa_out, lambda_out,
                                   U_out, s_out, stream);
+}
+
+mecuco_status mecuco_curvature_rsvd(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
+                                    int k, const int32_t *idx, int include_self, mecuco_variant var,
+                                    mecuco_precision prec, int rank, int sketch_cols, int power_iters,
+                                    const float *omega, float *kappa_out, void *stream) {
+    mecuco_status st = check_common(h, X, dt, N, m, ld, k, include_self);
+    if (st != MECUCO_OK) return st;
+    if (!kappa_out || !omega) return MECUCO_ERR_INVALID_ARG;
+    if (var != MECUCO_FAST_LITERAL && var != MECUCO_FAST_HAAR) return MECUCO_ERR_INVALID_ARG;
+    if (prec != MECUCO_PREC_FP32 && prec != MECUCO_PREC_BF16_MIXED) return MECUCO_ERR_INVALID_ARG;
+    if (rank < 1 || rank > k - 1 || (int64_t)rank > m || sketch_cols < rank || sketch_cols > k || power_iters < 0 ||
+        power_iters > 16)
+        return MECUCO_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = begin_call(h, s)) != MECUCO_OK) return st;
+    if ((st = ensure_items(h, k)) != MECUCO_OK) return st;
+    if (prec == MECUCO_PREC_BF16_MIXED && (st = ensure_pairs(h, k)) != MECUCO_OK) return st;
+    h->rsvd.rank = rank;
+    h->rsvd.cols = sketch_cols;
+    h->rsvd.power = power_iters;
+    h->rsvd.omega = omega;
+    st = ensure(h->ws, h->ws_bytes, curvature_bytes(h, X, dt, N, m, ld, k, idx != nullptr, N, prec));
+    if (st == MECUCO_OK)
+        st = run_curvature(h, h->ws, X, dt, N, m, ld, k, idx, include_self, var, prec, 0, N, kappa_out, nullptr,
+                           nullptr, nullptr, s);
+    h->rsvd.rank = h->rsvd.cols = h->rsvd.power = 0;
+    h->rsvd.omega = nullptr;
+    return st;
 }
 
 mecuco_status mecuco_curvature_backward(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,

@@ -10,8 +10,11 @@
 //   X_c d_P = R - A 1_p                                   (d_P = 1 - V_r^{o2} 1)
 //   t_A     = |R - A 1_p|^2 / (k-1)
 //   G_tens[j] = W^T M_j W  (p x p),  |G_tens|_F^2 = sum_j |W^T M_j W|_F^2
-//   |X_c V_r|_F^2 = sum_{l<p} s_l^2 = (k-1) tau, so the printed
-//   t_B = tau - 2 tau + |G_tens|^2/(k-1);  t_null = (t_A + 2 t_B)/(m - p)
+//   |X_c V_r|_F^2 = |G W|_F^2, which is sum_{l<p} s_l^2 = (k-1) tau when U_p
+//   holds eigenvectors of G, so the printed
+//   t_B = tau - 2 tau + |G_tens|^2/(k-1);  t_null = (t_A + 2 t_B)/(m - p).
+//   Given G (Ritz pairs of a randomised range finder, whose residuals G u_l -
+//   s_l^2 u_l are not 0) |G W|_F^2 is computed instead.
 //   Haar variant: sum_{j,a} X_c[j,a]^2 (1 - d_P[a]) = sum_l w_l^T Q w_l,
 //   t_B^H = tau - 2 (that)/(k-1) + |G_tens|^2/(k-1), t_null^H = (t_A + 2 t_B^H)/(m - p + 2)
 //   K = |(t_range + t_null)/2 + tau/2|.
@@ -36,8 +39,8 @@ constexpr int EST_SMEM = 3 * 64 * EST_LD * (int)sizeof(float);
 
 __global__ void __launch_bounds__(256)
 estimator_kernel(const float *__restrict__ sigma, const float *__restrict__ U, const float *__restrict__ M,
-                 const float *__restrict__ R, const float *__restrict__ Q, int k, int64_t m, int variant,
-                 float rank_eps, float *__restrict__ kappa, float *__restrict__ lambda_out,
+                 const float *__restrict__ R, const float *__restrict__ Q, const float *__restrict__ Gm, int k,
+                 int64_t m, int variant, float rank_eps, float *__restrict__ kappa, float *__restrict__ lambda_out,
                  float *__restrict__ s_out, DevCounters *ctr) {
     extern __shared__ __align__(16) float esm[];
     float(*Ws)[EST_LD] = reinterpret_cast<float(*)[EST_LD]>(esm);  // W[r][l], zero for l >= p
@@ -147,19 +150,31 @@ estimator_kernel(const float *__restrict__ sigma, const float *__restrict__ U, c
             acc_h += (double)Ws[r][l] * t;
         }
     }
-    // block reduction of (acc_gt2, acc_h) and thread 0's (acc_range, acc_A)
-    double v0 = acc_gt2, v1 = acc_h;
+    // |G W|_F^2 (only with G given)
+    double acc_b2 = 0.0;
+    if (Gm) {
+        const float *gm = Gm + pt * (int64_t)k * k;
+        for (int e = tid; e < k * p; e += 256) {
+            const int r = e / p, l = e % p;
+            float t = 0.f;
+            for (int c = 0; c < k; ++c) t = fmaf(gm[r * k + c], Ws[c][l], t);
+            acc_b2 += (double)t * t;
+        }
+    }
+    // block reduction of (acc_gt2, acc_h, acc_b2) and thread 0's (acc_range, acc_A)
+    double v0 = acc_gt2, v1 = acc_h, v2 = acc_b2;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         v0 += __shfl_xor_sync(0xffffffffu, v0, o);
         v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+        v2 += __shfl_xor_sync(0xffffffffu, v2, o);
     }
-    __shared__ double wred[8][2];
-    if ((tid & 31) == 0) { wred[tid >> 5][0] = v0; wred[tid >> 5][1] = v1; }
+    __shared__ double wred[8][3];
+    if ((tid & 31) == 0) { wred[tid >> 5][0] = v0; wred[tid >> 5][1] = v1; wred[tid >> 5][2] = v2; }
     __syncthreads();
     if (tid == 0) {
-        double gt2 = 0.0, h = 0.0;
-        for (int w = 0; w < 8; ++w) { gt2 += wred[w][0]; h += wred[w][1]; }
+        double gt2 = 0.0, h = 0.0, b2 = 0.0;
+        for (int w = 0; w < 8; ++w) { gt2 += wred[w][0]; h += wred[w][1]; b2 += wred[w][2]; }
         const double km1 = (double)(k - 1);
         double tau = 0.0;
         for (int l = 0; l < p; ++l) tau += (double)sg[l];
@@ -173,7 +188,8 @@ estimator_kernel(const float *__restrict__ sigma, const float *__restrict__ U, c
                 double tB = tau - 2.0 * h / km1 + gt2 / km1;
                 t_null = (t_A + 2.0 * tB) / (double)(q + 2);
             } else {
-                double tB = tau - 2.0 * tau + gt2 / km1;
+                const double t_B2 = Gm ? b2 / km1 : tau;  // |X_c V_r|_F^2 / (k-1)
+                double tB = tau - 2.0 * t_B2 + gt2 / km1;
                 t_null = (t_A + 2.0 * tB) / (double)q;
             }
         }
@@ -189,12 +205,12 @@ estimator_kernel(const float *__restrict__ sigma, const float *__restrict__ U, c
 cudaError_t launch_estimator(const float *sigma, const float *U, const float *M, const float *R,
                              const float *Q, int k, int64_t m, int64_t np, int variant, float rank_eps,
                              float *kappa, float *lambda_out, float *s_out, DevCounters *ctr,
-                             cudaStream_t s) {
+                             cudaStream_t s, const float *G) {
     if (np <= 0) return cudaSuccess;
     if (k > 64) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(estimator_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, EST_SMEM);
     if (e != cudaSuccess) return e;
-    estimator_kernel<<<(unsigned)np, 256, EST_SMEM, s>>>(sigma, U, M, R, Q, k, m, variant, rank_eps, kappa,
+    estimator_kernel<<<(unsigned)np, 256, EST_SMEM, s>>>(sigma, U, M, R, Q, G, k, m, variant, rank_eps, kappa,
                                                          lambda_out, s_out, ctr);
     return cudaGetLastError();
 }

@@ -123,10 +123,12 @@ cudaError_t launch_jacobi(const float *G, int k, int64_t np, int fp64, int max_s
 // sigma/U from launch_jacobi, M pair-major from launch_patch_m3, R and Q from
 // launch_patch_gram (Q only for the Haar variant).  Writes kappa (np) and,
 // when not NULL, lambda_out (np x k) and the singular values s_out (np x k).
+// G (np x k x k, nullable): the patch Grams, given when U holds Ritz vectors
+// rather than eigenvectors of G (|X_c V_r|_F^2 is then computed as |G W|_F^2).
 cudaError_t launch_estimator(const float *sigma, const float *U, const float *M, const float *R,
                              const float *Q, int k, int64_t m, int64_t np, int variant, float rank_eps,
                              float *kappa, float *lambda_out, float *s_out, DevCounters *ctr,
-                             cudaStream_t s);
+                             cudaStream_t s, const float *G = nullptr);
 
 // Numerical-rank thresholds (eigenvalues kept above eps * s_0):
 //  - a Gram accumulated in FP32 (or from BF16 products) carries rounding of
@@ -161,6 +163,17 @@ size_t fidelity_scratch_bytes(int64_t n);
 cudaError_t launch_fidelity(const float *a, const float *b, int64_t n, int normalize, void *scratch, double *out,
                             cudaStream_t s);
 cudaError_t launch_minmax_normalize(const float *x, int64_t n, float *y, void *scratch, cudaStream_t s);
+
+// ---- randomised low-rank SVD --------------------------------------------------
+// Range finder on each patch Gram (np x k x k) with the shared k x l test
+// matrix omega and `power` power iterations: Q (np x k x l, orthonormal
+// columns, collapsed ones 0) and B = Q^T G Q (np x l x l).  Then, from the
+// eigenpairs of B (launch_jacobi, descending), U (np x k x k, first r columns
+// Q V_B, the rest 0) and sigma (np x k, the r largest then 0).
+cudaError_t launch_rsvd_range(const float *G, int k, int64_t np, const float *omega, int l, int power, float *Q,
+                              float *B, cudaStream_t s);
+cudaError_t launch_rsvd_compose(const float *Q, const float *sigB, const float *VB, int k, int l, int r, int64_t np,
+                                float *sigma, float *U, cudaStream_t s);
 
 // ---- tangent bases ------------------------------------------------------------
 // V (np x m x d_out, l fastest) = X_c^T U_p S^-1 for the points of one chunk
