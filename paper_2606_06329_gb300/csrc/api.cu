@@ -64,6 +64,7 @@ struct mecuco_ctx {
     int32_t *m3_items[65] = {};  // per k: work items of the CUDA-core third-moment kernel
     int32_t *rowtab[65] = {};    // per k: row codes of the tensor-core moment kernel
     int knn_splits = 0;
+    int knn_pair = 0;
     int tc_slots = 4;
     // randomised low-rank SVD (mecuco_curvature_rsvd), set for the duration of a call
     struct {
@@ -271,7 +272,7 @@ mecuco_status run_knn(mecuco_t h, char *ws, const void *X, mecuco_dtype dt, int6
         if (p.tc) {
             LAUNCH(h, MECUCO_STAGE_KNN_SEARCH, s,
                    launch_knn_tc(Xb, N, m, p.ldb, b.norms, q0, nq, p.kcl, p.nsplit, include_self, b.cand_d,
-                                 b.cand_i, h->ctr, s));
+                                 b.cand_i, h->knn_pair, h->ctr, s));
         } else {
             LAUNCH(h, MECUCO_STAGE_KNN_SEARCH, s,
                    launch_knn_simt(X, dt, N, m, ld, b.norms, q0, nq, p.kc, p.nsplit, include_self, b.cand_d,
@@ -669,6 +670,10 @@ mecuco_status mecuco_set_option(mecuco_t h, mecuco_option opt, int64_t v) {
         case MECUCO_OPT_TC_SLOTS:
             if (v < 2 || v > 8) return MECUCO_ERR_INVALID_ARG;
             h->tc_slots = (int)v;
+            break;
+        case MECUCO_OPT_KNN_PAIR:
+            if (v < 0 || v > 1) return MECUCO_ERR_INVALID_ARG;
+            h->knn_pair = (int)v;
             break;
         case MECUCO_OPT_BATCH_LANES:
             if (v < 1 || v > 32) return MECUCO_ERR_INVALID_ARG;

@@ -33,9 +33,11 @@ cudaError_t launch_knn_simt(const void *X, mecuco_dtype dt, int64_t N, int64_t m
 // knn_tc_halves() lists of capacity kc per row and split.  Xb is BF16 row-major
 // with ldb % 8 == 0 and a 16-byte aligned base (X itself when it is stored that
 // way, else a copy made by launch_to_bf16).  kc <= 64.
+// pair != 0 (and nq >= 256): CTA pairs sharing 256 x 256 cta_group::2 MMAs;
+// the lists are the same.
 cudaError_t launch_knn_tc(const void *Xb, int64_t N, int64_t m, int64_t ldb, const float *norms,
                           int64_t q0, int64_t nq, int kc, int nsplit, int include_self,
-                          float *cand_d, int32_t *cand_i, DevCounters *ctr, cudaStream_t s);
+                          float *cand_d, int32_t *cand_i, int pair, DevCounters *ctr, cudaStream_t s);
 size_t knn_tc_smem_bytes(int kc);
 // Candidate lists the tensor-core search leaves per row and split (the epilogue's
 // column halves); list h of row r, split s starts at ((r nsplit + s) halves + h) kc.

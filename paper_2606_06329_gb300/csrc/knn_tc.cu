@@ -20,6 +20,17 @@
 //               memory as a max-heap, indices straight to global), so a row leaves with
 //               TC_HALVES lists per candidate split; d~ = |x|^2 + |y|^2 - 2 x.y;
 //               values below a list's admission threshold enter it.
+// CTA pairs (optional, for 256 or more query rows): two CTAs of a
+// thread-block cluster share one 256 x 256 tcgen05.mma (cta_group::2, M = 256)
+// per K step.  Each CTA loads its own 128 query rows and one 128-row half of
+// the candidate tile (16 KB a stage instead of 24 KB, nine stages in the same
+// shared memory); both CTAs' loads complete on the even CTA's stage barrier
+// (cta_group::2 TMA), whose warp 1 issues the MMAs and commits (multicast) to
+// both CTAs' barriers; each CTA drains its own 128 accumulator rows, and the eight
+// epilogue warps of both CTAs release an accumulator at the even CTA.  The
+// lists are those of the single-CTA form.  Measured on GB300 it ties the
+// single-CTA form at 1M x 4096 (8.0 s per search) and is 5% slower at 100k,
+// so single CTAs are the default.
 // Every mbarrier wait is bounded; a timeout sets MECUCO_ERR_TIMEOUT in the
 // device status word, raises a CTA-wide abort flag, drains the copies and MMAs
 // already in flight (also bounded), frees TMEM and returns.
@@ -51,7 +62,6 @@ __device__ __forceinline__ uint64_t kdesc(uint32_t saddr) {
 constexpr int TC_THREADS = 320;  // TMA warp, MMA warp, 8 epilogue warps
 constexpr int TC_HALVES = 2;     // epilogue warps per TMEM lane quarter (column halves)
 constexpr long long WAIT_LIMIT = 1000000000LL;  // ~0.5 s of SM clock per wait
-constexpr uint32_t IDESC = tc::idesc_bf16_f32(TBM, TBN);
 
 struct ListState {
     float thr;  // admission threshold: the largest distance held once the list is full
@@ -104,9 +114,27 @@ __device__ __noinline__ ListState list_insert(ListState st, float d, int c, floa
     return st;
 }
 
+constexpr int MAX_NSTAGE = 9;
+
+// Per-variant layout.  Single CTA: a work item is 128 query rows; each stage
+// holds the 128-row query slice and the 256-row candidate slice (24 KB at
+// K = 32), six stages.  CTA pair (cta_group::2, M = 256): a work item is 256
+// query rows, 128 per CTA; each CTA's stage holds its 128 query rows and its
+// 128 of the tile's 256 candidate rows (16 KB), nine stages in the same
+// shared memory, and one 256 x 256 MMA per K step covers both.
+template <bool PAIR>
+struct KCfg {
+    static constexpr int B_ROWS = PAIR ? TBN / 2 : TBN;
+    static constexpr int STAGE = A_BYTES + B_ROWS * TBK * 2;
+    static constexpr int NST = PAIR ? 9 : 6;
+    static constexpr int QROWS = PAIR ? 2 * TBM : TBM;
+    static constexpr uint32_t IDESC = tc::idesc_bf16_f32(PAIR ? 2 * TBM : TBM, TBN);
+};
+static_assert(KCfg<false>::NST * KCfg<false>::STAGE == KCfg<true>::NST * KCfg<true>::STAGE, "same ring size");
+
 struct TcShared {
-    uint64_t full[NSTAGE];
-    uint64_t empty[NSTAGE];
+    uint64_t full[MAX_NSTAGE];
+    uint64_t empty[MAX_NSTAGE];
     uint64_t tfull[2];
     uint64_t tempty[2];
     uint32_t tmem_base;
@@ -114,55 +142,77 @@ struct TcShared {
 };
 }  // namespace
 
+template <bool PAIR>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, int64_t N,
               int64_t m, const float *__restrict__ norms, int64_t q0, int64_t nq, int kc, int nsplit,
               int include_self, float *__restrict__ cand_d, int32_t *__restrict__ cand_i, DevCounters *ctr) {
-    // Persistent: CTA b takes work items b, b + G, b + 2G, ... (G = gridDim.x),
-    // item = (query block item / nsplit, candidate split item % nsplit).  All
-    // CTAs start their items together and every item has the same number of
-    // tiles, so the CTAs sweep the same candidate tiles in lockstep (each tile
-    // comes from HBM about once per wave) and a wave touches only
-    // G / nsplit query tiles, which stay resident in L2.
+    // Persistent: CTA (pair) b takes work items b, b + G, b + 2G, ... (G CTAs or
+    // pairs), item = (query block item / nsplit, candidate split item % nsplit).
+    // All start their items together and every item has the same number of
+    // tiles, so they sweep the same candidate tiles in lockstep (each tile comes
+    // from HBM about once per wave).
+    using C = KCfg<PAIR>;
+    constexpr int NST = C::NST;
+    constexpr int STAGE = C::STAGE;
     extern __shared__ __align__(1024) uint8_t tsm_raw[];
     // 1024-byte aligned stage ring, then candidate distances [kc][TBM], then barriers
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tsm_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *stages = base;
-    float *Ld0 = reinterpret_cast<float *>(base + NSTAGE * STAGE_BYTES);  // [TC_HALVES][kc][TBM] heaps
+    float *Ld0 = reinterpret_cast<float *>(base + NST * STAGE);  // [TC_HALVES][kc][TBM] heaps
     uint8_t *Ls0 = reinterpret_cast<uint8_t *>(Ld0 + (size_t)TC_HALVES * kc * TBM);  // [TC_HALVES][kc][TBM]
     TcShared *sh = reinterpret_cast<TcShared *>(Ls0 + (size_t)TC_HALVES * kc * TBM);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = PAIR ? tc::cluster_ctarank() : 0u;
     const int64_t qend = q0 + nq;
-    const int64_t nitems = ((nq + TBM - 1) / TBM) * nsplit;
+    const int64_t nitems = ((nq + C::QROWS - 1) / C::QROWS) * nsplit;
+    const int64_t first = PAIR ? blockIdx.x / 2 : blockIdx.x, stride = PAIR ? gridDim.x / 2 : gridDim.x;
     const int64_t per = (N + nsplit - 1) / nsplit;
     const int nkb = (int)((m + TBK - 1) / TBK);
     volatile int *abort_flag = &sh->abort;
     __shared__ int never;  // a flag that stays 0: drain waits are bounded by time only
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NSTAGE; ++s) {
+        for (int s = 0; s < NST; ++s) {
             tc::mbar_init(tc::smem_u32(&sh->full[s]), 1);
             tc::mbar_init(tc::smem_u32(&sh->empty[s]), 1);
         }
         for (int a = 0; a < 2; ++a) {
             tc::mbar_init(tc::smem_u32(&sh->tfull[a]), 1);
-            tc::mbar_init(tc::smem_u32(&sh->tempty[a]), 4 * TC_HALVES * 32);
+            // pair: one arrival per epilogue warp of both CTAs (at the even CTA)
+            tc::mbar_init(tc::smem_u32(&sh->tempty[a]), PAIR ? 2 * 4 * TC_HALVES : 4 * TC_HALVES * 32);
         }
         // circuit breaker: once any CTA of this launch timed out, later CTAs skip
         // the work (their lists come out empty) instead of timing out one by one
-        sh->abort = (*(volatile unsigned *)&ctr->status & DEV_TIMEOUT) ? 1 : 0;
+        // (a pair decides once, below)
+        sh->abort = (!PAIR && (*(volatile unsigned *)&ctr->status & DEV_TIMEOUT)) ? 1 : 0;
         never = 0;
         tc::fence_mbar_init();
         tc::prefetch_tmap(&map_a);
         tc::prefetch_tmap(&map_b);
     }
     if (warp == 1) {
-        tc::tmem_alloc(tc::smem_u32(&sh->tmem_base), 512);
-        tc::tmem_relinquish();
+        if constexpr (PAIR) {
+            tc::tmem_alloc2(tc::smem_u32(&sh->tmem_base), 512);
+        } else {
+            tc::tmem_alloc(tc::smem_u32(&sh->tmem_base), 512);
+            tc::tmem_relinquish();
+        }
     }
     tc::fence_before();
     __syncthreads();
+    if constexpr (PAIR) {
+        __syncwarp();
+        tc::cluster_sync();  // both CTAs' barriers initialised before any remote arrive
+        if (rank == 0 && threadIdx.x == 0) {
+            const uint32_t ab = (*(volatile unsigned *)&ctr->status & DEV_TIMEOUT) ? 1u : 0u;
+            tc::st_cluster_u32(tc::mapa(tc::smem_u32(&sh->abort), 0), ab);
+            tc::st_cluster_u32(tc::mapa(tc::smem_u32(&sh->abort), 1), ab);
+        }
+        __syncwarp();
+        tc::cluster_sync();
+    }
     tc::fence_after();
     const uint32_t tmem = sh->tmem_base;
 
@@ -176,21 +226,30 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
             bool ok = true;
             const uint32_t st0 = tc::smem_u32(stages), full0 = tc::smem_u32(&sh->full[0]),
                            empty0 = tc::smem_u32(&sh->empty[0]);
-            for (int64_t item = blockIdx.x; item < nitems && ok && !*abort_flag; item += gridDim.x) {
+            // pair: both CTAs' loads complete on the even CTA's barrier, which
+            // expects the bytes of both
+            const uint32_t pfull0 = PAIR ? tc::mapa(full0, 0) : 0u;
+            for (int64_t item = first; item < nitems && ok && !*abort_flag; item += stride) {
             const int split = (int)(item % nsplit);
-            const int64_t qb = q0 + (item / nsplit) * TBM;
+            const int64_t qb = q0 + (item / nsplit) * C::QROWS + (int64_t)rank * TBM;
             const int64_t cbeg = (int64_t)split * per, cend = min(N, cbeg + per);
             const int ntiles = cend > cbeg ? (int)((cend - cbeg + TBN - 1) / TBN) : 0;
             for (int t = 0; t < ntiles && ok && !*abort_flag; ++t) {
-                const int c0 = (int)(cbeg + (int64_t)t * TBN);
+                const int c0 = (int)(cbeg + (int64_t)t * TBN) + (int)rank * C::B_ROWS;
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     if (!tc::mbar_wait(empty0 + 8 * s, ph ^ 1u, abort_flag, WAIT_LIMIT)) { ok = false; break; }
-                    const uint32_t sa = st0 + s * (uint32_t)STAGE_BYTES;
-                    const uint32_t fb = full0 + 8 * s;
-                    tc::mbar_expect_tx(fb, STAGE_BYTES);
-                    tc::tma_load_2d(sa, &map_a, fb, kb * TBK, (int)qb);
-                    tc::tma_load_2d(sa + A_BYTES, &map_b, fb, kb * TBK, c0);
-                    if (++s == (uint32_t)NSTAGE) { s = 0; ph ^= 1u; }
+                    const uint32_t sa = st0 + s * (uint32_t)STAGE;
+                    if constexpr (PAIR) {
+                        if (rank == 0) tc::mbar_expect_tx(full0 + 8 * s, 2 * STAGE);
+                        tc::tma_load_2d_pair(sa, &map_a, pfull0 + 8 * s, kb * TBK, (int)qb);
+                        tc::tma_load_2d_pair(sa + A_BYTES, &map_b, pfull0 + 8 * s, kb * TBK, c0);
+                    } else {
+                        const uint32_t fb = full0 + 8 * s;
+                        tc::mbar_expect_tx(fb, STAGE);
+                        tc::tma_load_2d(sa, &map_a, fb, kb * TBK, (int)qb);
+                        tc::tma_load_2d(sa + A_BYTES, &map_b, fb, kb * TBK, c0);
+                    }
+                    if (++s == (uint32_t)NST) { s = 0; ph ^= 1u; }
                 }
             }
             }
@@ -199,14 +258,23 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
                 sh->abort = 1;
             }
             // drain: every issued stage must have landed before the CTA can exit
-            // (bounded by time only: the abort flag must not cut this wait short)
+            // (bounded by time only: the abort flag must not cut this wait short);
+            // a pair waits until the pair MMA has released them (they landed
+            // before it ran), so that no read of this CTA's stages or commit to
+            // its barriers is outstanding
             const int issued = it;
-            for (int j = issued - NSTAGE; j < issued; ++j) {
+            for (int j = issued - NST; j < issued; ++j) {
                 if (j < 0) continue;
-                tc::mbar_wait(tc::smem_u32(&sh->full[j % NSTAGE]), (j / NSTAGE) & 1, &never, WAIT_LIMIT);
+                if (PAIR)
+                    tc::mbar_wait(tc::smem_u32(&sh->empty[j % NST]), (j / NST) & 1, &never, WAIT_LIMIT);
+                else
+                    tc::mbar_wait(tc::smem_u32(&sh->full[j % NST]), (j / NST) & 1, &never, WAIT_LIMIT);
             }
         }
     } else if (warp == 1) {
+        if (PAIR && rank == 1) {
+            // odd CTA of a pair: the even CTA issues the pair MMAs
+        } else {
         // ------------------------------ MMA issuer ------------------------------
         if (lane == 0) {
             // lean issue loop (a single thread): running stage / phase counters,
@@ -218,33 +286,46 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
             const uint32_t st0 = tc::smem_u32(stages), full0 = tc::smem_u32(&sh->full[0]),
                            empty0 = tc::smem_u32(&sh->empty[0]);
             const uint64_t ad0 = kdesc(st0), bd0 = kdesc(st0 + A_BYTES);
-            for (int64_t item = blockIdx.x; item < nitems && ok && !*abort_flag; item += gridDim.x) {
+            for (int64_t item = first; item < nitems && ok && !*abort_flag; item += stride) {
             const int split = (int)(item % nsplit);
             const int64_t cbeg = (int64_t)split * per, cend = min(N, cbeg + per);
             const int ntiles = cend > cbeg ? (int)((cend - cbeg + TBN - 1) / TBN) : 0;
             for (int tt = 0; tt < ntiles && ok && !*abort_flag; ++tt, ++t) {
                 const int acc = t & 1;
-                if (!tc::mbar_wait(tc::smem_u32(&sh->tempty[acc]), ((t >> 1) & 1) ^ 1, abort_flag, WAIT_LIMIT)) {
+                const uint32_t te = tc::smem_u32(&sh->tempty[acc]);
+                const uint32_t tpar = ((t >> 1) & 1) ^ 1;
+                if (!(PAIR ? tc::mbar_wait_cluster(te, tpar, abort_flag, WAIT_LIMIT)
+                           : tc::mbar_wait(te, tpar, abort_flag, WAIT_LIMIT))) {
                     ok = false;
                     break;
                 }
                 tc::fence_after();
                 const uint32_t dt = tmem + (uint32_t)(acc * TBN);
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
-                    if (!tc::mbar_wait(full0 + 8 * s, ph, abort_flag, WAIT_LIMIT)) {
+                    if (!(PAIR ? tc::mbar_wait_cluster(full0 + 8 * s, ph, abort_flag, WAIT_LIMIT)
+                               : tc::mbar_wait(full0 + 8 * s, ph, abort_flag, WAIT_LIMIT))) {
                         ok = false;
                         break;
                     }
                     tc::fence_after();
-                    const uint64_t off = (uint64_t)(s * (uint32_t)(STAGE_BYTES >> 4));
+                    const uint64_t off = (uint64_t)(s * (uint32_t)(STAGE >> 4));
 #pragma unroll
-                    for (int kk = 0; kk < TBK / 16; ++kk)
-                        tc::mma_f16(dt, ad0 + off + (uint64_t)(2 * kk), bd0 + off + (uint64_t)(2 * kk), IDESC,
-                                    (kb | kk) != 0);
-                    tc::commit(empty0 + 8 * s);
-                    if (++s == (uint32_t)NSTAGE) { s = 0; ph ^= 1u; }
+                    for (int kk = 0; kk < TBK / 16; ++kk) {
+                        if constexpr (PAIR)
+                            tc::mma2_f16(dt, ad0 + off + (uint64_t)(2 * kk), bd0 + off + (uint64_t)(2 * kk),
+                                         C::IDESC, (kb | kk) != 0);
+                        else
+                            tc::mma_f16(dt, ad0 + off + (uint64_t)(2 * kk), bd0 + off + (uint64_t)(2 * kk),
+                                        C::IDESC, (kb | kk) != 0);
+                    }
+                    if constexpr (PAIR) tc::commit2_mc(empty0 + 8 * s, (uint16_t)3);
+                    else tc::commit(empty0 + 8 * s);
+                    if (++s == (uint32_t)NST) { s = 0; ph ^= 1u; }
                 }
-                if (ok) tc::commit(tc::smem_u32(&sh->tfull[acc]));
+                if (ok) {
+                    if constexpr (PAIR) tc::commit2_mc(tc::smem_u32(&sh->tfull[acc]), (uint16_t)3);
+                    else tc::commit(tc::smem_u32(&sh->tfull[acc]));
+                }
             }
             }
             if (!ok) {
@@ -254,10 +335,11 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
             // drain: the last commit covers every MMA issued by this thread
             if (it > 0) {
                 const int j = it - 1;
-                tc::mbar_wait(tc::smem_u32(&sh->empty[j % NSTAGE]), (j / NSTAGE) & 1, &never, WAIT_LIMIT);
+                tc::mbar_wait(tc::smem_u32(&sh->empty[j % NST]), (j / NST) & 1, &never, WAIT_LIMIT);
             }
         }
         __syncwarp();
+        }
     } else {
         // ------------------------------ epilogue ---------------------------------
         const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
@@ -265,10 +347,11 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
         const int row = quarter * 32 + lane;
         float *Ld = Ld0 + (size_t)half * kc * TBM;
         uint8_t *Ls = Ls0 + (size_t)half * kc * TBM;
+        const uint32_t tempty_even0 = PAIR ? tc::mapa(tc::smem_u32(&sh->tempty[0]), 0) : 0u;
         int t = 0;  // tiles drained so far by this CTA (all items)
-        for (int64_t item = blockIdx.x; item < nitems && !*abort_flag; item += gridDim.x) {
+        for (int64_t item = first; item < nitems && !*abort_flag; item += stride) {
             const int split = (int)(item % nsplit);
-            const int64_t qb = q0 + (item / nsplit) * TBM;
+            const int64_t qb = q0 + (item / nsplit) * C::QROWS + (int64_t)rank * TBM;
             const int64_t cbeg = (int64_t)split * per, cend = min(N, cbeg + per);
             const int ntiles = cend > cbeg ? (int)((cend - cbeg + TBN - 1) / TBN) : 0;
             const int64_t gq = qb + row;
@@ -306,7 +389,13 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
                     }
                 }
                 tc::fence_before();
-                tc::mbar_arrive(tc::smem_u32(&sh->tempty[acc]));
+                if constexpr (PAIR) {
+                    // one arrival per warp at the even CTA, once every lane has read its rows
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive_cluster(tempty_even0 + 8 * acc);
+                } else {
+                    tc::mbar_arrive(tc::smem_u32(&sh->tempty[acc]));
+                }
             }
             if (valid_row) {
                 for (int p = 0; p < st.cnt; ++p) cand_d[out_base + Ls[p * TBM + row]] = Ld[p * TBM + row];
@@ -319,9 +408,15 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
     }
     tc::fence_before();
     __syncthreads();
+    if constexpr (PAIR) {
+        // no remote arrive, commit or MMA read targets either CTA past here
+        __syncwarp();
+        tc::cluster_sync();
+    }
     if (warp == 1) {
         tc::fence_after();
-        tc::tmem_dealloc(tmem, 512);
+        if constexpr (PAIR) tc::tmem_dealloc2(tmem, 512);
+        else tc::tmem_dealloc(tmem, 512);
     }
 }
 
@@ -362,24 +457,54 @@ size_t knn_tc_smem_bytes(int kc) {
 int knn_tc_halves() { return TC_HALVES; }
 
 cudaError_t launch_knn_tc(const void *Xb, int64_t N, int64_t m, int64_t ldb, const float *norms, int64_t q0,
-                          int64_t nq, int kc, int nsplit, int include_self, float *cand_d, int32_t *cand_i,
+                          int64_t nq, int kc, int nsplit, int include_self, float *cand_d, int32_t *cand_i, int pair,
                           DevCounters *ctr, cudaStream_t s) {
     if (nq <= 0) return cudaSuccess;
     if ((reinterpret_cast<uintptr_t>(Xb) & 15) || (ldb % 8) != 0 || kc > 64) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
     if (!make_map(&ma, Xb, N, m, ldb, TBM) || !make_map(&mb, Xb, N, m, ldb, TBN)) return cudaErrorInvalidValue;
     const size_t smem = knn_tc_smem_bytes(kc);
-    cudaError_t e = cudaFuncSetAttribute(knn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
-    e = cudaGetDevice(&dev);
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
+    if (pair && nq >= 2 * TBM) {
+        // CTA pairs (cta_group::2): 256 query rows per item; each CTA's candidate
+        // half uses the 128-row box of the query map
+        e = cudaFuncSetAttribute(knn_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2);
+        cfg.blockDim = dim3(TC_THREADS);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        e = cudaOccupancyMaxActiveClusters(&nclusters, knn_tc_kernel<true>, &cfg);
+        if (e != cudaSuccess) return e;
+        if (nclusters > 0) {
+            const int64_t items = ((nq + 2 * TBM - 1) / (2 * TBM)) * nsplit;
+            cfg.gridDim = dim3((unsigned)(2 * (items < nclusters ? items : nclusters)));
+            e = cudaLaunchKernelEx(&cfg, knn_tc_kernel<true>, ma, ma, N, m, norms, q0, nq, kc, nsplit, include_self,
+                                   cand_d, cand_i, ctr);
+            if (e != cudaSuccess) return e;
+            return cudaGetLastError();
+        }
+        // no pair fits: single CTAs
+    }
+    e = cudaFuncSetAttribute(knn_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     const int64_t items = ((nq + TBM - 1) / TBM) * nsplit;
     dim3 grid((unsigned)(items < sms ? items : sms));  // persistent: one CTA per SM
-    knn_tc_kernel<<<grid, TC_THREADS, smem, s>>>(ma, mb, N, m, norms, q0, nq, kc, nsplit, include_self, cand_d,
-                                                  cand_i, ctr);
+    knn_tc_kernel<false><<<grid, TC_THREADS, smem, s>>>(ma, mb, N, m, norms, q0, nq, kc, nsplit, include_self,
+                                                         cand_d, cand_i, ctr);
     return cudaGetLastError();
 }
 

@@ -62,6 +62,24 @@ def test_tc_knn_sparse_clusters(ctx, orc):
     _check(ctx, orc, torch.from_numpy(X), X.astype(np.float64), 50, max_uncert=60)
 
 
+@pytest.mark.parametrize("n,m,k", [(1037, 200, 16), (700, 4096, 32), (3000, 256, 64)])
+def test_tc_knn_cta_pairs(ctx, orc, n, m, k):
+    # CTA pairs sharing two-SM (cta_group::2) MMAs: the same lists as one CTA
+    # per SM, and the oracle's neighbours (n not a multiple of the pair's 256 rows)
+    from paper_2606_06329_gb300 import _native as N
+    bits = synth.curved_patches(n=n, m=m, n_patches=3, seed=n + 2 * m)
+    Xd = _bf16(bits).cuda()
+    ctx.set_option(N.OPT_KNN_PAIR, 1)
+    try:
+        pair = _check(ctx, orc, _bf16(bits), synth.bf16_bits_to_f32(bits).astype(np.float64), k)
+        pi, pdist = ctx.mecuco_knn(Xd, k, precision="bf16_mixed", return_dist=True)
+    finally:
+        ctx.set_option(N.OPT_KNN_PAIR, 0)
+    si, sdist = ctx.mecuco_knn(Xd, k, precision="bf16_mixed", return_dist=True)
+    assert np.array_equal(pair, si.cpu().numpy())
+    assert torch.equal(pi, si) and torch.equal(pdist, sdist)
+
+
 def test_tc_knn_matches_plain_path(ctx):
     bits = synth.curved_patches(n=20000, m=512, n_patches=8, seed=3)
     Xd = _bf16(bits).cuda()
