@@ -199,6 +199,19 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def aggregate_timing(elapsed_ms: float, n_per_rank: int, steps: int, dist=None, device="cpu"):
+    """Whole-job timing of replicas: the slowest rank's timed region (max over
+    ranks) and the points all ranks processed per second in it."""
+    import torch
+    t = torch.tensor([float(elapsed_ms)], dtype=torch.float64, device=device)
+    world = 1
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        world = dist.get_world_size()
+    slowest = float(t.item())
+    return slowest, n_per_rank * world * steps / (slowest * 1e-3)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -240,11 +253,9 @@ def run_ours(args):
     barrier()
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    launches = 0
     ev0.record(stream)
     for _ in range(args.steps):
         kap = step()
-        launches += ctx.mecuco_get_stats()["kernel_launches"] if False else 0
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
@@ -253,12 +264,8 @@ def run_ours(args):
     stages = ctx.mecuco_get_stage_times()
     ctx.set_option(NAT.OPT_PROFILE, 0)
     launches = stats["kernel_launches"] * args.steps
-    t = torch.tensor([elapsed_ms], device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed_ms = float(t.item())
+    elapsed_ms, value = aggregate_timing(elapsed_ms, N, args.steps, dist, device="cuda")
     ms_per_step = elapsed_ms / args.steps
-    value = N * world * args.steps / (elapsed_ms * 1e-3)
 
     # roofline of the dominant kernel
     peaks, src = _peaks()
@@ -291,7 +298,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "bf16-gemm/f32/f64-eig" if prec == "bf16_mixed" else "f32",
+            "dtype": "bf16-gemm/f32/f32x2-refine" if prec == "bf16_mixed" else "f32",
             "data": "synthetic",
             "config": {"workload": f"{args.workload}: {w['desc']}", "N": N, "m": m, "k": k, "variant": var,
                        "precision": prec, "l2": "inputs larger than L2 (X is %.1f GB)" % (Xd.numel() * Xd.element_size() / 1e9),
