@@ -187,11 +187,13 @@ def run_reference(args):
             vals.append(res["value"])
             times.append(args.ref_rows / res["value"] * 1e3)
     value = sum(vals) / len(vals)
-    line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": 0, "steps": args.steps,
+    # n_gpus: the N this run was launched with (the pairing with our line of that N);
+    # the oracle itself runs on rank 0's host cores, as config.device says
+    line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": sum(times) / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": f"{args.workload}: {w['desc']}", "N": w["N"], "m": w["m"], "k": w["k"],
-                       "variant": "literal", "precision": "fp64 oracle",
+                       "variant": "literal", "precision": "fp64 oracle", "device": "host cores (rank 0)",
                        "sample_rows_per_step": args.ref_rows},
             "cpu_baseline": {"value": value, "unit": "points/s", "cores": res["cores"], "kind": "oracle",
                              "sample": res["sample"]},
