@@ -1,6 +1,8 @@
 """Adjoint of the Fast-mode curvature (mecuco_curvature_backward and the torch
 autograd wrapper): d(sum_i K_i)/dX with the neighbour lists frozen, against
-FP64 central finite differences of the oracle (target: 1e-3 relative)."""
+FP64 central finite differences of the oracle on sampled coordinates and
+against the oracle's FP64 reverse-mode gradient on every coordinate (target:
+1e-3 relative)."""
 import numpy as np
 import pytest
 
@@ -70,3 +72,34 @@ def test_autograd_function_matches_entry_point(ctx):
     ref = ctx.mecuco_curvature_backward(X.detach(), k, idx, w)
     assert torch.allclose(X.grad, ref, rtol=1e-5, atol=1e-6 * ref.abs().max().item())
     assert torch.allclose(kappa.detach(), ctx.mecuco_curvature(X.detach(), k, idx=idx))
+
+
+@pytest.mark.parametrize("variant", ["literal", "haar"])
+def test_backward_every_coordinate_vs_fp64_adjoint(ctx, orc, variant):
+    # every entry of dX against the FP64 reference gradient (autograd through
+    # Alg. 1's Fast branch, pinned to extrapolated central differences).  Where a
+    # patch has nearly coinciding eigenvalues the gradient itself is ill
+    # conditioned: perturbing X at FP32 rounding level (2^-24 relative) moves
+    # the FP64 reference by up to ~2e-2 there, so each coordinate is held to
+    # max(1e-3, 4 x that spread) (the spread from four perturbed references)
+    from oracle import adjoint as A
+    X = synth.mlp_decoder(n=3000, m=24, latent=4, seed=3)
+    k = 8
+    X64 = X.astype(np.float64)
+    idx, _ = orc.knn(X64, k)
+    dX = ctx.mecuco_curvature_backward(torch.from_numpy(X).cuda(), k, torch.from_numpy(idx).cuda(),
+                                       torch.ones(X.shape[0], device="cuda"), variant=variant)
+    ref = A.grad_adjoint(X64, idx, variant=variant)
+    rng = np.random.default_rng(0)
+    spread = np.zeros_like(ref)
+    for _ in range(4):
+        Xp = X64 * (1.0 + 2.0 ** -24 * rng.standard_normal(X64.shape))
+        spread = np.maximum(spread, np.abs(A.grad_adjoint(Xp, idx, variant=variant) - ref))
+    scale = np.maximum(np.abs(ref), 1e-2 * np.sqrt(np.mean(ref ** 2)))
+    err = np.abs(dX.cpu().numpy().astype(np.float64) - ref) / scale
+    floor = spread / scale
+    print(f"grad {variant}, all {err.size} coordinates: max rel err {err.max():.2e}, "
+          f"99.9% {np.quantile(err, 0.999):.2e}, median {np.median(err):.2e}; above 1e-3: {(err > GRAD_TOL).sum()} "
+          f"(conditioning floor there {floor[err > GRAD_TOL].min() if (err > GRAD_TOL).any() else 0:.1e}..)")
+    assert np.all(err <= np.maximum(GRAD_TOL, 4.0 * floor))
+    assert err[floor < 1e-4].max() < GRAD_TOL
