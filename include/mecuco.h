@@ -103,8 +103,9 @@ typedef enum {
     MECUCO_OPT_BATCH_LANES = 7,      /* concurrent streams of mecuco_curvature_batched (1..32, default 8;
                                         a batch signature tuned by mecuco_autotune_batched uses its own) */
     MECUCO_OPT_TC_SLOTS = 8,         /* TMEM slots for the row-product operand of the tensor-core moment
-                                        kernel (2..8, default 4; more slots leave fewer accumulator tiles
-                                        per pass over the patch) */
+                                        kernel (2, 4, 6 or 8, default 4; slots are handed between warps in
+                                        pairs; more slots leave fewer accumulator tiles per pass over the
+                                        patch) */
     MECUCO_OPT_KNN_PAIR = 9          /* 1: the tensor-core kNN search runs as CTA pairs sharing 256 x 256
                                         two-SM MMAs (tcgen05 cta_group::2); 0 (default): one CTA per SM.
                                         The candidate lists are identical */

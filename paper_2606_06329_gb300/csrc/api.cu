@@ -690,7 +690,7 @@ mecuco_status mecuco_set_option(mecuco_t h, mecuco_option opt, int64_t v) {
             h->knn_splits = (int)v;
             break;
         case MECUCO_OPT_TC_SLOTS:
-            if (v < 2 || v > 8) return MECUCO_ERR_INVALID_ARG;
+            if (v < 2 || v > 8 || (v & 1)) return MECUCO_ERR_INVALID_ARG;
             h->tc_slots = (int)v;
             break;
         case MECUCO_OPT_KNN_PAIR:

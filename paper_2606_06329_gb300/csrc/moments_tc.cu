@@ -28,6 +28,10 @@
 //   1 MMA warp        issues tcgen05.mma with A in TMEM, B in shared memory and
 //                     FP32 accumulators in TMEM, and releases each slot and
 //                     chunk buffer with tcgen05.commit.
+// Formers and the MMA warp hand tiles over in groups of MT_GROUP slots: an
+// mbarrier wait or arrive issued after tcgen05 work costs the issuing thread a
+// few hundred cycles, so each side takes one wait and one arrive per group
+// rather than per tile (the MMA thread then queues 4 MT_GROUP MMAs per wait).
 // TMEM holds the accumulators of up to (512 - 32 slots)/N tiles, so the tiles are covered
 // in passes over the columns (the patch is re-read from L2).  After a pass the
 // formers read the accumulators back (tcgen05.ld) and store each row to its
@@ -50,7 +54,7 @@ constexpr int MT_THREADS = (MT_PRODUCER_WARPS + MT_FORMER_WARPS + 1) * 32;  // +
 constexpr int MT_CH = 64;                              // columns per chunk
 constexpr int MT_MAX_SLOTS = 8;                        // A slots in TMEM (runtime count, 2..8)
 constexpr int MT_SLOT_COLS = MT_CH / 2;                // 32-bit TMEM columns per slot
-constexpr int MT_GROUP = 1;                            // tiles a former writes per store wait
+constexpr int MT_GROUP = 2;                            // tiles per slot hand-over (slots come in groups)
 constexpr int MT_XS_LD = 68;                           // FP32 staging row stride (floats)
 constexpr int MT_XP_LD = 36;                           // packed BF16x2 row stride (words)
 constexpr int MT_ROW_ONES = 64, MT_ROW_W = 65, MT_ROW_ZERO = 66, MT_XP_ROWS = 67;
@@ -328,7 +332,8 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
         // ================= formers: row products into TMEM; drain =================
         const int qd = warp & 3, half = (warp - MT_PRODUCER_WARPS) >> 2;  // TMEM lane quarter, K half
         const int trow = qd * 32 + lane;
-        uint32_t q = 0, gc = 0;
+        const uint32_t ngs = (uint32_t)(nslots / MT_GROUP);  // slot groups
+        uint32_t gs = 0, gph = 0, gq = 0, gc = 0;             // group slot, its phase, groups formed, chunks
         for (int ps = 0; ps < npass; ++ps) {
             const int t0 = ps * tpp, nt = min(tpp, ntiles - t0);
             for (int ci = 0; ci < nchunks; ++ci, ++gc) {
@@ -336,15 +341,12 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
                 if (lane == 0) wait(&chunk_ready[b], (gc >> 1) & 1);
                 __syncwarp();
                 const uint32_t *Xp = Xp0 + b * MT_XP_ROWS * MT_XP_LD;
-                // tiles in groups of MT_GROUP: their stores are issued back to back and
-                // completed with one wait, so the store latency is paid once per group
-                for (int t = 0; t < nt; t += MT_GROUP) {
+                // tiles in groups of MT_GROUP: one wait for the group's slots, the
+                // group's products stored back to back, one store wait and one
+                // arrive (forming the products before the wait was measured slower)
+                for (int t = 0; t < nt; t += MT_GROUP, ++gq) {
                     const int cnt = min(MT_GROUP, nt - t);
-                    for (int u = 0; u < cnt; ++u) {
-                        const uint32_t qq = q + u;
-                        if (qq >= (uint32_t)nslots && lane == 0)
-                            wait(&slot_empty[qq % nslots], ((qq / nslots) - 1) & 1);
-                    }
+                    if (gq >= ngs && lane == 0) wait(&slot_empty[gs], gph ^ 1u);
                     __syncwarp();
                     tc::fence_after();
                     for (int u = 0; u < cnt; ++u) {
@@ -367,15 +369,15 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
                             }
                         }
                         tc::tmem_st_32x32b_x16(tmem + ((uint32_t)(qd * 32) << 16) +
-                                                   (uint32_t)(dcols + ((q + u) % nslots) * MT_SLOT_COLS + half * 16),
+                                                   (uint32_t)(dcols + ((int)gs * MT_GROUP + u) * MT_SLOT_COLS +
+                                                              half * 16),
                                                z);
                     }
                     tc::tmem_st_wait();
                     tc::fence_before();
                     __syncwarp();
-                    if (lane == 0)
-                        for (int u = 0; u < cnt; ++u) tc::mbar_arrive(tc::smem_u32(&slot_full[(q + u) % nslots]));
-                    q += cnt;
+                    if (lane == 0) tc::mbar_arrive(tc::smem_u32(&slot_full[gs]));
+                    if (++gs == ngs) { gs = 0; gph ^= 1u; }
                 }
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(tc::smem_u32(&formers_done[b]));
@@ -418,11 +420,12 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
         // ================= MMA warp (lane 0 issues) =================
         if (lane == 0) {
             // A single thread issues every MMA, so its loop is kept free of
-            // long dependent chains: the slot index and its phase are running
+            // long dependent chains: the slot group and its phase are running
             // counters (no division), the B descriptor is built once per chunk
             // and advanced by adding the 32-byte K step (>> 4) to its address
             // field, and the abort flag is read only when a wait has to spin.
             uint32_t gc = 0, s = 0, ph = 0;
+            const uint32_t ngs = (uint32_t)(nslots / MT_GROUP);
             bool ok = true;
             const uint32_t a_base = tmem + (uint32_t)dcols;
             const uint32_t slot_full0 = tc::smem_u32(&slot_full[0]), slot_empty0 = tc::smem_u32(&slot_empty[0]);
@@ -436,20 +439,30 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
                 for (int ci = 0; ci < nchunks && ok; ++ci, ++gc) {
                     const uint64_t bd0 = tc::sdesc_sw128(tc::smem_u32(Bop0 + (gc & 1) * MT_B_BYTES));
                     uint32_t d = tmem;
-                    for (int t = 0; t < nt; ++t, d += (uint32_t)Nb) {
+                    for (int t = 0; t < nt; t += MT_GROUP, d += (uint32_t)(MT_GROUP * Nb)) {
                         if (!tc::mbar_wait(slot_full0 + 8 * s, ph, abortp, MT_WAIT)) {
                             fail();
                             ok = false;
                             break;
                         }
                         tc::fence_after();
-                        const uint32_t a_t = a_base + s * (uint32_t)MT_SLOT_COLS;
+                        const uint32_t a_g = a_base + s * (uint32_t)(MT_GROUP * MT_SLOT_COLS);
+                        if (t + MT_GROUP <= nt) {
 #pragma unroll
-                        for (int kk = 0; kk < MT_CH / 16; ++kk)
-                            tc::mma_f16_ts(d, a_t + (uint32_t)(kk * 8), bd0 + (uint64_t)(2 * kk), idesc,
-                                           (ci | kk) != 0);
+                            for (int u = 0; u < MT_GROUP; ++u)
+#pragma unroll
+                                for (int kk = 0; kk < MT_CH / 16; ++kk)
+                                    tc::mma_f16_ts(d + (uint32_t)(u * Nb), a_g + (uint32_t)(u * MT_SLOT_COLS + kk * 8),
+                                                   bd0 + (uint64_t)(2 * kk), idesc, (ci | kk) != 0);
+                        } else {  // a pass whose tile count is not a multiple of MT_GROUP
+                            for (int u = 0; u < nt - t; ++u)
+#pragma unroll
+                                for (int kk = 0; kk < MT_CH / 16; ++kk)
+                                    tc::mma_f16_ts(d + (uint32_t)(u * Nb), a_g + (uint32_t)(u * MT_SLOT_COLS + kk * 8),
+                                                   bd0 + (uint64_t)(2 * kk), idesc, (ci | kk) != 0);
+                        }
                         tc::commit(slot_empty0 + 8 * s);
-                        if (++s == (uint32_t)nslots) { s = 0; ph ^= 1u; }
+                        if (++s == ngs) { s = 0; ph ^= 1u; }
                     }
                     tc::commit(tc::smem_u32(&chunk_done[gc & 1]));
                 }
@@ -473,7 +486,8 @@ cudaError_t launch_moments_tc(const void *X, mecuco_dtype dt, int64_t N, int64_t
                               int nslots, DevCounters *ctr, cudaStream_t s) {
     if (np <= 0) return cudaSuccess;
     if (k > 64 || k < 2) return cudaErrorInvalidValue;
-    if (nslots < 2 || nslots > MT_MAX_SLOTS || (512 - nslots * MT_SLOT_COLS) < moments_tc_n(k))
+    if (nslots < MT_GROUP || nslots > MT_MAX_SLOTS || nslots % MT_GROUP != 0 ||
+        (512 - nslots * MT_SLOT_COLS) < moments_tc_n(k))
         return cudaErrorInvalidValue;
     const int nrows = moments_tc_rows(k);
     if (nrows > MT_MAX_ROWS) return cudaErrorInvalidValue;

@@ -110,3 +110,29 @@ def test_tc_curvature_bf16_mixed(ctx, orc, k, variant):
     assert err.max() < BF16_KAPPA_TOL
     lam = out["lambda"].cpu().numpy()[rows]
     assert np.allclose(lam[:, :k - 1], ref_lam[:, :k - 1], rtol=2e-2, atol=1e-3 * ref_lam[:, 0:1])
+
+
+@pytest.mark.parametrize("k,variant", [(64, "haar"), (10, "literal")])
+def test_tc_moment_slots_do_not_change_results(ctx, k, variant):
+    # the row-product operand's TMEM slots (handed between warps in pairs) only
+    # change the schedule: every tile accumulates its K chunks in the same
+    # order, so kappa is bit-identical for 2, 4, 6 and 8 slots; odd counts are
+    # rejected
+    from paper_2606_06329_gb300 import _native as N
+    bits = synth.curved_patches(n=2000, m=1000, n_patches=3, seed=7 + k)
+    Xd = _bf16(bits).cuda()
+    idx = ctx.mecuco_knn(Xd, k, precision="bf16_mixed")
+    outs = []
+    try:
+        for slots in (2, 4, 6, 8):
+            ctx.set_option(N.OPT_TC_SLOTS, slots)
+            outs.append(ctx.mecuco_curvature(Xd, k, idx=idx, precision="bf16_mixed", variant=variant))
+            torch.cuda.synchronize()
+            assert ctx.mecuco_get_last_status() == 0
+        for bad in (1, 3, 7, 10):
+            with pytest.raises(Exception):
+                ctx.set_option(N.OPT_TC_SLOTS, bad)
+    finally:
+        ctx.set_option(N.OPT_TC_SLOTS, 4)
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
