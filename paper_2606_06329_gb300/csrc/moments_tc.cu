@@ -74,6 +74,21 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     return *reinterpret_cast<uint32_t *>(&v);
 }
 
+// 32 bytes (lo, hi) of a lane at dst.  Eight lanes with consecutive 32-byte
+// destinations write the lower halves in one 128-bit store and the upper halves
+// in another; lanes 4..7 of each eight swap the two (swap = true), so that each
+// store covers all 32 banks instead of hitting 16 of them twice.
+__device__ __forceinline__ void store_halves(float *dst, float4 lo, float4 hi, bool swap) {
+    reinterpret_cast<float4 *>(dst)[swap ? 1 : 0] = swap ? hi : lo;
+    reinterpret_cast<float4 *>(dst)[swap ? 0 : 1] = swap ? lo : hi;
+}
+__device__ __forceinline__ void load_halves(const float *src, float4 &lo, float4 &hi, bool swap) {
+    const float4 first = reinterpret_cast<const float4 *>(src)[swap ? 1 : 0];
+    const float4 second = reinterpret_cast<const float4 *>(src)[swap ? 0 : 1];
+    lo = swap ? second : first;
+    hi = swap ? first : second;
+}
+
 // Raw gather of one 8-column unit of one row (zero past m).
 template <typename T>
 struct Unit8;
@@ -91,7 +106,8 @@ struct Unit8<__nv_bfloat16> {
         }
     }
     __device__ __forceinline__ void zero() { v = make_uint4(0, 0, 0, 0); }
-    __device__ __forceinline__ void store(float *dst) const {
+    // swap: write the upper 16 bytes first (see store_halves)
+    __device__ __forceinline__ void store(float *dst, bool swap) const {
         const uint32_t w[4] = {v.x, v.y, v.z, v.w};
         float f[8];
 #pragma unroll
@@ -99,8 +115,7 @@ struct Unit8<__nv_bfloat16> {
             f[2 * e] = __uint_as_float(w[e] << 16);
             f[2 * e + 1] = __uint_as_float(w[e] & 0xffff0000u);
         }
-        reinterpret_cast<float4 *>(dst)[0] = make_float4(f[0], f[1], f[2], f[3]);
-        reinterpret_cast<float4 *>(dst)[1] = make_float4(f[4], f[5], f[6], f[7]);
+        store_halves(dst, make_float4(f[0], f[1], f[2], f[3]), make_float4(f[4], f[5], f[6], f[7]), swap);
     }
 };
 template <>
@@ -118,10 +133,7 @@ struct Unit8<float> {
         }
     }
     __device__ __forceinline__ void zero() { lo = hi = make_float4(0.f, 0.f, 0.f, 0.f); }
-    __device__ __forceinline__ void store(float *dst) const {
-        reinterpret_cast<float4 *>(dst)[0] = lo;
-        reinterpret_cast<float4 *>(dst)[1] = hi;
-    }
+    __device__ __forceinline__ void store(float *dst, bool swap) const { store_halves(dst, lo, hi, swap); }
 };
 }  // namespace
 
@@ -176,7 +188,7 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
     float *Part = Xs + 64 * MT_XS_LD;                                           // [4][64] column partials
     int32_t *codes = reinterpret_cast<int32_t *>(Part + 4 * 64);                // [nrows]
     __shared__ uint64_t slot_full[MT_MAX_SLOTS], slot_empty[MT_MAX_SLOTS];
-    __shared__ uint64_t chunk_ready[2], formers_done[2], chunk_done[2], pass_done, d_free;
+    __shared__ uint64_t chunk_ready[2], chunk_done[2], pass_done, d_free;
     __shared__ uint32_t tmem_slot;
     __shared__ int rows[64];
     __shared__ int abort_flag, never;
@@ -215,7 +227,6 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
         }
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(tc::smem_u32(&chunk_ready[b]), 1);
-            tc::mbar_init(tc::smem_u32(&formers_done[b]), MT_FORMER_WARPS);
             tc::mbar_init(tc::smem_u32(&chunk_done[b]), 1);
         }
         tc::mbar_init(tc::smem_u32(&pass_done), 1);
@@ -261,8 +272,8 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
             for (int ci = 0; ci < nchunks; ++ci, ++gc) {
                 const int b = gc & 1;
                 const uint32_t use = gc >> 1;
-                pre0.store(Xs + gr0 * MT_XS_LD + gg * 8);
-                pre1.store(Xs + (gr0 + 32) * MT_XS_LD + gg * 8);
+                pre0.store(Xs + gr0 * MT_XS_LD + gg * 8, gg >= 4);
+                pre1.store(Xs + (gr0 + 32) * MT_XS_LD + gg * 8, gg >= 4);
                 // next chunk (wrapping into the next pass) is loaded while this one is processed
                 const bool more = ci + 1 < nchunks || ps + 1 < npass;
                 if (more) {
@@ -290,19 +301,19 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
                 }
                 asm volatile("bar.sync 1, 256;" ::: "memory");  // every thread has read Part
                 Part[rg * 64 + cc] = w;
-                // buffer b is free once the formers and the MMAs of its previous chunk are done with it
-                if (ptid == 0 && use >= 1) {
-                    wait(&formers_done[b], (use - 1) & 1);
-                    wait(&chunk_done[b], (use - 1) & 1);
-                }
+                // buffer b is free once the MMAs of its previous chunk are done with it:
+                // they ran after every former warp had formed its tiles of that chunk
+                // (each slot group's MMAs wait for all formers' arrivals), so the
+                // formers are done with it too
+                if (ptid == 0 && use >= 1) wait(&chunk_done[b], (use - 1) & 1);
                 asm volatile("bar.sync 1, 256;" ::: "memory");
                 uint32_t *Xp = Xp0 + b * MT_XP_ROWS * MT_XP_LD;
                 uint8_t *Bop = Bop0 + b * MT_B_BYTES;
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int r = gr0 + 32 * h;
-                    const float4 lo = reinterpret_cast<const float4 *>(Xs + r * MT_XS_LD + gg * 8)[0];
-                    const float4 hi = reinterpret_cast<const float4 *>(Xs + r * MT_XS_LD + gg * 8)[1];
+                    float4 lo, hi;
+                    load_halves(Xs + r * MT_XS_LD + gg * 8, lo, hi, gg >= 4);
                     const uint4 pk = make_uint4(pack_bf16x2(lo.x, lo.y), pack_bf16x2(lo.z, lo.w),
                                                 pack_bf16x2(hi.x, hi.y), pack_bf16x2(hi.z, hi.w));
                     *reinterpret_cast<uint4 *>(Xp + r * MT_XP_LD + gg * 4) = pk;
@@ -341,6 +352,11 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
                 if (lane == 0) wait(&chunk_ready[b], (gc >> 1) & 1);
                 __syncwarp();
                 const uint32_t *Xp = Xp0 + b * MT_XP_ROWS * MT_XP_LD;
+                // x_a of the lane's previous tile: along a row of 8 x 8 pair blocks a
+                // lane keeps its a, so only x_b is reloaded (shared-memory traffic,
+                // not arithmetic, bounds the formers)
+                uint4 xa[4];
+                int ka = -1;
                 // tiles in groups of MT_GROUP: one wait for the group's slots, the
                 // group's products stored back to back, one store wait and one
                 // arrive (forming the products before the wait was measured slower)
@@ -351,13 +367,18 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
                     tc::fence_after();
                     for (int u = 0; u < cnt; ++u) {
                         const int code = codes[(t0 + t + u) * 128 + trow];
-                        const uint4 *pa = reinterpret_cast<const uint4 *>(Xp + (code & 0xff) * MT_XP_LD + half * 16);
+                        if ((code & 0xff) != ka) {
+                            ka = code & 0xff;
+                            const uint4 *pa = reinterpret_cast<const uint4 *>(Xp + ka * MT_XP_LD + half * 16);
+#pragma unroll
+                            for (int e4 = 0; e4 < 4; ++e4) xa[e4] = pa[e4];
+                        }
                         const uint4 *pb =
                             reinterpret_cast<const uint4 *>(Xp + ((code >> 8) & 0xff) * MT_XP_LD + half * 16);
                         uint32_t z[16];
 #pragma unroll
                         for (int e4 = 0; e4 < 4; ++e4) {
-                            const uint4 av = pa[e4], bv = pb[e4];
+                            const uint4 av = xa[e4], bv = pb[e4];
                             const uint32_t aw[4] = {av.x, av.y, av.z, av.w};
                             const uint32_t bw[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
@@ -379,8 +400,6 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
                     if (lane == 0) tc::mbar_arrive(tc::smem_u32(&slot_full[gs]));
                     if (++gs == ngs) { gs = 0; gph ^= 1u; }
                 }
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(tc::smem_u32(&formers_done[b]));
             }
             // ---- drain the pass's accumulators: this warp takes tiles half, half + 2, ...
             if (lane == 0) wait(&pass_done, ps & 1);
