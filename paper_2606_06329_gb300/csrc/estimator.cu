@@ -73,13 +73,28 @@ estimator_kernel(const float *__restrict__ sigma, const float *__restrict__ U, c
     }
     const int bi = tid >> 4, bj = tid & 15;  // 4 x 4 block coordinates
     const float *D = M + pt * m3_pair_floats_d(k);
+    // rows of M_j as 16-byte loads when k % 4 == 0: a warp takes rpw rows at a
+    // time, lane = (row within the warp's rows, float4 within the row); the
+    // split is fixed, so the loop over j does no index division
+    const bool vec = (k & 3) == 0;
+    const int q4 = k >> 2, rpw = vec ? 32 / q4 : 0;
+    const int rr = vec ? (tid & 31) / q4 : 0, c4 = vec ? (tid & 31) - rr * q4 : 0;
     double acc_range = 0.0, acc_gt2 = 0.0, acc_A = 0.0;
     for (int j = 0; j < k; ++j) {
         // M_j[r][t] = D[pair(min(j,r), max(j,r))][t]
-        for (int e = tid; e < k * k; e += 256) {
-            int r = e / k, t = e % k;
-            int a = j < r ? j : r, b = j < r ? r : j;
-            Mj[r][t] = D[(int64_t)pair_index(a, b, k) * k + t];
+        if (vec) {
+            if (rr < rpw)
+                for (int r = (tid >> 5) * rpw + rr; r < k; r += 8 * rpw) {
+                    const int a = j < r ? j : r, b = j < r ? r : j;
+                    *reinterpret_cast<float4 *>(&Mj[r][4 * c4]) =
+                        __ldg(reinterpret_cast<const float4 *>(D + (int64_t)pair_index(a, b, k) * k) + c4);
+                }
+        } else {
+            for (int e = tid; e < k * k; e += 256) {
+                int r = e / k, t = e % k;
+                int a = j < r ? j : r, b = j < r ? r : j;
+                Mj[r][t] = D[(int64_t)pair_index(a, b, k) * k + t];
+            }
         }
         __syncthreads();
         // B = M_j W  (k x p); M_j[4 bi + i][c] = M_j[c][4 bi + i]
