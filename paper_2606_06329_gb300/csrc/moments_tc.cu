@@ -24,10 +24,12 @@
 //   8 former warps    for every tile of the current pass, each thread forms
 //                     32 products of its tile row (HMUL2 on BF16 pairs) and
 //                     writes them with tcgen05.st straight into a TMEM slot
-//                     holding the A operand (2..8 slots of 64 K-columns);
+//                     holding the A operand (2, 4, 6 or 8 slots of 64
+//                     K-columns);
 //   1 MMA warp        issues tcgen05.mma with A in TMEM, B in shared memory and
 //                     FP32 accumulators in TMEM, and releases each slot and
-//                     chunk buffer with tcgen05.commit.
+//                     chunk buffer with tcgen05.commit (a chunk's commit follows
+//                     every former's reads of it, so it alone frees the buffer).
 // Formers and the MMA warp hand tiles over in groups of MT_GROUP slots: an
 // mbarrier wait or arrive issued after tcgen05 work costs the issuing thread a
 // few hundred cycles, so each side takes one wait and one arrive per group
