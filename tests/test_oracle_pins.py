@@ -318,6 +318,46 @@ def test_golden_patches(orc, path):
             g["kappa_fast_haar"], rel=1e-13)
 
 
+# Hand-derived patches with a null space (q > 0) on which t_A, t_B and t_null
+# are all non-zero: they fix the null-space combination of Alg. 1 (eq. tnull,
+# denominator m - p) and its Haar counterpart (denominator q + 2), term by term,
+# including a rank-deficient patch (p = numerical rank < k - 1).
+@pytest.mark.parametrize("path", sorted(glob.glob(os.path.join(GOLDEN, "nullspace_*.txt"))),
+                         ids=os.path.basename)
+def test_golden_null_space_terms(orc, path):
+    g = _read_golden(path)
+    P = g["points"]
+    k, m = int(g["k"]), int(g["m"])
+    assert P.shape == (k, m)
+    Xc = orc.center_patch(P, np.arange(k))
+    # absolute slack for terms that cancel to a small value
+    tol = dict(rel=1e-12, abs=1e-11 * g["tau"])
+    for route in (0, 1):
+        lit = orc.fast_patch(Xc, variant=orc.LITERAL, route=route)
+        haar = orc.fast_patch(Xc, variant=orc.HAAR, route=route)
+        assert lit["p"] == haar["p"] == int(g["p"])
+        for r in (lit, haar):
+            assert r["tau"] == pytest.approx(g["tau"], **tol)
+            assert r["t_range"] == pytest.approx(g["t_range"], **tol)
+            assert r["t_A"] == pytest.approx(g["t_A"], **tol)
+            assert r["t_B2"] == pytest.approx(g["t_B2"], **tol)
+            assert r["gt2"] == pytest.approx(g["gtens_sq"], **tol)
+        assert lit["t_B"] == pytest.approx(g["literal_t_B"], **tol)
+        assert lit["t_null"] == pytest.approx(g["literal_t_null"], **tol)
+        assert lit["kappa"] == pytest.approx(g["kappa_fast_literal"], **tol)
+        assert haar["t_B"] == pytest.approx(g["haar_t_B"], **tol)
+        assert haar["t_null"] == pytest.approx(g["haar_t_null"], **tol)
+        assert haar["kappa"] == pytest.approx(g["kappa_fast_haar"], **tol)
+        # the two variants must differ here, or the fixture pins nothing
+        assert abs(lit["kappa"] - haar["kappa"]) > 0.1 * g["tau"]
+    if "kappa_exact" in g:
+        assert orc.exact_patch(Xc) == pytest.approx(g["kappa_exact"], rel=1e-12)
+    # the same patch as one point's neighbourhood of the dataset-level loop
+    # (every point is its own neighbour's patch when the k points are all of X)
+    ref = orc.curvature(P, k, np.tile(np.arange(k, dtype=np.int32), (k, 1)), variant=orc.LITERAL)
+    assert np.allclose(ref, g["kappa_fast_literal"], rtol=1e-12, atol=1e-11 * g["tau"])
+
+
 # --------------------------------------------------------------------------
 # Reference gradient (P8): central differences are O(h^2)
 # --------------------------------------------------------------------------
