@@ -153,25 +153,58 @@ def _profile_traffic(N: int, nq: int):
     return None
 
 
-def _cpu_baseline(host, kind, k, n_rows, seed=7):
+def _cpu_baseline(host, kind, k, rows):
     """The FP64 oracle (brute-force kNN over all N points + Alg. 1 Fast branch)
-    on a bounded sample of query rows, timed on the host cores."""
+    on a bounded sample of query rows, timed on the host cores.  Returns the
+    cpu_baseline object and the oracle's lists, distances and curvatures of
+    those rows (the accuracy reference)."""
     import numpy as np
     import oracle
     oracle.build()
     N = host.shape[0]
-    rows = np.random.default_rng(seed).choice(N, n_rows, replace=False)
+    rows = np.asarray(rows, dtype=np.int64)
     bf = kind == "bf16"
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
-    idx, _ = oracle.knn(host, k, rows=rows, bf16_bits=bf, nthreads=cores)
+    idx, dist = oracle.knn(host, k, rows=rows, bf16_bits=bf, nthreads=cores)
     full = np.zeros((N, k), dtype=np.int32)
     full[rows] = idx
-    oracle.curvature(host, k, full, rows=rows, bf16_bits=bf, nthreads=cores)
+    kap = oracle.curvature(host, k, full, rows=rows, bf16_bits=bf, nthreads=cores)
     dt = time.perf_counter() - t0
-    return {"value": n_rows / dt, "unit": "points/s", "cores": cores, "kind": "oracle",
-            "sample": f"{n_rows} random query rows of the same workload, each a brute-force FP64 kNN scan "
-                      f"over all {N} points plus the FP64 Fast estimator; {dt:.1f} s"}
+    res = {"value": rows.size / dt, "unit": "points/s", "cores": cores, "kind": "oracle",
+           "sample": f"{rows.size} random query rows of the same workload, each a brute-force FP64 kNN scan "
+                     f"over all {N} points plus the FP64 Fast estimator; {dt:.1f} s"}
+    return res, idx, dist, kap
+
+
+def _row_f64(host, kind, r):
+    import numpy as np
+    x = host[r]
+    if kind == "bf16":
+        return (x.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    return x.astype(np.float64)
+
+
+def _accuracy(host, kind, rows, idx_gpu, kap_gpu, ref_idx, ref_d, ref_kap, tie_rel=1e-6):
+    """Relative curvature error against the FP64 oracle and neighbour-list
+    mismatches the tie rule does not excuse (positions may differ only between
+    distances equal within tie_rel relative), on the sampled rows."""
+    import numpy as np
+    err = np.abs(np.asarray(kap_gpu, np.float64) - ref_kap) / np.abs(ref_kap)
+    bad = 0
+    for i, q in enumerate(rows):
+        g = idx_gpu[i]
+        if np.array_equal(g, ref_idx[i]):
+            continue
+        if len(set(g.tolist())) != g.size or g.min() < 0 or g.max() >= host.shape[0]:
+            bad += 1
+            continue
+        xq = _row_f64(host, kind, q)
+        dg = np.array([((_row_f64(host, kind, j) - xq) ** 2).sum() for j in g])
+        if np.any(np.abs(dg - ref_d[i]) > tie_rel * np.maximum(np.abs(ref_d[i]), 1e-300)):
+            bad += 1
+    return {"kappa_max_rel": float(err.max()), "kappa_median_rel": float(np.median(err)),
+            "knn_mismatch_rows": int(bad), "rows": int(len(rows))}
 
 
 def run_reference(args):
@@ -181,8 +214,10 @@ def run_reference(args):
     w = WORKLOADS[args.workload]
     host, kind = _make_workload(args.workload)
     vals, times = [], []
+    import numpy as np
     for step in range(args.warmup + args.steps):
-        res = _cpu_baseline(host, kind, w["k"], args.ref_rows, seed=100 + step)
+        rows = np.random.default_rng(100 + step).choice(host.shape[0], args.ref_rows, replace=False)
+        res = _cpu_baseline(host, kind, w["k"], rows)[0]
         if step >= args.warmup:
             vals.append(res["value"])
             times.append(args.ref_rows / res["value"] * 1e3)
@@ -214,6 +249,51 @@ def aggregate_timing(elapsed_ms: float, n_per_rank: int, steps: int, dist=None, 
     return slowest, n_per_rank * world * steps / (slowest * 1e-3)
 
 
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA (2 FLOP) x 2.07 GHz
+
+
+def _stage_fracs(stages, steps, N, m, k, prec, rotations, peaks):
+    """Per-stage achieved rate against its binding roof, from one profiled step
+    (CUDA events around every launch).  Algorithmic work per stage:
+      knn_search  2 N^2 m FLOP (tensor, BF16; FP32 lanes in the plain form)
+      knn_rerank  N x 128 candidate rows x m x 2 bytes read (2 lists of 64 per
+                  row from the tensor-core search at k = 64), against HBM
+      moments     k(k+1)(k+2)/6 m multiply-adds per point (the distinct third
+                  moments), x 2 FLOP (tensor, BF16)
+      jacobi      18 k FLOP per plane rotation (two-sided update of A and the
+                  eigenvector update) + 8 k^3 per patch for the refinement's
+                  three products, against the FP32 lanes
+      estimator   k (2 k^2 p + k p (p + 1)) FLOP per point (B = M_j W and the
+                  upper triangle of W^T B), p = k - 1, against the FP32 lanes"""
+    bf = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    hbm = peaks.get("hbm_gbs")
+    p = k - 1
+    work = {
+        "knn_search": (2.0 * N * N * m, "tensor" if prec == "bf16_mixed" else "alu"),
+        "knn_rerank": (N * 128.0 * m * 2.0, "hbm"),
+        "moments": (2.0 * k * (k + 1) * (k + 2) / 6.0 * m * N, "tensor"),
+        "jacobi": (18.0 * k * rotations + 8.0 * k ** 3 * N, "alu"),
+        "estimator": (k * (2.0 * k * k * p + k * p * (p + 1)) * N, "alu"),
+    }
+    out = {}
+    for name, (ms, n) in stages.items():
+        if n == 0:
+            continue
+        ent = {"ms_per_step": ms / steps, "launches_per_step": n / steps}
+        if name in work:
+            w, bound = work[name]
+            sec = ms / steps * 1e-3
+            if bound == "hbm":
+                ach, pk, unit = w / sec / 1e9, hbm, "GB/s"
+            elif bound == "tensor":
+                ach, pk, unit = w / sec / 1e12, bf, "TFLOP/s"
+            else:
+                ach, pk, unit = w / sec / 1e12, FP32_PEAK_TFLOPS, "TFLOP/s"
+            ent.update({"bound": bound, "achieved": ach, "peak": pk, "unit": unit, "frac": ach / pk})
+        out[name] = ent
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -236,6 +316,7 @@ def run_ours(args):
         ctx.set_option(NAT.OPT_JACOBI_FP64, args.jacobi_fp64)
     prec, var = args.precision, args.variant
     stream = torch.cuda.current_stream()
+    knn_stage = NAT.STAGES.index("knn_search")
 
     def barrier():
         if dist is not None:
@@ -249,6 +330,9 @@ def run_ours(args):
         kap = step()
     torch.cuda.synchronize()
     status = ctx.mecuco_get_last_status()
+    # timed region: only the distance-search launches are bracketed by events
+    # (4 launches per step), the rest of the path runs un-instrumented
+    ctx.set_option(NAT.OPT_PROFILE_STAGES, 1 << knn_stage)
     ctx.set_option(NAT.OPT_PROFILE, 1)
     ctx.mecuco_get_stage_times()
     clocks = ClockSampler(local)
@@ -263,40 +347,49 @@ def run_ours(args):
     clk = clocks.stop()
     elapsed_ms = ev0.elapsed_time(ev1)
     stats = ctx.mecuco_get_stats()
-    stages = ctx.mecuco_get_stage_times()
-    ctx.set_option(NAT.OPT_PROFILE, 0)
+    timed = ctx.mecuco_get_stage_times()
     launches = stats["kernel_launches"] * args.steps
     elapsed_ms, value = aggregate_timing(elapsed_ms, N, args.steps, dist, device="cuda")
     ms_per_step = elapsed_ms / args.steps
+    status = status or ctx.mecuco_get_last_status()
 
-    # roofline of the dominant kernel
+    # stage times: one more step with every launch bracketed (outside the timed region)
+    ctx.set_option(NAT.OPT_PROFILE_STAGES, 0)
+    ctx.mecuco_get_stage_times()
+    step()
+    torch.cuda.synchronize()
+    stages = ctx.mecuco_get_stage_times()
+    stats1 = ctx.mecuco_get_stats()
+    ctx.set_option(NAT.OPT_PROFILE, 0)
+
+    # roofline of the dominant kernel, its launches timed inside the timed region
     peaks, src = _peaks()
-    dom = max(stages, key=lambda s: stages[s][0])
     roof = None
-    knn_ms, knn_n = stages["knn_search"]
+    knn_ms, knn_n = timed["knn_search"]
     if knn_n:
+        flops_per_launch = 2.0 * N * N * m / knn_n * args.steps
+        ach = flops_per_launch / (knn_ms / knn_n * 1e-3) / 1e12
+        nq_launch = N / knn_n * args.steps
         if prec == "bf16_mixed":
-            flops_per_launch = 2.0 * N * N * m / knn_n * args.steps
-            ach = flops_per_launch / (knn_ms / knn_n * 1e-3) / 1e12
             pk = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-            nq_launch = N / knn_n * args.steps
             traffic = _profile_traffic(N, nq_launch)
             roof = {"kernel": "knn_tc_kernel (distance GEMM + fused candidate select)", "bound": "tensor",
-                    "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                    "traffic": traffic,
-                    "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a smaller capture, "
-                                      "scaled by query-candidate pairs (profiles/)" if traffic else None,
+                    "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk, "traffic": traffic,
+                    "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, scaled "
+                                      "by query-candidate pairs (profiles/)" if traffic else None,
                     "peak_source": f"{src} bf16_tflops_sustained (kernel timed inside a multi-second step)",
                     "algorithmic": "2*N*N*m FLOP per step (dot products of every query with every point)",
-                    "share_of_step": knn_ms / elapsed_ms}
+                    "launches_timed": knn_n, "share_of_step": knn_ms / elapsed_ms}
         else:
-            flops_per_launch = 2.0 * N * N * m / knn_n * args.steps
-            ach = flops_per_launch / (knn_ms / knn_n * 1e-3) / 1e12
-            roof = {"kernel": "knn_simt_kernel", "bound": "alu", "achieved": ach, "peak": 2 * 128 * 152 * 2.07e9 / 1e12,
-                    "unit": "TFLOP/s", "frac": ach / (2 * 128 * 152 * 2.07e9 / 1e12), "traffic": None,
-                    "peak_source": "FP32 FFMA: 128 lanes x 152 SMs x 2 FLOP x 2.07 GHz",
+            roof = {"kernel": "knn_simt_kernel", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
+                    "peak_source": "derived: FP32 FMA lanes 152 SMs x 128 x 2 FLOP x 2.07 GHz",
                     "share_of_step": knn_ms / elapsed_ms}
 
+    jac = args.jacobi_fp64 if args.jacobi_fp64 is not None else (1 if prec == "bf16_mixed" else 0)
+    jac_desc = {0: "FP32 sweeps", 1: "FP32 sweeps (to 2^-14), then one Ogita-Aishima refinement step with "
+                                     "two-term-FP32 products (~2^-48)",
+                2: "every sweep in FP64"}[jac]
     line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
@@ -304,29 +397,70 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": f"{args.workload}: {w['desc']}", "N": N, "m": m, "k": k, "variant": var,
                        "precision": prec, "l2": "inputs larger than L2 (X is %.1f GB)" % (Xd.numel() * Xd.element_size() / 1e9),
-                       "parallelism": f"replicas x{world}", "jacobi_fp64": args.jacobi_fp64},
+                       "parallelism": f"replicas x{world}", "jacobi": jac_desc,
+                       "timing": "headline with only the distance-search launches event-bracketed; stage "
+                                 "times from one further step with every launch bracketed"},
             "roofline": roof, "gpu_launches": launches, "clocks": clk, "status": status,
-            "stages": {s: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
-                       for s, v in stages.items()},
+            "stages": _stage_fracs(stages, 1, N, m, k, prec, stats1["jacobi_rotations"], peaks),
             "knn_stats": {kk: stats[kk] for kk in ("knn_uncertified", "knn_fallback_rows", "jacobi_max_sweeps",
-                                                  "jacobi_not_converged", "rank_deficient")}}
+                                                  "jacobi_not_converged", "rank_deficient", "jacobi_rotations")}}
 
-    # plain FP32 form on a sample of query rows (all N points remain candidates)
+    S = min(args.plain_rows, N)
+    rows = np.sort(np.random.default_rng(7).choice(S, min(args.cpu_rows, S), replace=False))
+    kap_chosen = kap.cpu().numpy()
+    if rank == 0 and prec != "fp32":
+        idx_chosen = ctx.mecuco_knn_range(Xd, k, 0, S, precision=prec).cpu().numpy()
+    # plain FP32 form on query rows [0, S) (all N points remain candidates)
+    plain = None
     if rank == 0 and not args.no_plain and prec != "fp32":
-        S = min(args.plain_rows, N)
-        ctx.mecuco_knn_range(Xd, k, 0, S, precision="fp32")
+        ctx.mecuco_knn_range(Xd, k, 0, min(S, 256), precision="fp32")
         torch.cuda.synchronize()
+        ctx.set_option(NAT.OPT_PROFILE, 1)
+        ctx.mecuco_get_stage_times()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        idx = ctx.mecuco_knn_range(Xd, k, 0, S, precision="fp32")
-        ctx.mecuco_curvature_range(Xd, k, 0, S, idx=idx, precision="fp32", variant=var)
+        idx_p = ctx.mecuco_knn_range(Xd, k, 0, S, precision="fp32")
+        kap_p = ctx.mecuco_curvature_range(Xd, k, 0, S, idx=idx_p, precision="fp32", variant=var)
         e1.record(stream)
         torch.cuda.synchronize()
+        pst = ctx.mecuco_get_stage_times()
+        ctx.set_option(NAT.OPT_PROFILE, 0)
         pms = e0.elapsed_time(e1)
+        pk_ms, pk_n = pst["knn_search"]
+        p_ach = 2.0 * S * N * m / (pk_ms * 1e-3) / 1e12 if pk_n else None
+        plain = {"idx": idx_p.cpu().numpy(), "kappa": kap_p.cpu().numpy()}
         line["plain_fp32"] = {"value": S / (pms * 1e-3), "unit": "points/s",
                               "sample": f"query rows [0,{S}) of the same workload against all {N} points, "
-                                        f"kNN + estimator in plain FP32; {pms:.0f} ms",
-                              "chosen_over_plain": value / world / (S / (pms * 1e-3))}
+                                        f"kNN + estimator in plain FP32 (FP32 search, FP64 centring, rotated "
+                                        f"patch, FP32 Jacobi + two-term-FP32 refinement); {pms:.0f} ms",
+                              "chosen_over_plain": value / world / (S / (pms * 1e-3)),
+                              "knn_simt_roofline": {"bound": "alu", "achieved": p_ach, "peak": FP32_PEAK_TFLOPS,
+                                                    "unit": "TFLOP/s",
+                                                    "frac": p_ach / FP32_PEAK_TFLOPS if p_ach else None}}
+
+    # FP64-sweep Jacobi arm on a row range: its stage time and how far K moves
+    if rank == 0 and prec == "bf16_mixed" and args.fp64_rows > 0:
+        R = min(args.fp64_rows, N)
+        idx_r = ctx.mecuco_knn_range(Xd, k, 0, R, precision=prec)
+        arm = {}
+        for mode in (1, 2):
+            ctx.set_option(NAT.OPT_JACOBI_FP64, mode)
+            ctx.mecuco_curvature_range(Xd, k, 0, R, idx=idx_r, precision=prec, variant=var)
+            torch.cuda.synchronize()
+            ctx.set_option(NAT.OPT_PROFILE, 1)
+            ctx.mecuco_get_stage_times()
+            kr = ctx.mecuco_curvature_range(Xd, k, 0, R, idx=idx_r, precision=prec, variant=var)
+            torch.cuda.synchronize()
+            jt = ctx.mecuco_get_stage_times()["jacobi"][0]
+            ctx.set_option(NAT.OPT_PROFILE, 0)
+            arm[mode] = (kr.cpu().numpy().astype(np.float64), jt)
+        ctx.set_option(NAT.OPT_JACOBI_FP64, -1 if args.jacobi_fp64 is None else args.jacobi_fp64)
+        dev = np.abs(arm[2][0] - arm[1][0]) / np.abs(arm[2][0])
+        line["jacobi_fp64_arm"] = {
+            "rows": f"query rows [0,{R}) of the same workload (BF16-mixed moments, same neighbour lists)",
+            "default_jacobi_ms": arm[1][1], "fp64_sweeps_jacobi_ms": arm[2][1],
+            "kappa_max_rel_dev": float(dev.max()), "kappa_median_rel_dev": float(np.median(dev)),
+            "fp64_kappa_rows": arm[2][0]}
 
     # end to end through the host-buffer C entry point (copies inside the timed region)
     if rank == 0 and not args.no_e2e:
@@ -336,12 +470,36 @@ def run_ours(args):
         for _ in range(args.e2e_steps):
             ctx.mecuco_curvature_host(Xh_pinned, k, precision=prec, variant=var, kappa_out=kap_h)
         dt = time.perf_counter() - t0
+        # the bare host-to-device copy of X for comparison (CUDA events)
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        Xd.copy_(Xh_pinned, non_blocking=True)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        nbytes = int(Xh_pinned.numel() * Xh_pinned.element_size())
         line["e2e"] = {"value": N * args.e2e_steps / dt, "unit": "points/s",
-                       "h2d_bytes_per_step": int(Xh_pinned.numel() * Xh_pinned.element_size()),
-                       "d2h_bytes_per_step": int(N * 4), "steps": args.e2e_steps}
+                       "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": int(N * 4), "steps": args.e2e_steps,
+                       "ms_per_step": dt / args.e2e_steps * 1e3,
+                       "bare_h2d_ms": h0.elapsed_time(h1), "bare_h2d_gbs": nbytes / (h0.elapsed_time(h1) * 1e-3) / 1e9}
 
     if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = _cpu_baseline(host, kind, k, args.cpu_rows)
+        cpu, ref_idx, ref_d, ref_kap = _cpu_baseline(host, kind, k, rows)
+        line["cpu_baseline"] = cpu
+        acc = {"reference": "FP64 oracle: brute-force kNN over all N points, Alg. 1 Fast branch on its lists",
+               "tie_rule": "list positions may differ only between distances equal within 1e-6 relative"}
+        if prec != "fp32":
+            acc["chosen"] = _accuracy(host, kind, rows, idx_chosen[rows], kap_chosen[rows], ref_idx, ref_d, ref_kap)
+        if plain is not None:
+            acc["plain_fp32"] = _accuracy(host, kind, rows, plain["idx"][rows], plain["kappa"][rows], ref_idx,
+                                          ref_d, ref_kap)
+        if "jacobi_fp64_arm" in line:
+            kr = line["jacobi_fp64_arm"]["fp64_kappa_rows"][rows]
+            e = np.abs(kr - ref_kap) / np.abs(ref_kap)
+            acc["chosen_fp64_sweeps"] = {"kappa_max_rel": float(e.max()), "kappa_median_rel": float(np.median(e)),
+                                         "rows": int(len(rows))}
+        line["accuracy"] = acc
+    if "jacobi_fp64_arm" in line:
+        del line["jacobi_fp64_arm"]["fp64_kappa_rows"]
 
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -360,11 +518,12 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="curved_patches_1m")
     ap.add_argument("--precision", choices=["bf16_mixed", "fp32"], default="bf16_mixed")
     ap.add_argument("--variant", choices=["literal", "haar"], default="literal")
-    ap.add_argument("--jacobi-fp64", type=int, choices=[0, 1], default=None)
+    ap.add_argument("--jacobi-fp64", type=int, choices=[0, 1, 2], default=None)
     ap.add_argument("--plain-rows", type=int, default=4096)
     ap.add_argument("--cpu-rows", type=int, default=32)
     ap.add_argument("--ref-rows", type=int, default=16)
-    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--fp64-rows", type=int, default=16384)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

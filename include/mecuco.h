@@ -106,9 +106,21 @@ typedef enum {
                                         kernel (2, 4, 6 or 8, default 4; slots are handed between warps in
                                         pairs; more slots leave fewer accumulator tiles per pass over the
                                         patch) */
-    MECUCO_OPT_KNN_PAIR = 9          /* 1: the tensor-core kNN search runs as CTA pairs sharing 256 x 256
+    MECUCO_OPT_KNN_PAIR = 9,         /* 1: the tensor-core kNN search runs as CTA pairs sharing 256 x 256
                                         two-SM MMAs (tcgen05 cta_group::2); 0 (default): one CTA per SM.
                                         The candidate lists are identical */
+    MECUCO_OPT_WAIT_LIMIT = 10,      /* SM clock cycles after which a bounded wait in the work loops of the
+                                        tensor-core kernels (kNN search on single CTAs, patch moments) gives
+                                        up: the launch sets MECUCO_ERR_TIMEOUT in the status word, waits for
+                                        the copies and MMAs it has in flight (always with the default limit),
+                                        frees its tensor memory and returns; its outputs are then invalid.
+                                        0 (default): 1e9 cycles (~0.5 s at 2 GHz) */
+    MECUCO_OPT_WORKSPACE_LIMIT = 11, /* cap in bytes on each device buffer the context grows (workspace,
+                                        host-call copies, batched-call lanes); a call that needs more returns
+                                        MECUCO_ERR_OOM before allocating, leaving the context usable.
+                                        0 (default): no cap */
+    MECUCO_OPT_PROFILE_STAGES = 12   /* bit mask of the mecuco_stage values that MECUCO_OPT_PROFILE brackets
+                                        with events (1 << stage); 0 (default): every stage */
 } mecuco_option;
 
 /* Kernel stages, for mecuco_get_stage_times. */
@@ -137,6 +149,7 @@ typedef struct {
     int64_t jacobi_not_converged;/* patches that hit the sweep cap */
     int64_t rank_deficient;      /* patches with numerical rank < min(k-1, m) */
     int64_t kernel_launches;     /* kernels launched by the call */
+    int64_t jacobi_rotations;    /* plane rotations applied by the Jacobi sweeps (all patches) */
 } mecuco_stats;
 
 /* Create a context on CUDA device `device`.  It owns a device workspace that
@@ -344,9 +357,11 @@ MECUCO_API mecuco_status mecuco_curvature_host(mecuco_t h, const void *X_host, m
  * the process exits.  Runs on the calling thread's current device; X, idx_out
  * and dist_out as for mecuco_knn with MECUCO_PREC_FP32, and the lists are the
  * same as that call returns.  N above 4,194,304 rows is rejected with
- * MECUCO_ERR_INVALID_ARG.  The first call on a device looks up the scratch
- * array's device address (it may load the module); make that call before any
- * stream capture.  All calls share the scratch and it keeps the last call's
+ * MECUCO_ERR_INVALID_ARG (mecuco_last_error_message says why).  The first call
+ * on a device looks up the scratch array's device address (it may load the
+ * module); make that call before any stream capture.  The address is cached per
+ * device and CUDA context, so a call after cudaDeviceReset looks it up again in
+ * the new context.  All calls share the scratch and it keeps the last call's
  * contents; calls whose GPU work overlaps (other streams, other host threads
  * on the same device) race on it and must be serialised by the caller.
  * Device-side counters of this entry point are not reported. */

@@ -17,7 +17,8 @@ F32, BF16 = 0, 1
 FAST_LITERAL, FAST_HAAR = 0, 1
 PREC_FP32, PREC_BF16_MIXED = 0, 1
 (OPT_KNN_MARGIN, OPT_JACOBI_FP64, OPT_JACOBI_MAX_SWEEPS, OPT_CHUNK_POINTS, OPT_KNN_QUERY_CHUNK, OPT_PROFILE,
- OPT_KNN_SPLITS, OPT_BATCH_LANES, OPT_TC_SLOTS, OPT_KNN_PAIR) = range(10)
+ OPT_KNN_SPLITS, OPT_BATCH_LANES, OPT_TC_SLOTS, OPT_KNN_PAIR, OPT_WAIT_LIMIT, OPT_WORKSPACE_LIMIT,
+ OPT_PROFILE_STAGES) = range(13)
 STAGES = ("rownorm", "knn_search", "knn_rerank", "knn_fallback", "gram", "moments", "jacobi", "estimator", "adjoint",
           "basis", "exact", "fidelity")
 
@@ -40,7 +41,7 @@ class MecucoError(RuntimeError):
 class mecuco_stats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in (
         "knn_rows", "knn_uncertified", "knn_fallback_rows", "jacobi_max_sweeps",
-        "jacobi_not_converged", "rank_deficient", "kernel_launches")]
+        "jacobi_not_converged", "rank_deficient", "kernel_launches", "jacobi_rotations")]
 
 
 class mecuco_dataset(C.Structure):

@@ -87,6 +87,9 @@ struct mecuco_ctx {
     int64_t chunk_points = 0;
     int64_t knn_qchunk = 0;
     int profile = 0;
+    int64_t profile_mask = -1;  // stages bracketed while profiling (bit = mecuco_stage)
+    long long wait_limit = 0;   // clock cycles of the tensor-core kernels' work waits (0: default)
+    size_t ws_cap = 0;          // cap on the bytes of one device allocation of the context (0: none)
     // per-call bookkeeping
     int64_t launches = 0;
     int64_t knn_rows = 0;
@@ -120,7 +123,7 @@ mecuco_status flush_events(mecuco_t h) {
 
 mecuco_status prof_begin(mecuco_t h, int stage, cudaStream_t s, EventPair **out) {
     *out = nullptr;
-    if (!h->profile) return MECUCO_OK;
+    if (!h->profile || !((h->profile_mask >> stage) & 1)) return MECUCO_OK;
     if (h->events_used >= 4096) {
         mecuco_status st = flush_events(h);
         if (st != MECUCO_OK) return st;
@@ -150,8 +153,18 @@ mecuco_status prof_begin(mecuco_t h, int stage, cudaStream_t s, EventPair **out)
         ++(h)->launches;                                                         \
     } while (0)
 
-mecuco_status ensure(char *&buf, size_t &cur, size_t need) {
+// Grow a context-owned device buffer to `need` bytes.  A request above the
+// context's allocation cap (MECUCO_OPT_WORKSPACE_LIMIT) fails with
+// MECUCO_ERR_OOM before any allocation, as a failed cudaMalloc would.
+mecuco_status ensure(char *&buf, size_t &cur, size_t need, size_t cap = 0) {
     if (need <= cur) return MECUCO_OK;
+    if (cap && need > cap) {
+        char msg[160];
+        snprintf(msg, sizeof(msg), "workspace of %zu bytes exceeds the context's allocation limit of %zu bytes", need,
+                 cap);
+        set_error_text(msg);
+        return MECUCO_ERR_OOM;
+    }
     if (buf) {
         // earlier asynchronous work may still use the old buffer
         cudaError_t e = cudaDeviceSynchronize();
@@ -273,7 +286,7 @@ mecuco_status run_knn(mecuco_t h, char *ws, const void *X, mecuco_dtype dt, int6
         if (p.tc) {
             LAUNCH(h, MECUCO_STAGE_KNN_SEARCH, s,
                    launch_knn_tc(Xb, N, m, p.ldb, b.norms, q0, nq, p.kcl, p.nsplit, include_self, b.cand_d,
-                                 b.cand_i, h->knn_pair, h->ctr, s));
+                                 b.cand_i, h->knn_pair, h->wait_limit, h->ctr, s));
         } else {
             LAUNCH(h, MECUCO_STAGE_KNN_SEARCH, s,
                    launch_knn_simt(X, dt, N, m, ld, b.norms, q0, nq, p.kc, p.nsplit, include_self, b.cand_d,
@@ -419,7 +432,8 @@ mecuco_status run_curvature(mecuco_t h, char *ws, const void *X, mecuco_dtype dt
             if (tc_moments) {
                 LAUNCH(h, MECUCO_STAGE_MOMENTS, s,
                        launch_moments_tc(X, dt, N, m, ld, nb, k, np, h->rowtab[k], b.M, b.G, b.R,
-                                         var == MECUCO_FAST_HAAR ? b.Q : nullptr, h->tc_slots, h->ctr, s));
+                                         var == MECUCO_FAST_HAAR ? b.Q : nullptr, h->tc_slots, h->wait_limit,
+                                         h->ctr, s));
             } else {
                 LAUNCH(h, MECUCO_STAGE_GRAM, s,
                        launch_patch_gram(X, dt, N, m, ld, nb, k, 0, np, nullptr, b.G, b.R,
@@ -443,7 +457,8 @@ mecuco_status run_curvature(mecuco_t h, char *ws, const void *X, mecuco_dtype dt
             float *Ud = U_out ? U_out + p0 * (int64_t)k * k : b.U;
             LAUNCH(h, MECUCO_STAGE_MOMENTS, s,
                    launch_moments_tc(X, dt, N, m, ld, nb, k, np, h->rowtab[k], b.M, b.G, b.R,
-                                     var == MECUCO_FAST_HAAR ? b.Q : nullptr, h->tc_slots, h->ctr, s));
+                                     var == MECUCO_FAST_HAAR ? b.Q : nullptr, h->tc_slots, h->wait_limit, h->ctr,
+                                     s));
             LAUNCH(h, MECUCO_STAGE_JACOBI, s,
                    launch_jacobi(b.G, k, np, fp64, h->jacobi_max_sweeps, b.sig, Ud, h->ctr, s, kJacobiPreLoose));
             if (fp64 == 1 || fp64 == 3) ++h->launches;  // the refinement is a second kernel
@@ -543,7 +558,7 @@ mecuco_status run_batched_lanes(mecuco_t h, const mecuco_dataset *sets, int nset
     std::vector<size_t> lane_off(lanes, 0);
     size_t total = 0;
     for (int l = 0; l < lanes; ++l) { lane_off[l] = total; total += lane_bytes[l]; }
-    if ((st = ensure(h->bws, h->bws_bytes, total)) != MECUCO_OK) return st;
+    if ((st = ensure(h->bws, h->bws_bytes, total, h->ws_cap)) != MECUCO_OK) return st;
     for (int l = 0; l < lanes; ++l) {
         if (!h->lane_stream[l]) CK(cudaStreamCreateWithFlags(&h->lane_stream[l], cudaStreamNonBlocking));
         if (!h->lane_event[l]) CK(cudaEventCreateWithFlags(&h->lane_event[l], cudaEventDisableTiming));
@@ -697,6 +712,18 @@ mecuco_status mecuco_set_option(mecuco_t h, mecuco_option opt, int64_t v) {
             if (v < 0 || v > 1) return MECUCO_ERR_INVALID_ARG;
             h->knn_pair = (int)v;
             break;
+        case MECUCO_OPT_PROFILE_STAGES:
+            if (v < 0 || v >= ((int64_t)1 << MECUCO_STAGE_COUNT)) return MECUCO_ERR_INVALID_ARG;
+            h->profile_mask = v == 0 ? -1 : v;
+            break;
+        case MECUCO_OPT_WAIT_LIMIT:
+            if (v < 0) return MECUCO_ERR_INVALID_ARG;
+            h->wait_limit = (long long)v;
+            break;
+        case MECUCO_OPT_WORKSPACE_LIMIT:
+            if (v < 0) return MECUCO_ERR_INVALID_ARG;
+            h->ws_cap = (size_t)v;
+            break;
         case MECUCO_OPT_BATCH_LANES:
             if (v < 1 || v > 32) return MECUCO_ERR_INVALID_ARG;
             h->batch_lanes = (int)v;
@@ -716,7 +743,8 @@ mecuco_status mecuco_knn_range(mecuco_t h, const void *X, mecuco_dtype dt, int64
     if (prec != MECUCO_PREC_FP32 && prec != MECUCO_PREC_BF16_MIXED) return MECUCO_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = begin_call(h, s)) != MECUCO_OK) return st;
-    if ((st = ensure(h->ws, h->ws_bytes, knn_bytes(h, X, dt, N, m, ld, re - rb, k, prec, 0))) != MECUCO_OK)
+    if ((st = ensure(h->ws, h->ws_bytes, knn_bytes(h, X, dt, N, m, ld, re - rb, k, prec, 0), h->ws_cap)) !=
+        MECUCO_OK)
         return st;
     return run_knn(h, h->ws, X, dt, N, m, ld, k, include_self, prec, rb, re, idx_out, dist_out, s, 0);
 }
@@ -740,8 +768,8 @@ mecuco_status mecuco_curvature_range(mecuco_t h, const void *X, mecuco_dtype dt,
     if ((st = begin_call(h, s)) != MECUCO_OK) return st;
     if ((st = ensure_items(h, k)) != MECUCO_OK) return st;
     if (prec == MECUCO_PREC_BF16_MIXED && (st = ensure_pairs(h, k)) != MECUCO_OK) return st;
-    if ((st = ensure(h->ws, h->ws_bytes, curvature_bytes(h, X, dt, N, m, ld, k, idx != nullptr, re - rb, prec))) !=
-        MECUCO_OK)
+    if ((st = ensure(h->ws, h->ws_bytes, curvature_bytes(h, X, dt, N, m, ld, k, idx != nullptr, re - rb, prec),
+                     h->ws_cap)) != MECUCO_OK)
         return st;
     return run_curvature(h, h->ws, X, dt, N, m, ld, k, idx, include_self, var, prec, rb, re, kappa_out, lambda_out,
                          U_out, s_out, s);
@@ -774,7 +802,7 @@ mecuco_status mecuco_curvature_rsvd(mecuco_t h, const void *X, mecuco_dtype dt, 
     h->rsvd.cols = sketch_cols;
     h->rsvd.power = power_iters;
     h->rsvd.omega = omega;
-    st = ensure(h->ws, h->ws_bytes, curvature_bytes(h, X, dt, N, m, ld, k, idx != nullptr, N, prec));
+    st = ensure(h->ws, h->ws_bytes, curvature_bytes(h, X, dt, N, m, ld, k, idx != nullptr, N, prec), h->ws_cap);
     if (st == MECUCO_OK)
         st = run_curvature(h, h->ws, X, dt, N, m, ld, k, idx, include_self, var, prec, 0, N, kappa_out, nullptr,
                            nullptr, nullptr, s);
@@ -807,7 +835,7 @@ mecuco_status mecuco_curvature_backward(mecuco_t h, const void *X, mecuco_dtype 
     t.take<float>((size_t)chunk * k * k);
     t.take<float>((size_t)chunk * k * k * k);
     t.take<float>((size_t)chunk * k * k * k);
-    if ((st = ensure(h->ws, h->ws_bytes, t.off)) != MECUCO_OK) return st;
+    if ((st = ensure(h->ws, h->ws_bytes, t.off, h->ws_cap)) != MECUCO_OK) return st;
     Carver c(h->ws);
     est_scratch(c, chunk, k, &b);
     float *U0 = b.U0;
@@ -859,7 +887,7 @@ mecuco_status mecuco_tangent_basis(mecuco_t h, const void *X, mecuco_dtype dt, i
     t.take<float>((size_t)chunk * k);
     t.take<float>((size_t)chunk * k);
     t.take<float>((size_t)chunk * k * k);
-    if ((st = ensure(h->ws, h->ws_bytes, t.off)) != MECUCO_OK) return st;
+    if ((st = ensure(h->ws, h->ws_bytes, t.off, h->ws_cap)) != MECUCO_OK) return st;
     Carver c(h->ws);
     float *G = c.take<float>((size_t)chunk * k * k);
     float *R = c.take<float>((size_t)chunk * k);
@@ -899,7 +927,7 @@ mecuco_status mecuco_curvature_exact(mecuco_t h, const void *X, mecuco_dtype dt,
     t.take<float>((size_t)chunk * m * m);
     size_t need = t.off;
     if (!idx) need = std::max(need, knn_bytes(h, X, dt, N, m, ld, nrows, k, prec, idx_bytes));
-    if ((st = ensure(h->ws, h->ws_bytes, need)) != MECUCO_OK) return st;
+    if ((st = ensure(h->ws, h->ws_bytes, need, h->ws_cap)) != MECUCO_OK) return st;
     const int32_t *nbr = idx ? idx + rb * k : nullptr;
     if (!idx) {
         int32_t *idx_buf = reinterpret_cast<int32_t *>(h->ws);
@@ -943,7 +971,7 @@ mecuco_status mecuco_fidelity(mecuco_t h, const float *kappa_ref, const float *k
     cudaStream_t s = (cudaStream_t)stream;
     mecuco_status st;
     if ((st = begin_call(h, s)) != MECUCO_OK) return st;
-    if ((st = ensure(h->ws, h->ws_bytes, fidelity_scratch_bytes(n))) != MECUCO_OK) return st;
+    if ((st = ensure(h->ws, h->ws_bytes, fidelity_scratch_bytes(n), h->ws_cap)) != MECUCO_OK) return st;
     LAUNCH(h, MECUCO_STAGE_FIDELITY, s, launch_fidelity(kappa_ref, kappa, n, normalize != 0, h->ws, metrics_out, s));
     return MECUCO_OK;
 }
@@ -953,7 +981,7 @@ mecuco_status mecuco_minmax_normalize(mecuco_t h, const float *x, int64_t n, flo
     cudaStream_t s = (cudaStream_t)stream;
     mecuco_status st;
     if ((st = begin_call(h, s)) != MECUCO_OK) return st;
-    if ((st = ensure(h->ws, h->ws_bytes, 8192)) != MECUCO_OK) return st;
+    if ((st = ensure(h->ws, h->ws_bytes, 8192, h->ws_cap)) != MECUCO_OK) return st;
     LAUNCH(h, MECUCO_STAGE_FIDELITY, s, launch_minmax_normalize(x, n, y, h->ws, s));
     return MECUCO_OK;
 }
@@ -1023,7 +1051,7 @@ mecuco_status mecuco_curvature_host(mecuco_t h, const void *X_host, mecuco_dtype
     t.take<char>(xbytes);
     t.take<float>((size_t)N);
     t.take<int32_t>((size_t)N * k);
-    if ((st = ensure(h->io, h->io_bytes, t.off)) != MECUCO_OK) return st;
+    if ((st = ensure(h->io, h->io_bytes, t.off, h->ws_cap)) != MECUCO_OK) return st;
     Carver c(h->io);
     char *Xd = c.take<char>(xbytes);
     float *kd = c.take<float>((size_t)N);
@@ -1033,7 +1061,7 @@ mecuco_status mecuco_curvature_host(mecuco_t h, const void *X_host, mecuco_dtype
     if (prec == MECUCO_PREC_BF16_MIXED && (st = ensure_pairs(h, k)) != MECUCO_OK) return st;
     const size_t need = std::max(knn_bytes(h, Xd, dt, N, m, ld, N, k, prec, 0),
                                  curvature_bytes(h, Xd, dt, N, m, ld, k, true, N, prec));
-    if ((st = ensure(h->ws, h->ws_bytes, need)) != MECUCO_OK) return st;
+    if ((st = ensure(h->ws, h->ws_bytes, need, h->ws_cap)) != MECUCO_OK) return st;
     if ((st = run_knn(h, h->ws, Xd, dt, N, m, ld, k, include_self, prec, 0, N, id, nullptr, s, 0)) != MECUCO_OK)
         return st;
     if ((st = run_curvature(h, h->ws, Xd, dt, N, m, ld, k, id, include_self, var, prec, 0, N, kd, nullptr, nullptr,
@@ -1073,6 +1101,7 @@ mecuco_status mecuco_get_stats(mecuco_t h, mecuco_stats *out, void *stream) {
     out->jacobi_max_sweeps = (int64_t)c.jacobi_max_sweeps;
     out->jacobi_not_converged = (int64_t)c.jacobi_not_converged;
     out->rank_deficient = (int64_t)c.rank_deficient;
+    out->jacobi_rotations = (int64_t)c.jacobi_rotations;
     out->kernel_launches = h->launches;
     return MECUCO_OK;
 }

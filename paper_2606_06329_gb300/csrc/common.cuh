@@ -23,6 +23,7 @@ struct DevCounters {
     unsigned long long jacobi_max_sweeps;
     unsigned long long jacobi_not_converged;
     unsigned long long rank_deficient;
+    unsigned long long jacobi_rotations;  // plane rotations applied by the Jacobi sweeps
     unsigned status;
     unsigned pad;
 };

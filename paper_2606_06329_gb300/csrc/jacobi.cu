@@ -78,6 +78,7 @@ jacobi_kernel(const float *__restrict__ G, int k, int64_t np, int max_sweeps, Re
 
     int sweep = 0;
     bool converged = false;
+    unsigned long long rotations = 0;  // tid 0's running total (counters only)
     for (; sweep < max_sweeps; ++sweep) {
         for (int round = 0; round < kp - 1; ++round) {
             if (tid < h) {
@@ -136,6 +137,7 @@ jacobi_kernel(const float *__restrict__ G, int k, int64_t np, int max_sweeps, Re
             __syncthreads();
         }
         const int rot = s_rot;
+        rotations += (unsigned long long)rot;
         __syncthreads();
         if (tid == 0) s_rot = 0;
         __syncthreads();
@@ -156,6 +158,7 @@ jacobi_kernel(const float *__restrict__ G, int k, int64_t np, int max_sweeps, Re
     }
     if (tid == 0) {
         atomicMax(&ctr->jacobi_max_sweeps, (unsigned long long)(converged ? sweep : max_sweeps));
+        atomicAdd(&ctr->jacobi_rotations, rotations);
         if (!converged) {
             atomicAdd(&ctr->jacobi_not_converged, 1ull);
             atomicOr(&ctr->status, (unsigned)DEV_NOT_CONVERGED);

@@ -34,10 +34,13 @@ cudaError_t launch_knn_simt(const void *X, mecuco_dtype dt, int64_t N, int64_t m
 // with ldb % 8 == 0 and a 16-byte aligned base (X itself when it is stored that
 // way, else a copy made by launch_to_bf16).  kc <= 64.
 // pair != 0 (and nq >= 256): CTA pairs sharing 256 x 256 cta_group::2 MMAs;
-// the lists are the same.
+// the lists are the same.  wait_limit: clock cycles after which a wait of the
+// work loops gives up (MECUCO_ERR_TIMEOUT); <= 0 selects the default (~0.5 s).
+// The drains of copies and MMAs in flight always use the default.
 cudaError_t launch_knn_tc(const void *Xb, int64_t N, int64_t m, int64_t ldb, const float *norms,
                           int64_t q0, int64_t nq, int kc, int nsplit, int include_self,
-                          float *cand_d, int32_t *cand_i, int pair, DevCounters *ctr, cudaStream_t s);
+                          float *cand_d, int32_t *cand_i, int pair, long long wait_limit, DevCounters *ctr,
+                          cudaStream_t s);
 size_t knn_tc_smem_bytes(int kc);
 // Candidate lists the tensor-core search leaves per row and split (the epilogue's
 // column halves); list h of row r, split s starts at ((r nsplit + s) halves + h) kc.
@@ -92,12 +95,13 @@ void m3_build_items(int k, int32_t *items /* m3_items(k) */);
 
 // BF16-mixed form: G, R, Q and the pair-major M of each patch from
 // tensor-core GEMMs over 128-row tiles of row products (BF16 operands, FP32
-// accumulation), nslots TMEM slots for the A operand.  rowtab holds moments_tc_rows(k) row codes built by
+// accumulation), nslots TMEM slots for the A operand; wait_limit as for
+// launch_knn_tc.  rowtab holds moments_tc_rows(k) row codes built by
 // moments_tc_build_rows; idx points at the chunk's first neighbour row; Q may
 // be NULL.
 cudaError_t launch_moments_tc(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, const int32_t *idx,
                               int k, int64_t np, const int32_t *rowtab, float *M, float *G, float *R, float *Q,
-                              int nslots, DevCounters *ctr, cudaStream_t s);
+                              int nslots, long long wait_limit, DevCounters *ctr, cudaStream_t s);
 int moments_tc_rows(int k);
 void moments_tc_build_rows(int k, int32_t *codes /* moments_tc_rows(k) */);
 size_t moments_tc_smem_bytes(int k);

@@ -227,8 +227,12 @@ knn_rerank_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld,
     const T *xq = X + q * ld;
 
     float err_max = -INFINITY, err_min = INFINITY, nmax = 0.f;
+    bool bad = false;
     for (int c = 0; c < L; ++c) {
         int j = cidx[c];
+        // a complete search leaves -1 or a row of X in every slot; anything else
+        // (slots a search that timed out never wrote) is skipped, never read
+        if (j >= N) { bad = true; j = -1; }
         ff acc{0.f, 0.f};
         if (j >= 0) {
             const T *xj = X + (int64_t)j * ld;
@@ -251,7 +255,7 @@ knn_rerank_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld,
         bool full = true;
         for (int c = lane; c < kc; c += 32) {
             float v = cd[sp * kc + c];
-            full = full && (cidx[sp * kc + c] >= 0);
+            full = full && (ci[sp * kc + c] >= 0);
             mx = fmaxf(mx, v);
         }
         mx = warp_max(mx);
@@ -276,6 +280,7 @@ knn_rerank_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld,
         if (rank == k - 1) theta = me.hi;
     }
     theta = warp_max(theta);
+    if (lane == 0 && bad) atomicOr(&ctr->status, (unsigned)DEV_INVALID);
     if (lane == 0) {
         const float spread = err_max - err_min;
         const float e_hi = fmaxf(err_max, 0.f) + 3.f * spread + ldexpf(norms[q] + nmax, -21);

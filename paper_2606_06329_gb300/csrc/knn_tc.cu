@@ -33,7 +33,9 @@
 // so single CTAs are the default.
 // Every mbarrier wait is bounded; a timeout sets MECUCO_ERR_TIMEOUT in the
 // device status word, raises a CTA-wide abort flag, drains the copies and MMAs
-// already in flight (also bounded), frees TMEM and returns.
+// already in flight (also bounded), frees TMEM and returns.  The limit of the
+// waits in the work loops is a launch argument (default WAIT_LIMIT); the drains
+// always use WAIT_LIMIT, since the copies and MMAs they wait for complete.
 #include <cudaTypedefs.h>
 #include <math.h>
 
@@ -146,7 +148,8 @@ template <bool PAIR>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, int64_t N,
               int64_t m, const float *__restrict__ norms, int64_t q0, int64_t nq, int kc, int nsplit,
-              int include_self, float *__restrict__ cand_d, int32_t *__restrict__ cand_i, DevCounters *ctr) {
+              int include_self, float *__restrict__ cand_d, int32_t *__restrict__ cand_i, long long wait_limit,
+              DevCounters *ctr) {
     // Persistent: CTA (pair) b takes work items b, b + G, b + 2G, ... (G CTAs or
     // pairs), item = (query block item / nsplit, candidate split item % nsplit).
     // All start their items together and every item has the same number of
@@ -237,7 +240,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
             for (int t = 0; t < ntiles && ok && !*abort_flag; ++t) {
                 const int c0 = (int)(cbeg + (int64_t)t * TBN) + (int)rank * C::B_ROWS;
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
-                    if (!tc::mbar_wait(empty0 + 8 * s, ph ^ 1u, abort_flag, WAIT_LIMIT)) { ok = false; break; }
+                    if (!tc::mbar_wait(empty0 + 8 * s, ph ^ 1u, abort_flag, wait_limit)) { ok = false; break; }
                     const uint32_t sa = st0 + s * (uint32_t)STAGE;
                     if constexpr (PAIR) {
                         if (rank == 0) tc::mbar_expect_tx(full0 + 8 * s, 2 * STAGE);
@@ -294,16 +297,16 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
                 const int acc = t & 1;
                 const uint32_t te = tc::smem_u32(&sh->tempty[acc]);
                 const uint32_t tpar = ((t >> 1) & 1) ^ 1;
-                if (!(PAIR ? tc::mbar_wait_cluster(te, tpar, abort_flag, WAIT_LIMIT)
-                           : tc::mbar_wait(te, tpar, abort_flag, WAIT_LIMIT))) {
+                if (!(PAIR ? tc::mbar_wait_cluster(te, tpar, abort_flag, wait_limit)
+                           : tc::mbar_wait(te, tpar, abort_flag, wait_limit))) {
                     ok = false;
                     break;
                 }
                 tc::fence_after();
                 const uint32_t dt = tmem + (uint32_t)(acc * TBN);
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
-                    if (!(PAIR ? tc::mbar_wait_cluster(full0 + 8 * s, ph, abort_flag, WAIT_LIMIT)
-                               : tc::mbar_wait(full0 + 8 * s, ph, abort_flag, WAIT_LIMIT))) {
+                    if (!(PAIR ? tc::mbar_wait_cluster(full0 + 8 * s, ph, abort_flag, wait_limit)
+                               : tc::mbar_wait(full0 + 8 * s, ph, abort_flag, wait_limit))) {
                         ok = false;
                         break;
                     }
@@ -363,7 +366,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
             int32_t *out_i = cand_i + out_base;
             for (int tt = 0; tt < ntiles && !*abort_flag; ++tt, ++t) {
                 const int acc = t & 1;
-                if (!tc::mbar_wait(tc::smem_u32(&sh->tfull[acc]), (t >> 1) & 1, abort_flag, WAIT_LIMIT)) {
+                if (!tc::mbar_wait(tc::smem_u32(&sh->tfull[acc]), (t >> 1) & 1, abort_flag, wait_limit)) {
                     atomicOr(&ctr->status, (unsigned)DEV_TIMEOUT);
                     sh->abort = 1;
                     break;
@@ -458,8 +461,9 @@ int knn_tc_halves() { return TC_HALVES; }
 
 cudaError_t launch_knn_tc(const void *Xb, int64_t N, int64_t m, int64_t ldb, const float *norms, int64_t q0,
                           int64_t nq, int kc, int nsplit, int include_self, float *cand_d, int32_t *cand_i, int pair,
-                          DevCounters *ctr, cudaStream_t s) {
+                          long long wait_limit, DevCounters *ctr, cudaStream_t s) {
     if (nq <= 0) return cudaSuccess;
+    if (wait_limit <= 0) wait_limit = WAIT_LIMIT;
     if ((reinterpret_cast<uintptr_t>(Xb) & 15) || (ldb % 8) != 0 || kc > 64) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
     if (!make_map(&ma, Xb, N, m, ldb, TBM) || !make_map(&mb, Xb, N, m, ldb, TBN)) return cudaErrorInvalidValue;
@@ -492,8 +496,10 @@ cudaError_t launch_knn_tc(const void *Xb, int64_t N, int64_t m, int64_t ldb, con
         if (nclusters > 0) {
             const int64_t items = ((nq + 2 * TBM - 1) / (2 * TBM)) * nsplit;
             cfg.gridDim = dim3((unsigned)(2 * (items < nclusters ? items : nclusters)));
+            // the pair form keeps the default limit: its cross-CTA arrivals are
+            // not exercised with shortened waits
             e = cudaLaunchKernelEx(&cfg, knn_tc_kernel<true>, ma, ma, N, m, norms, q0, nq, kc, nsplit, include_self,
-                                   cand_d, cand_i, ctr);
+                                   cand_d, cand_i, WAIT_LIMIT, ctr);
             if (e != cudaSuccess) return e;
             return cudaGetLastError();
         }
@@ -504,7 +510,7 @@ cudaError_t launch_knn_tc(const void *Xb, int64_t N, int64_t m, int64_t ldb, con
     const int64_t items = ((nq + TBM - 1) / TBM) * nsplit;
     dim3 grid((unsigned)(items < sms ? items : sms));  // persistent: one CTA per SM
     knn_tc_kernel<false><<<grid, TC_THREADS, smem, s>>>(ma, mb, N, m, norms, q0, nq, kc, nsplit, include_self,
-                                                         cand_d, cand_i, ctr);
+                                                         cand_d, cand_i, wait_limit, ctr);
     return cudaGetLastError();
 }
 

@@ -37,8 +37,10 @@
 // TMEM holds the accumulators of up to (512 - 32 slots)/N tiles, so the tiles are covered
 // in passes over the columns (the patch is re-read from L2).  After a pass the
 // formers read the accumulators back (tcgen05.ld) and store each row to its
-// destination.  Every wait is bounded (MECUCO_ERR_TIMEOUT, no trap); the MMA
-// warp waits for its last MMAs before TMEM is freed.
+// destination.  Every wait is bounded (MECUCO_ERR_TIMEOUT, no trap; the
+// limit of the waits in the work loops is a launch argument, default ~0.5 s);
+// the MMA warp waits for its last MMAs (always with the default limit) before
+// TMEM is freed.
 #include <math.h>
 
 #include <algorithm>
@@ -181,7 +183,8 @@ template <typename T>
 __global__ void __launch_bounds__(MT_THREADS, 1)
 moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, const int32_t *__restrict__ idx, int k,
                   const int32_t *__restrict__ rowtab, int nrows, float *__restrict__ M, float *__restrict__ G,
-                  float *__restrict__ R, float *__restrict__ Q, int nslots, DevCounters *ctr) {
+                  float *__restrict__ R, float *__restrict__ Q, int nslots, long long wait_limit,
+                  DevCounters *ctr) {
     extern __shared__ __align__(1024) uint8_t msm_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(msm_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *Bop0 = base;                                                       // 2 x B operand
@@ -190,7 +193,7 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
     float *Part = Xs + 64 * MT_XS_LD;                                           // [4][64] column partials
     int32_t *codes = reinterpret_cast<int32_t *>(Part + 4 * 64);                // [nrows]
     __shared__ uint64_t slot_full[MT_MAX_SLOTS], slot_empty[MT_MAX_SLOTS];
-    __shared__ uint64_t chunk_ready[2], chunk_done[2], pass_done, d_free;
+    __shared__ uint64_t chunk_ready[2], chunk_done[2], pass_done, d_free, mma_fin;
     __shared__ uint32_t tmem_slot;
     __shared__ int rows[64];
     __shared__ int abort_flag, never;
@@ -233,6 +236,7 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
         }
         tc::mbar_init(tc::smem_u32(&pass_done), 1);
         tc::mbar_init(tc::smem_u32(&d_free), MT_FORMER_WARPS);
+        tc::mbar_init(tc::smem_u32(&mma_fin), 1);
         abort_flag = (*(volatile unsigned *)&ctr->status & DEV_TIMEOUT) ? 1 : 0;
         never = 0;
         tc::fence_mbar_init();
@@ -251,7 +255,7 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
         abort_flag = 1;
     };
     auto wait = [&](uint64_t *bar, uint32_t parity) {
-        if (!*abortp && !tc::mbar_wait(tc::smem_u32(bar), parity, abortp, MT_WAIT)) fail();
+        if (!*abortp && !tc::mbar_wait(tc::smem_u32(bar), parity, abortp, wait_limit)) fail();
     };
 
     if (warp < MT_PRODUCER_WARPS) {
@@ -461,7 +465,7 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
                     const uint64_t bd0 = tc::sdesc_sw128(tc::smem_u32(Bop0 + (gc & 1) * MT_B_BYTES));
                     uint32_t d = tmem;
                     for (int t = 0; t < nt; t += MT_GROUP, d += (uint32_t)(MT_GROUP * Nb)) {
-                        if (!tc::mbar_wait(slot_full0 + 8 * s, ph, abortp, MT_WAIT)) {
+                        if (!tc::mbar_wait(slot_full0 + 8 * s, ph, abortp, wait_limit)) {
                             fail();
                             ok = false;
                             break;
@@ -489,8 +493,14 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
                 }
                 tc::commit(tc::smem_u32(&pass_done));
             }
-            // every MMA has completed before TMEM is freed, whatever happened elsewhere
-            if (!tc::mbar_wait(tc::smem_u32(&pass_done), (npass - 1) & 1, &never, MT_WAIT)) fail();
+            // every MMA has completed before TMEM is freed, whatever happened
+            // elsewhere: a commit tracks all earlier MMAs of this thread, and a
+            // barrier used once has an unambiguous phase 0 (after an abort,
+            // pass_done may have two commits pending, and a parity wait there can
+            // name a phase that completed earlier).  The wait keeps the long
+            // default limit: MMAs in flight always complete.
+            tc::commit(tc::smem_u32(&mma_fin));
+            if (!tc::mbar_wait(tc::smem_u32(&mma_fin), 0u, &never, MT_WAIT)) fail();
         }
         __syncwarp();
     }
@@ -504,8 +514,9 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
 
 cudaError_t launch_moments_tc(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, const int32_t *idx,
                               int k, int64_t np, const int32_t *rowtab, float *M, float *G, float *R, float *Q,
-                              int nslots, DevCounters *ctr, cudaStream_t s) {
+                              int nslots, long long wait_limit, DevCounters *ctr, cudaStream_t s) {
     if (np <= 0) return cudaSuccess;
+    if (wait_limit <= 0) wait_limit = MT_WAIT;
     if (k > 64 || k < 2) return cudaErrorInvalidValue;
     if (nslots < MT_GROUP || nslots > MT_MAX_SLOTS || nslots % MT_GROUP != 0 ||
         (512 - nslots * MT_SLOT_COLS) < moments_tc_n(k))
@@ -519,12 +530,12 @@ cudaError_t launch_moments_tc(const void *X, mecuco_dtype dt, int64_t N, int64_t
                                  (int)smem);
         if (e != cudaSuccess) return e;
         moments_tc_kernel<<<(unsigned)np, MT_THREADS, smem, s>>>((const __nv_bfloat16 *)X, N, m, ld, idx, k, rowtab,
-                                                                 nrows, M, G, R, Q, nslots, ctr);
+                                                                 nrows, M, G, R, Q, nslots, wait_limit, ctr);
     } else {
         e = cudaFuncSetAttribute(moments_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         moments_tc_kernel<<<(unsigned)np, MT_THREADS, smem, s>>>((const float *)X, N, m, ld, idx, k, rowtab, nrows, M,
-                                                                 G, R, Q, nslots, ctr);
+                                                                 G, R, Q, nslots, wait_limit, ctr);
     }
     return cudaGetLastError();
 }

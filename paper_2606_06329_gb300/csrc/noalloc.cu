@@ -11,16 +11,20 @@
 // copy is loaded holds until the process exits.
 //
 // The array's name in host code is only a host-side stand-in, so its device
-// address is looked up once per device with cudaGetSymbolAddress (on that
-// device, under a lock) and passed to the kernels.  The first call on a device
-// does that lookup (which may load this module) and should therefore come
-// before any stream capture.  All calls share the array and it keeps the last
+// address is looked up with cudaGetSymbolAddress once per device and context
+// (on that device, under a lock) and passed to the kernels.  The first call on
+// a device does that lookup (which may load this module) and should therefore
+// come before any stream capture.  The cache is keyed on the current CUDA
+// context, so after a cudaDeviceReset (which destroys the primary context and
+// this module's copy of the array with it) the next call looks the address up
+// again in the new context instead of using a stale one.  All calls share the array and it keeps the last
 // call's contents: the counters are cleared at the start of each call, and
 // calls whose work overlaps on the GPU (different streams, or different host
 // threads on one device) race on the array and must be serialised by the
 // caller.  The work is the plain FP32 candidate search, the exact re-rank and
 // the exact full-scan fallback of mecuco_knn, so the lists are the same as
 // mecuco_knn(..., MECUCO_PREC_FP32, ...) returns.
+#include <cuda.h>
 #include <stdio.h>
 
 #include <algorithm>
@@ -40,21 +44,46 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
 std::mutex g_noalloc_mu;
 void *g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+CUcontext g_noalloc_ctx[NOALLOC_MAX_DEVICES] = {};
 
 inline size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 
-// Device address of the scratch array on the current device (looked up once).
+// cuCtxGetCurrent from the driver the runtime already loaded (no -lcuda).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+CtxGetCurrentFn ctx_get_current() {
+    static CtxGetCurrentFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrentFn>(p);
+    }
+    return fn;
+}
+
+// Device address of the scratch array on the current device (looked up once
+// per device and context).
 cudaError_t scratch_address(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+    CUcontext cur = nullptr;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    CtxGetCurrentFn get = ctx_get_current();
+    if (get && get(&cur) != CUDA_SUCCESS) cur = nullptr;
+    if (!g_noalloc_addr[dev] || !get || !cur || cur != g_noalloc_ctx[dev]) {
+        // the lookup binds the device's primary context if none is current yet,
+        // so the context is read again after it
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
+        if (get && get(&cur) != CUDA_SUCCESS) cur = nullptr;
         g_noalloc_addr[dev] = p;
+        g_noalloc_ctx[dev] = cur;
     }
     *out = g_noalloc_addr[dev];
     return cudaSuccess;
@@ -102,7 +131,13 @@ extern "C" MECUCO_API mecuco_status mecuco_knn_noalloc(const void *X, mecuco_dty
     };
     while (nsplit > 1 && need(qchunk, nsplit) > NOALLOC_BYTES) --nsplit;
     while (qchunk > 128 && need(qchunk, nsplit) > NOALLOC_BYTES) qchunk /= 2;
-    if (need(qchunk, nsplit) > NOALLOC_BYTES) return MECUCO_ERR_INVALID_ARG;
+    if (need(qchunk, nsplit) > NOALLOC_BYTES) {
+        char msg[160];
+        snprintf(msg, sizeof(msg), "mecuco_knn_noalloc: N = %lld needs more than the %zu bytes of its fixed scratch",
+                 (long long)N, NOALLOC_BYTES);
+        set_error_text(msg);
+        return MECUCO_ERR_INVALID_ARG;
+    }
 
     char *p = static_cast<char *>(base);
     DevCounters *ctr = reinterpret_cast<DevCounters *>(p);

@@ -59,6 +59,20 @@ def test_noalloc_matches_context_entry_point_twice(lib_ctx):
     assert torch.equal(idx_c, ctx.mecuco_knn(X, k, include_self=inc))
 
 
+def test_noalloc_crosses_its_query_chunks(lib_ctx):
+    # N above the entry point's 16,384-row query chunk: three launches writing
+    # at row offsets, and a candidate split different from mecuco_knn's plan;
+    # after the exact re-rank the lists and distances must still be the same
+    lib, ctx = lib_ctx
+    X = torch.from_numpy(synth.sphere(n=40000, m=32, seed=13)).cuda()
+    for _ in range(2):
+        idx_a, dist_a = _noalloc(lib, X, 10)
+        idx_b, dist_b = ctx.mecuco_knn(X, 10, precision="fp32", return_dist=True)
+        torch.cuda.synchronize()
+        assert torch.equal(idx_a, idx_b)
+        assert torch.allclose(dist_a, dist_b, rtol=1e-6, atol=0)
+
+
 def test_noalloc_rejects_oversized_problems(lib_ctx):
     lib, _ = lib_ctx
     from paper_2606_06329_gb300 import _native as N
