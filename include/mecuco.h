@@ -107,8 +107,9 @@ typedef enum {
                                         pairs; more slots leave fewer accumulator tiles per pass over the
                                         patch) */
     MECUCO_OPT_KNN_PAIR = 9,         /* 1: the tensor-core kNN search runs as CTA pairs sharing 256 x 256
-                                        two-SM MMAs (tcgen05 cta_group::2); 0 (default): one CTA per SM.
-                                        The candidate lists are identical */
+                                        two-SM MMAs (tcgen05 cta_group::2); 0: one CTA per SM; -1 (default):
+                                        pairs for N >= 200,000 points, where they are faster.  The candidate
+                                        lists are identical */
     MECUCO_OPT_WAIT_LIMIT = 10,      /* SM clock cycles after which a bounded wait in the work loops of the
                                         tensor-core kernels (kNN search on single CTAs, patch moments) gives
                                         up: the launch sets MECUCO_ERR_TIMEOUT in the status word, waits for

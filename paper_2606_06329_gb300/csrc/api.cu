@@ -64,7 +64,7 @@ struct mecuco_ctx {
     int32_t *m3_items[65] = {};  // per k: work items of the CUDA-core third-moment kernel
     int32_t *rowtab[65] = {};    // per k: row codes of the tensor-core moment kernel
     int knn_splits = 0;
-    int knn_pair = 0;
+    int knn_pair = -1;  // -1: CTA pairs for N >= KNN_PAIR_MIN_N
     int chunk_share = 1;  // concurrent lanes sharing the chunk budget (batched calls)
     int tc_slots = 4;
     // randomised low-rank SVD (mecuco_curvature_rsvd), set for the duration of a call
@@ -209,12 +209,15 @@ int candidate_capacity(mecuco_t h, int k) {
     return (int)kc;
 }
 
+constexpr int64_t KNN_PAIR_MIN_N = 200000;
+
 struct KnnPlan {
     int kc, nsplit;
     int lists;      // candidate lists per query row (splits x the tensor-core kernel's column halves)
     int kcl;        // capacity of each list
     int64_t qchunk;
     bool tc;        // candidate search on the tensor cores (BF16 operands)
+    bool pair;      // tensor-core search as CTA pairs sharing two-SM MMAs
     bool bf16_copy; // the tensor-core path needs a BF16 copy of X
     int64_t ldb;    // leading dimension of the BF16 operand
 };
@@ -224,6 +227,11 @@ KnnPlan plan_knn(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t 
     KnnPlan p;
     p.kc = candidate_capacity(h, k);
     p.tc = prec == MECUCO_PREC_BF16_MIXED;
+    // CTA pairs (256 x 256 two-SM MMAs, half the candidate bytes per SM) pay
+    // from a few hundred thousand candidates up: measured at m = 4096, k = 64,
+    // 1M points 7.53 s against 7.93 s per search, 300k 0.683 against 0.716 s,
+    // but 100k 88.5 against 85.4 ms
+    p.pair = p.tc && (h->knn_pair > 0 || (h->knn_pair < 0 && N >= KNN_PAIR_MIN_N));
     const bool direct = dt == MECUCO_BF16 && ld % 8 == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
     p.bf16_copy = p.tc && !direct;
     p.ldb = direct ? ld : (m + 7) / 8 * 8;
@@ -286,7 +294,7 @@ mecuco_status run_knn(mecuco_t h, char *ws, const void *X, mecuco_dtype dt, int6
         if (p.tc) {
             LAUNCH(h, MECUCO_STAGE_KNN_SEARCH, s,
                    launch_knn_tc(Xb, N, m, p.ldb, b.norms, q0, nq, p.kcl, p.nsplit, include_self, b.cand_d,
-                                 b.cand_i, h->knn_pair, h->wait_limit, h->ctr, s));
+                                 b.cand_i, p.pair ? 1 : 0, h->wait_limit, h->ctr, s));
         } else {
             LAUNCH(h, MECUCO_STAGE_KNN_SEARCH, s,
                    launch_knn_simt(X, dt, N, m, ld, b.norms, q0, nq, p.kc, p.nsplit, include_self, b.cand_d,
@@ -709,7 +717,7 @@ mecuco_status mecuco_set_option(mecuco_t h, mecuco_option opt, int64_t v) {
             h->tc_slots = (int)v;
             break;
         case MECUCO_OPT_KNN_PAIR:
-            if (v < 0 || v > 1) return MECUCO_ERR_INVALID_ARG;
+            if (v < -1 || v > 1) return MECUCO_ERR_INVALID_ARG;
             h->knn_pair = (int)v;
             break;
         case MECUCO_OPT_PROFILE_STAGES:

@@ -76,6 +76,7 @@ def test_tc_knn_cta_pairs(ctx, orc, n, m, k):
     finally:
         ctx.set_option(N.OPT_KNN_PAIR, 0)
     si, sdist = ctx.mecuco_knn(Xd, k, precision="bf16_mixed", return_dist=True)
+    ctx.set_option(N.OPT_KNN_PAIR, -1)
     assert np.array_equal(pair, si.cpu().numpy())
     assert torch.equal(pi, si) and torch.equal(pdist, sdist)
 
@@ -191,3 +192,4 @@ def test_tc_moment_slots_do_not_change_results(ctx, k, variant):
         ctx.set_option(N.OPT_TC_SLOTS, 4)
     for o in outs[1:]:
         assert torch.equal(o, outs[0])
+
