@@ -252,12 +252,15 @@ def aggregate_timing(elapsed_ms: float, n_per_rank: int, steps: int, dist=None, 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA (2 FLOP) x 2.07 GHz
 
 
-def _stage_fracs(stages, steps, N, m, k, prec, rotations, peaks):
+def _stage_fracs(stages, steps, N, m, k, prec, rotations, peaks, elt=2):
     """Per-stage achieved rate against its binding roof, from one profiled step
     (CUDA events around every launch).  Algorithmic work per stage:
       knn_search  2 N^2 m FLOP (tensor, BF16; FP32 lanes in the plain form)
       knn_rerank  N x 128 candidate rows x m x 2 bytes read (2 lists of 64 per
                   row from the tensor-core search at k = 64), against HBM
+      gram        the gathered patches, N k m elements, against HBM
+      rotate      the gathered patches plus the rotated patches written
+                  (N x 64 rows x m BF16), against HBM
       moments     k(k+1)(k+2)/6 m multiply-adds per point (the distinct third
                   moments), x 2 FLOP (tensor, BF16)
       jacobi      18 k FLOP per plane rotation (two-sided update of A and the
@@ -271,6 +274,8 @@ def _stage_fracs(stages, steps, N, m, k, prec, rotations, peaks):
     work = {
         "knn_search": (2.0 * N * N * m, "tensor" if prec == "bf16_mixed" else "alu"),
         "knn_rerank": (N * 128.0 * m * 2.0, "hbm"),
+        "gram": (float(N) * k * m * elt, "hbm"),
+        "rotate": (float(N) * k * m * elt + N * 64.0 * m * 2.0, "hbm"),
         "moments": (2.0 * k * (k + 1) * (k + 2) / 6.0 * m * N, "tensor"),
         "jacobi": (18.0 * k * rotations + 8.0 * k ** 3 * N, "alu"),
         "estimator": (k * (2.0 * k * k * p + k * p * (p + 1)) * N, "alu"),
@@ -401,7 +406,8 @@ def run_ours(args):
                        "timing": "headline with only the distance-search launches event-bracketed; stage "
                                  "times from one further step with every launch bracketed"},
             "roofline": roof, "gpu_launches": launches, "clocks": clk, "status": status,
-            "stages": _stage_fracs(stages, 1, N, m, k, prec, stats1["jacobi_rotations"], peaks),
+            "stages": _stage_fracs(stages, 1, N, m, k, prec, stats1["jacobi_rotations"], peaks,
+                                   elt=Xd.element_size()),
             "knn_stats": {kk: stats[kk] for kk in ("knn_uncertified", "knn_fallback_rows", "jacobi_max_sweeps",
                                                   "jacobi_not_converged", "rank_deficient", "jacobi_rotations")}}
 

@@ -78,11 +78,15 @@ typedef enum { MECUCO_FAST_LITERAL = 0, MECUCO_FAST_HAAR = 1 } mecuco_variant;
  *               FP32 on the CUDA cores; FP32 Jacobi.  (the plain form)
  *   BF16_MIXED: distance GEMM in BF16 on the tensor cores with FP32
  *               accumulation and an FP32 exact re-rank of the candidates;
- *               patch moments (G, R, Q, third moments) from BF16 operands on
- *               the tensor cores with FP32 accumulation; Jacobi sweeps in FP32
- *               followed by one refinement step of the eigenpairs whose
- *               products are carried beyond FP32 (two-term FP32, ~2^-48
- *               relative).  (the chosen form) */
+ *               the patch Gram (and Q) from BF16 operands on the tensor cores
+ *               with FP32 accumulation; Jacobi sweeps in FP32 followed by one
+ *               refinement step of the eigenpairs whose products are carried
+ *               beyond FP32 (two-term FP32, ~2^-48 relative); the rotated
+ *               patch Y = U^T X_c on the tensor cores (U in two BF16 terms),
+ *               rounded to BF16; the estimator's sums from the third moments
+ *               of Y, BF16 products with FP32 accumulation, on the tensor
+ *               cores.  (the chosen form; with a randomised SVD the third
+ *               moments of X_c and the k-space estimator of the plain form) */
 typedef enum { MECUCO_PREC_FP32 = 0, MECUCO_PREC_BF16_MIXED = 1 } mecuco_precision;
 
 /* Tunable options (mecuco_set_option).  Values are int64. */
@@ -131,14 +135,16 @@ typedef enum {
     MECUCO_STAGE_KNN_RERANK = 2, /* exact re-rank + certification */
     MECUCO_STAGE_KNN_FALLBACK = 3,/* exact full scan of uncertified rows */
     MECUCO_STAGE_GRAM = 4,       /* gather, centre, G = X_c X_c^T, R, Q */
-    MECUCO_STAGE_MOMENTS = 5,    /* gather, centre, third moments M */
+    MECUCO_STAGE_MOMENTS = 5,    /* third moments: of X_c (plain form, M stored), or of the rotated patch
+                                    reduced on the fly to the estimator's sums (BF16-mixed form) */
     MECUCO_STAGE_JACOBI = 6,     /* k x k eigensolve */
     MECUCO_STAGE_ESTIMATOR = 7,  /* k-space Fast estimator */
     MECUCO_STAGE_ADJOINT = 8,    /* k-space adjoint + patch adjoint and scatter */
     MECUCO_STAGE_BASIS = 9,      /* tangent-basis expansion V_r = X_c^T U_p S^-1 */
     MECUCO_STAGE_EXACT = 10,     /* Exact mode: m x m covariance and K from its eigenbasis */
     MECUCO_STAGE_FIDELITY = 11,  /* agreement metrics: sorts, ranks, sums */
-    MECUCO_STAGE_COUNT = 12
+    MECUCO_STAGE_ROTATE = 12,    /* BF16-mixed form: gather, centre, rotated patch Y = U^T X_c */
+    MECUCO_STAGE_COUNT = 13
 } mecuco_stage;
 
 /* Counters of the last completed call (valid after the stream is synchronised). */

@@ -20,7 +20,7 @@ PREC_FP32, PREC_BF16_MIXED = 0, 1
  OPT_KNN_SPLITS, OPT_BATCH_LANES, OPT_TC_SLOTS, OPT_KNN_PAIR, OPT_WAIT_LIMIT, OPT_WORKSPACE_LIMIT,
  OPT_PROFILE_STAGES) = range(13)
 STAGES = ("rownorm", "knn_search", "knn_rerank", "knn_fallback", "gram", "moments", "jacobi", "estimator", "adjoint",
-          "basis", "exact", "fidelity")
+          "basis", "exact", "fidelity", "rotate")
 
 
 class MecucoNotBuilt(ImportError):

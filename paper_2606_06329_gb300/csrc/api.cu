@@ -63,6 +63,8 @@ struct mecuco_ctx {
     DevCounters *ctr = nullptr;
     int32_t *m3_items[65] = {};  // per k: work items of the CUDA-core third-moment kernel
     int32_t *rowtab[65] = {};    // per k: row codes of the tensor-core moment kernel
+    int32_t *gramtab[65][2] = {};// per k, without / with the Q rows: row codes of the Gram pass
+    int32_t *tttab[65] = {};     // per k: row codes of the third-moment pass (pairs only)
     int knn_splits = 0;
     int knn_pair = -1;  // -1: CTA pairs for N >= KNN_PAIR_MIN_N
     int chunk_share = 1;  // concurrent lanes sharing the chunk budget (batched calls)
@@ -351,6 +353,24 @@ mecuco_status ensure_pairs(mecuco_t h, int k) {
     return upload_table(&h->rowtab[k], host);
 }
 
+// Tables of the BF16-mixed estimator in the rotated basis: the Gram pass's G
+// (and Q) rows and the third-moment pass's pair rows.
+mecuco_status ensure_rotated(mecuco_t h, int k) {
+    mecuco_status st;
+    for (int w = 0; w < 2; ++w) {
+        if (h->gramtab[k][w]) continue;
+        std::vector<int32_t> host(128);
+        moments_tc_build_gram_rows(k, w, host.data());
+        if ((st = upload_table(&h->gramtab[k][w], host)) != MECUCO_OK) return st;
+    }
+    if (!h->tttab[k]) {
+        std::vector<int32_t> host((size_t)tthird_rows(k));
+        tthird_build_rows(k, host.data());
+        if ((st = upload_table(&h->tttab[k], host)) != MECUCO_OK) return st;
+    }
+    return MECUCO_OK;
+}
+
 mecuco_status ensure_items(mecuco_t h, int k) {
     if (h->m3_items[k]) return MECUCO_OK;
     std::vector<int32_t> host((size_t)mecuco::m3_items(k));
@@ -358,15 +378,23 @@ mecuco_status ensure_items(mecuco_t h, int k) {
     return upload_table(&h->m3_items[k], host);
 }
 
+// Leading dimension (BF16 elements) of the rotated patch Y: m rounded up to
+// whole 64-column chunks.
+inline int64_t rot_ld(int64_t m) { return (m + 63) / 64 * 64; }
+
 struct EstBufs {
     float *G, *R, *Q, *M, *sig, *U, *U0;
+    uint16_t *Y;  // rotated patches (BF16-mixed form): 64 rows of rot_ld(m) per point
     float *rQ, *rB, *rsig, *rV;  // randomised SVD: range basis, projected Gram and its eigenpairs
 };
-void est_scratch(Carver &c, int64_t chunk, int k, EstBufs *b, int rsvd_cols = 0) {
+// ym > 0: the rotated-basis estimator (BF16-mixed form) with Y for ambient
+// dimension ym in place of the third moments M.
+void est_scratch(Carver &c, int64_t chunk, int k, EstBufs *b, int rsvd_cols = 0, int64_t ym = 0) {
     b->G = c.take<float>((size_t)chunk * k * k);
     b->R = c.take<float>((size_t)chunk * k);
     b->Q = c.take<float>((size_t)chunk * k * k);
-    b->M = c.take<float>((size_t)chunk * m3_pair_floats(k));
+    b->M = ym ? nullptr : c.take<float>((size_t)chunk * m3_pair_floats(k));
+    b->Y = ym ? c.take<uint16_t>((size_t)chunk * 64 * rot_ld(ym)) : nullptr;
     b->sig = c.take<float>((size_t)chunk * k);
     b->U = c.take<float>((size_t)chunk * k * k);
     b->U0 = c.take<float>((size_t)chunk * k * k);
@@ -380,8 +408,8 @@ void est_scratch(Carver &c, int64_t chunk, int k, EstBufs *b, int rsvd_cols = 0)
 // Points per estimator chunk: an 8 GB scratch budget (shared by the lanes of a
 // batched call) - larger chunks leave smaller partial last waves: at k = 64,
 // 14k-point chunks took the per-chunk kernels 2.6% less time than 3.6k ones.
-int64_t est_chunk(mecuco_t h, int64_t nrows, int k) {
-    const int64_t per_point = m3_pair_floats(k) + 4LL * k * k + 3LL * k;
+int64_t est_chunk(mecuco_t h, int64_t nrows, int k, int64_t ym = 0) {
+    const int64_t per_point = (ym ? 32 * rot_ld(ym) : m3_pair_floats(k)) + 4LL * k * k + 3LL * k;
     int64_t chunk = h->chunk_points;
     if (chunk <= 0) {
         const size_t budget = ((size_t)8 << 30) / (size_t)std::max(1, h->chunk_share);
@@ -393,14 +421,21 @@ int64_t est_chunk(mecuco_t h, int64_t nrows, int k) {
 
 // Workspace bytes of run_curvature for nrows query rows (idx given, or
 // computed into the front of the workspace).
+// The BF16-mixed form runs the rotated-basis estimator (Gram pass, eigensolve,
+// rotation, third-moment pass) unless a randomised SVD replaces the eigensolve.
+inline int64_t rotated_m(mecuco_t h, int64_t m, mecuco_precision prec) {
+    return (prec == MECUCO_PREC_BF16_MIXED && !h->rsvd.cols) ? m : 0;
+}
+
 size_t curvature_bytes(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, int k,
                        bool idx_given, int64_t nrows, mecuco_precision prec) {
-    const int64_t chunk = est_chunk(h, nrows, k);
+    const int64_t ym = rotated_m(h, m, prec);
+    const int64_t chunk = est_chunk(h, nrows, k, ym);
     const size_t idx_bytes = idx_given ? 0 : align_up((size_t)nrows * k * sizeof(int32_t), 256);
     size_t need = idx_given ? 0 : knn_bytes(h, X, dt, N, m, ld, nrows, k, prec, idx_bytes);
     Carver c(nullptr, idx_bytes);
     EstBufs b;
-    est_scratch(c, chunk, k, &b, h->rsvd.cols);
+    est_scratch(c, chunk, k, &b, h->rsvd.cols, ym);
     return std::max(need, c.off);
 }
 
@@ -413,9 +448,11 @@ mecuco_status run_curvature(mecuco_t h, char *ws, const void *X, mecuco_dtype dt
                             float *s_out, cudaStream_t s) {
     mecuco_status st = MECUCO_OK;
     const bool tc_moments = prec == MECUCO_PREC_BF16_MIXED;
-    if (!h->m3_items[k] || (tc_moments && !h->rowtab[k])) return MECUCO_ERR_INVALID_ARG;
+    const int64_t ym = rotated_m(h, m, prec);
+    if (!h->m3_items[k] || (tc_moments && !h->rowtab[k]) || (ym && (!h->tttab[k] || !h->gramtab[k][1])))
+        return MECUCO_ERR_INVALID_ARG;
     const int64_t nrows = re - rb;
-    const int64_t chunk = est_chunk(h, nrows, k);
+    const int64_t chunk = est_chunk(h, nrows, k, ym);
     const size_t idx_bytes = idx ? 0 : align_up((size_t)nrows * k * sizeof(int32_t), 256);
     const int32_t *nbr = idx;
     if (!idx) {
@@ -426,7 +463,7 @@ mecuco_status run_curvature(mecuco_t h, char *ws, const void *X, mecuco_dtype dt
     }
     Carver c(ws, idx_bytes);
     EstBufs b;
-    est_scratch(c, chunk, k, &b, h->rsvd.cols);
+    est_scratch(c, chunk, k, &b, h->rsvd.cols, ym);
     const int fp64 = h->jacobi_fp64 >= 0 ? h->jacobi_fp64 : (prec == MECUCO_PREC_BF16_MIXED ? 1 : 0);
     const float *Qarg = var == MECUCO_FAST_HAAR ? b.Q : nullptr;
     for (int64_t p0 = 0; p0 < nrows; p0 += chunk) {
@@ -439,7 +476,7 @@ mecuco_status run_curvature(mecuco_t h, char *ws, const void *X, mecuco_dtype dt
             const int l = h->rsvd.cols;
             if (tc_moments) {
                 LAUNCH(h, MECUCO_STAGE_MOMENTS, s,
-                       launch_moments_tc(X, dt, N, m, ld, nb, k, np, h->rowtab[k], b.M, b.G, b.R,
+                       launch_moments_tc(X, dt, N, m, ld, nb, k, np, h->rowtab[k], 0, b.M, b.G, b.R,
                                          var == MECUCO_FAST_HAAR ? b.Q : nullptr, h->tc_slots, h->wait_limit,
                                          h->ctr, s));
             } else {
@@ -461,19 +498,23 @@ mecuco_status run_curvature(mecuco_t h, char *ws, const void *X, mecuco_dtype dt
                                     lambda_out ? lambda_out + p0 * k : nullptr, s_out ? s_out + p0 * k : nullptr,
                                     h->ctr, s, b.G));
         } else if (tc_moments) {
-            // BF16-mixed: moments of X_c on the tensor cores, eigenpairs of its Gram
+            // BF16-mixed, in the rotated basis: G, R (Q) of X_c on the tensor cores,
+            // the eigenpairs of G, the rotated patch Y = U^T X_c, then every term of
+            // the estimator from the third moments of Y (no M is stored)
             float *Ud = U_out ? U_out + p0 * (int64_t)k * k : b.U;
-            LAUNCH(h, MECUCO_STAGE_MOMENTS, s,
-                   launch_moments_tc(X, dt, N, m, ld, nb, k, np, h->rowtab[k], b.M, b.G, b.R,
-                                     var == MECUCO_FAST_HAAR ? b.Q : nullptr, h->tc_slots, h->wait_limit, h->ctr,
-                                     s));
+            LAUNCH(h, MECUCO_STAGE_GRAM, s,
+                   launch_moments_tc(X, dt, N, m, ld, nb, k, np, h->gramtab[k][var == MECUCO_FAST_HAAR ? 1 : 0], 128,
+                                     nullptr, b.G, b.R, var == MECUCO_FAST_HAAR ? b.Q : nullptr, h->tc_slots,
+                                     h->wait_limit, h->ctr, s));
             LAUNCH(h, MECUCO_STAGE_JACOBI, s,
                    launch_jacobi(b.G, k, np, fp64, h->jacobi_max_sweeps, b.sig, Ud, h->ctr, s, kJacobiPreLoose));
             if (fp64 == 1 || fp64 == 3) ++h->launches;  // the refinement is a second kernel
-            LAUNCH(h, MECUCO_STAGE_ESTIMATOR, s,
-                   launch_estimator(b.sig, Ud, b.M, b.R, Qarg, k, m, np, (int)var, rank_eps_gram32(m), kappa_out + p0,
-                                    lambda_out ? lambda_out + p0 * k : nullptr, s_out ? s_out + p0 * k : nullptr,
-                                    h->ctr, s));
+            LAUNCH(h, MECUCO_STAGE_ROTATE, s,
+                   launch_rotate_tc(X, dt, N, m, ld, nb, k, np, Ud, b.Y, rot_ld(m), h->wait_limit, h->ctr, s));
+            LAUNCH(h, MECUCO_STAGE_MOMENTS, s,
+                   launch_tthird_tc(b.Y, rot_ld(m), k, m, np, h->tttab[k], b.sig, Ud, b.R, Qarg, (int)var,
+                                    rank_eps_gram32(m), kappa_out + p0, lambda_out ? lambda_out + p0 * k : nullptr,
+                                    s_out ? s_out + p0 * k : nullptr, h->tc_slots, h->wait_limit, h->ctr, s));
         } else {
             // plain FP32: moments of the rotated patch Z = U0^T X_c (U0 = refined
             // eigenvectors of the FP32 Gram; K is invariant under the rotation and the
@@ -537,7 +578,9 @@ mecuco_status run_batched_lanes(mecuco_t h, const mecuco_dataset *sets, int nset
     mecuco_status st;
     for (int i = 0; i < nsets; ++i) {
         if ((st = ensure_items(h, sets[i].k)) != MECUCO_OK) return st;
-        if (prec == MECUCO_PREC_BF16_MIXED && (st = ensure_pairs(h, sets[i].k)) != MECUCO_OK) return st;
+        if (prec == MECUCO_PREC_BF16_MIXED &&
+            ((st = ensure_pairs(h, sets[i].k)) != MECUCO_OK || (st = ensure_rotated(h, sets[i].k)) != MECUCO_OK))
+            return st;
     }
     lanes = std::max(1, std::min(lanes, std::min(nsets, 32)));
     // longest first onto the least-loaded lane (cost: kNN N^2 m + moments N k^2 m)
@@ -670,6 +713,9 @@ mecuco_status mecuco_destroy(mecuco_t h) {
     for (int kk = 0; kk <= 64; ++kk) {
         if (h->m3_items[kk]) cudaFree(h->m3_items[kk]);
         if (h->rowtab[kk]) cudaFree(h->rowtab[kk]);
+        if (h->tttab[kk]) cudaFree(h->tttab[kk]);
+        for (int w = 0; w < 2; ++w)
+            if (h->gramtab[kk][w]) cudaFree(h->gramtab[kk][w]);
     }
     if (h->bws) cudaFree(h->bws);
     for (int i = 0; i < 32; ++i) {
@@ -775,7 +821,9 @@ mecuco_status mecuco_curvature_range(mecuco_t h, const void *X, mecuco_dtype dt,
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = begin_call(h, s)) != MECUCO_OK) return st;
     if ((st = ensure_items(h, k)) != MECUCO_OK) return st;
-    if (prec == MECUCO_PREC_BF16_MIXED && (st = ensure_pairs(h, k)) != MECUCO_OK) return st;
+    if (prec == MECUCO_PREC_BF16_MIXED && ((st = ensure_pairs(h, k)) != MECUCO_OK ||
+                                           (st = ensure_rotated(h, k)) != MECUCO_OK))
+        return st;
     if ((st = ensure(h->ws, h->ws_bytes, curvature_bytes(h, X, dt, N, m, ld, k, idx != nullptr, re - rb, prec),
                      h->ws_cap)) != MECUCO_OK)
         return st;
@@ -805,7 +853,9 @@ mecuco_status mecuco_curvature_rsvd(mecuco_t h, const void *X, mecuco_dtype dt, 
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = begin_call(h, s)) != MECUCO_OK) return st;
     if ((st = ensure_items(h, k)) != MECUCO_OK) return st;
-    if (prec == MECUCO_PREC_BF16_MIXED && (st = ensure_pairs(h, k)) != MECUCO_OK) return st;
+    if (prec == MECUCO_PREC_BF16_MIXED && ((st = ensure_pairs(h, k)) != MECUCO_OK ||
+                                           (st = ensure_rotated(h, k)) != MECUCO_OK))
+        return st;
     h->rsvd.rank = rank;
     h->rsvd.cols = sketch_cols;
     h->rsvd.power = power_iters;
@@ -1066,7 +1116,9 @@ mecuco_status mecuco_curvature_host(mecuco_t h, const void *X_host, mecuco_dtype
     int32_t *id = c.take<int32_t>((size_t)N * k);
     CK(cudaMemcpyAsync(Xd, X_host, xbytes, cudaMemcpyHostToDevice, s));
     if ((st = ensure_items(h, k)) != MECUCO_OK) return st;
-    if (prec == MECUCO_PREC_BF16_MIXED && (st = ensure_pairs(h, k)) != MECUCO_OK) return st;
+    if (prec == MECUCO_PREC_BF16_MIXED && ((st = ensure_pairs(h, k)) != MECUCO_OK ||
+                                           (st = ensure_rotated(h, k)) != MECUCO_OK))
+        return st;
     const size_t need = std::max(knn_bytes(h, Xd, dt, N, m, ld, N, k, prec, 0),
                                  curvature_bytes(h, Xd, dt, N, m, ld, k, true, N, prec));
     if ((st = ensure(h->ws, h->ws_bytes, need, h->ws_cap)) != MECUCO_OK) return st;

@@ -43,6 +43,16 @@ struct JacobiEps<double> {
 
 constexpr int JT = 128;  // threads per patch
 
+// One rotation of a round's table, read by every walker as one 16-byte (FP32)
+// or 32-byte (FP64) shared load: the kernel is bound by shared-memory
+// wavefronts, and four separate table loads per rotation cost as many as its
+// data accesses.
+template <typename Real>
+struct alignas(2 * sizeof(Real) + 2 * sizeof(int) > 16 ? 32 : 16) JRot {
+    Real c, s;
+    int p, q;
+};
+
 template <typename Real>
 __global__ void __launch_bounds__(JT)
 jacobi_kernel(const float *__restrict__ G, int k, int64_t np, int max_sweeps, Real eps, float *__restrict__ sigma,
@@ -53,10 +63,9 @@ jacobi_kernel(const float *__restrict__ G, int k, int64_t np, int max_sweeps, Re
     const int ld = kp + 1;
     Real *A = reinterpret_cast<Real *>(jsm);
     Real *V = A + (size_t)kp * ld;
-    Real *tc = V + (size_t)kp * ld;  // [h] cosines
-    Real *ts = tc + h;               // [h] sines
-    int *tp = reinterpret_cast<int *>(ts + h);  // [h] p
-    int *tq = tp + h;                           // [h] q
+    // [h] rotations of the round, after A and V (rounded up to the entry alignment)
+    JRot<Real> *tab = reinterpret_cast<JRot<Real> *>(
+        (reinterpret_cast<uintptr_t>(V + (size_t)kp * ld) + alignof(JRot<Real>) - 1) & ~(uintptr_t)(alignof(JRot<Real>) - 1));
     __shared__ int s_rot;
     __shared__ int s_act;  // rotations in the current round (compacted table length)
 
@@ -93,7 +102,7 @@ jacobi_kernel(const float *__restrict__ G, int k, int64_t np, int max_sweeps, Re
                     const Real c = (Real)1 / sqrt((Real)1 + t * t);
                     // rotations of one round commute: keep only those that rotate, in any order
                     const int slot = atomicAdd(&s_act, 1);
-                    tc[slot] = c; ts[slot] = t * c; tp[slot] = p; tq[slot] = q;
+                    tab[slot] = JRot<Real>{c, t * c, p, q};
                 }
             }
             __syncthreads();
@@ -105,8 +114,9 @@ jacobi_kernel(const float *__restrict__ G, int k, int64_t np, int max_sweeps, Re
                 Real *row = A + line * ld;
 #pragma unroll 4
                 for (int i = i0; i < i1; ++i) {
-                    const int p = tp[i], q = tq[i];
-                    const Real c = tc[i], s = ts[i];
+                    const JRot<Real> rt = tab[i];
+                    const int p = rt.p, q = rt.q;
+                    const Real c = rt.c, s = rt.s;
                     const Real x = row[p], y = row[q];
                     row[p] = c * x - s * y;
                     row[q] = s * x + c * y;
@@ -118,8 +128,9 @@ jacobi_kernel(const float *__restrict__ G, int k, int64_t np, int max_sweeps, Re
                 Real *urow = V + line * ld;
 #pragma unroll 4
                 for (int i = i0; i < i1; ++i) {
-                    const int p = tp[i], q = tq[i];
-                    const Real c = tc[i], s = ts[i];
+                    const JRot<Real> rt = tab[i];
+                    const int p = rt.p, q = rt.q;
+                    const Real c = rt.c, s = rt.s;
                     const Real x = A[p * ld + line], y = A[q * ld + line];
                     A[p * ld + line] = c * x - s * y;
                     A[q * ld + line] = s * x + c * y;
@@ -130,8 +141,9 @@ jacobi_kernel(const float *__restrict__ G, int k, int64_t np, int max_sweeps, Re
             }
             __syncthreads();
             if (tid < nact) {
-                A[tp[tid] * ld + tq[tid]] = 0;
-                A[tq[tid] * ld + tp[tid]] = 0;
+                const JRot<Real> rt = tab[tid];
+                A[rt.p * ld + rt.q] = 0;
+                A[rt.q * ld + rt.p] = 0;
             }
             if (tid == 0) { s_rot += nact; s_act = 0; }
             __syncthreads();
@@ -350,7 +362,8 @@ size_t refine_ff_smem_bytes(int k) {
 size_t jacobi_smem_bytes(int k, int fp64) {
     const int kp = (k + 1) & ~1;
     const size_t real = fp64 ? sizeof(double) : sizeof(float);
-    return (size_t)2 * kp * (kp + 1) * real + (size_t)kp * real + (size_t)kp * sizeof(int);
+    const size_t ent = fp64 ? sizeof(JRot<double>) : sizeof(JRot<float>);
+    return (size_t)2 * kp * (kp + 1) * real + ent + (size_t)(kp / 2) * ent;
 }
 
 cudaError_t launch_jacobi(const float *G, int k, int64_t np, int fp64, int max_sweeps, float *sigma, float *U,

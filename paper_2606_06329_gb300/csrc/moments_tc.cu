@@ -47,6 +47,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "patch_gather.cuh"
 #include "tc_ptx.cuh"
 
 namespace mecuco {
@@ -63,82 +64,14 @@ constexpr int MT_XS_LD = 68;                           // FP32 staging row strid
 constexpr int MT_XP_LD = 36;                           // packed BF16x2 row stride (words)
 constexpr int MT_ROW_ONES = 64, MT_ROW_W = 65, MT_ROW_ZERO = 66, MT_XP_ROWS = 67;
 constexpr int MT_B_BYTES = 64 * 128;                   // B operand: up to 64 rows x 128 bytes
-constexpr int MT_MAX_ROWS = 2304;                      // row table bound (k = 64)
 constexpr long long MT_WAIT = 1000000000LL;
 
 enum : int { ROW_NONE = 0, ROW_PAIR = 1, ROW_G = 2, ROW_Q = 3 };
+using pg::load_halves;
+using pg::pack_bf16x2;
+using pg::sw128;
+using pg::Unit8;
 
-__device__ __forceinline__ uint32_t sw128(int row, int unit16) {
-    // byte offset of 16-byte unit `unit16` (0..7) of `row` in a 128B-swizzled K-major tile
-    return (uint32_t)(row * 128 + ((unit16 ^ (row & 7)) << 4));
-}
-
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
-    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t *>(&v);
-}
-
-// 32 bytes (lo, hi) of a lane at dst.  Eight lanes with consecutive 32-byte
-// destinations write the lower halves in one 128-bit store and the upper halves
-// in another; lanes 4..7 of each eight swap the two (swap = true), so that each
-// store covers all 32 banks instead of hitting 16 of them twice.
-__device__ __forceinline__ void store_halves(float *dst, float4 lo, float4 hi, bool swap) {
-    reinterpret_cast<float4 *>(dst)[swap ? 1 : 0] = swap ? hi : lo;
-    reinterpret_cast<float4 *>(dst)[swap ? 0 : 1] = swap ? lo : hi;
-}
-__device__ __forceinline__ void load_halves(const float *src, float4 &lo, float4 &hi, bool swap) {
-    const float4 first = reinterpret_cast<const float4 *>(src)[swap ? 1 : 0];
-    const float4 second = reinterpret_cast<const float4 *>(src)[swap ? 0 : 1];
-    lo = swap ? second : first;
-    hi = swap ? first : second;
-}
-
-// Raw gather of one 8-column unit of one row (zero past m).
-template <typename T>
-struct Unit8;
-template <>
-struct Unit8<__nv_bfloat16> {
-    uint4 v;
-    __device__ __forceinline__ void load(const __nv_bfloat16 *row, int64_t a, int64_t m, bool vec) {
-        if (vec && a + 8 <= m) {
-            v = __ldg(reinterpret_cast<const uint4 *>(row + a));
-        } else {
-            uint32_t h[8];
-            for (int e = 0; e < 8; ++e)
-                h[e] = (a + e < m) ? (uint32_t)__ldg(reinterpret_cast<const unsigned short *>(row) + a + e) : 0u;
-            v = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
-        }
-    }
-    __device__ __forceinline__ void zero() { v = make_uint4(0, 0, 0, 0); }
-    // swap: write the upper 16 bytes first (see store_halves)
-    __device__ __forceinline__ void store(float *dst, bool swap) const {
-        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-        float f[8];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            f[2 * e] = __uint_as_float(w[e] << 16);
-            f[2 * e + 1] = __uint_as_float(w[e] & 0xffff0000u);
-        }
-        store_halves(dst, make_float4(f[0], f[1], f[2], f[3]), make_float4(f[4], f[5], f[6], f[7]), swap);
-    }
-};
-template <>
-struct Unit8<float> {
-    float4 lo, hi;
-    __device__ __forceinline__ void load(const float *row, int64_t a, int64_t m, bool vec) {
-        if (vec && a + 8 <= m) {
-            lo = __ldg(reinterpret_cast<const float4 *>(row + a));
-            hi = __ldg(reinterpret_cast<const float4 *>(row + a) + 1);
-        } else {
-            float f[8];
-            for (int e = 0; e < 8; ++e) f[e] = (a + e < m) ? __ldg(row + a + e) : 0.f;
-            lo = make_float4(f[0], f[1], f[2], f[3]);
-            hi = make_float4(f[4], f[5], f[6], f[7]);
-        }
-    }
-    __device__ __forceinline__ void zero() { lo = hi = make_float4(0.f, 0.f, 0.f, 0.f); }
-    __device__ __forceinline__ void store(float *dst, bool swap) const { store_halves(dst, lo, hi, swap); }
-};
 }  // namespace
 
 __host__ __device__ inline int moments_tc_n(int k) { return k <= 16 ? 16 : ((k + 15) / 16) * 16; }
@@ -172,6 +105,15 @@ void moments_tc_build_rows(int k, int32_t *codes) {
             while (((codes[next] >> 16) & 3) != ROW_NONE) ++next;
             codes[next] = which == 0 ? code(a, MT_ROW_ONES, ROW_G) : code(a, MT_ROW_W, ROW_Q);
         }
+}
+
+void moments_tc_build_gram_rows(int k, int with_q, int32_t *codes) {
+    auto code = [](int a, int b, int kind) { return (int32_t)(a | (b << 8) | (kind << 16)); };
+    for (int n = 0; n < 128; ++n) codes[n] = code(MT_ROW_ZERO, MT_ROW_ZERO, ROW_NONE);
+    for (int a = 0; a < k; ++a) {
+        codes[a] = code(a, MT_ROW_ONES, ROW_G);
+        if (with_q) codes[64 + a] = code(a, MT_ROW_W, ROW_Q);
+    }
 }
 
 size_t moments_tc_smem_bytes(int k) {
@@ -513,16 +455,16 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
 }
 
 cudaError_t launch_moments_tc(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, const int32_t *idx,
-                              int k, int64_t np, const int32_t *rowtab, float *M, float *G, float *R, float *Q,
-                              int nslots, long long wait_limit, DevCounters *ctr, cudaStream_t s) {
+                              int k, int64_t np, const int32_t *rowtab, int nrows, float *M, float *G, float *R,
+                              float *Q, int nslots, long long wait_limit, DevCounters *ctr, cudaStream_t s) {
     if (np <= 0) return cudaSuccess;
     if (wait_limit <= 0) wait_limit = MT_WAIT;
     if (k > 64 || k < 2) return cudaErrorInvalidValue;
     if (nslots < MT_GROUP || nslots > MT_MAX_SLOTS || nslots % MT_GROUP != 0 ||
         (512 - nslots * MT_SLOT_COLS) < moments_tc_n(k))
         return cudaErrorInvalidValue;
-    const int nrows = moments_tc_rows(k);
-    if (nrows > MT_MAX_ROWS) return cudaErrorInvalidValue;
+    if (nrows <= 0) nrows = moments_tc_rows(k);
+    if (nrows > moments_tc_rows(k) || nrows % 128 != 0) return cudaErrorInvalidValue;
     const size_t smem = moments_tc_smem_bytes(k);
     cudaError_t e;
     if (dt == MECUCO_BF16) {

@@ -1,0 +1,276 @@
+// rotate_tc.cu - the rotated patch of the BF16-mixed estimator: for every
+// patch, Y = U^T X_c (k x m), U the k x k eigenvector matrix of the patch Gram
+// G = X_c X_c^T (eq. svd_cov; Alg. 1 SVD_p).  Row l of Y is s_l v_l^T: the
+// l-th right singular vector scaled by its singular value, so the tangent
+// basis V_r = X_c^T U_p S^-1 of Alg. 1 is Y's first p rows divided by s_l, and
+// X_c = U Y exactly for the full orthogonal U.  The third-moment pass of the
+// Fast estimator works on Y (tthird_tc.cu).
+//
+// One CTA per patch.  8 producer warps gather the k neighbour rows of each
+// 64-column chunk, centre every column in FP32 (the same arithmetic, in the
+// same order, as the Gram pass of moments_tc.cu, so both see identical BF16
+// values) and write the chunk transposed, X_c^T (64 columns x 64 rows, BF16,
+// K-major with the 128-byte swizzle), as the B operand.  One MMA thread
+// computes D = [U_hi^T | U_lo^T] [X_c^T | X_c^T]^T on the tensor cores: U is
+// split into two BF16 terms (U_hi = bf16(U), U_lo = bf16(U - U_hi), together
+// U to ~2^-17 relative) placed side by side along K, so one FP32 accumulator
+// sums both products; BF16 x BF16 products are exact in FP32.  Rows 64..127 of
+// the MMA's A operand are zero.  Four producer warps drain the accumulator
+// (TMEM lanes 0..63 = rows l of Y), round to BF16 and store the chunk of Y.
+// Accumulators and B operands are double-buffered; every wait is bounded
+// (MECUCO_ERR_TIMEOUT, no trap) and the MMA thread waits for its last MMAs
+// before tensor memory is freed.
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "patch_gather.cuh"
+#include "tc_ptx.cuh"
+
+namespace mecuco {
+
+namespace {
+constexpr int RT_PRODUCER_WARPS = 8;
+constexpr int RT_THREADS = (RT_PRODUCER_WARPS + 1) * 32;  // + the MMA warp
+constexpr int RT_CH = 64;                                  // columns per chunk
+constexpr int RT_XS_LD = 68;                               // FP32 staging row stride (floats)
+constexpr int RT_A_TILE = 128 * 128;                       // one A tile: 128 rows x 64 K (BF16), 16 KB
+constexpr int RT_B_BYTES = 64 * 128;                       // X_c^T chunk: 64 rows x 64 K (BF16), 8 KB
+constexpr long long RT_WAIT = 1000000000LL;
+using pg::load_halves;
+using pg::pack_bf16x2;
+using pg::sw128;
+using pg::Unit8;
+}  // namespace
+
+size_t rotate_tc_smem_bytes() {
+    return 1024 + 2 * (size_t)RT_A_TILE + 2 * (size_t)RT_B_BYTES + 64 * (size_t)RT_XS_LD * 4 + 4 * 64 * 4;
+}
+
+// two CTAs per SM (113 registers a thread): the gather needs warps in flight
+template <typename T>
+__global__ void __launch_bounds__(RT_THREADS, 2)
+rotate_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, const int32_t *__restrict__ idx, int k,
+                 const float *__restrict__ U, __nv_bfloat16 *__restrict__ Y, int64_t ldy, long long wait_limit,
+                 DevCounters *ctr) {
+    extern __shared__ __align__(1024) uint8_t rsm_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(rsm_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *Aop = base;                                             // 2 A tiles (U_hi^T, U_lo^T)
+    uint8_t *Bop0 = base + 2 * RT_A_TILE;                            // 2 x B operand
+    float *Xs = reinterpret_cast<float *>(Bop0 + 2 * RT_B_BYTES);    // [64][68] FP32 staging
+    float *Part = Xs + 64 * RT_XS_LD;                                // [4][64] column partials
+    __shared__ uint64_t b_full[2], b_empty[2], d_full[2], d_empty[2], mma_fin;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int rows[64];
+    __shared__ int abort_flag, never;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t pt = blockIdx.x;
+    const int nchunks = (int)((m + RT_CH - 1) / RT_CH);
+    const uint32_t idesc = tc::idesc_bf16_f32(128, 64);
+    const bool vec = (ld % 8 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+
+    if (tid < 64) {
+        int r = 0;
+        if (tid < k) {
+            r = idx[pt * k + tid];
+            if (r < 0 || (int64_t)r >= N) { atomicOr(&ctr->status, (unsigned)DEV_INVALID); r = 0; }
+        }
+        rows[tid] = r;
+    }
+    // U (row j, column l) staged as Xs[j][l], zero outside k x k
+    const float *u = U + pt * (int64_t)k * k;
+    for (int e = tid; e < 64 * 64; e += RT_THREADS) {
+        const int j = e >> 6, l = e & 63;
+        Xs[j * RT_XS_LD + l] = (j < k && l < k) ? u[j * k + l] : 0.f;
+    }
+    if (tid == 0) {
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(tc::smem_u32(&b_full[b]), 1);
+            tc::mbar_init(tc::smem_u32(&b_empty[b]), 1);
+            tc::mbar_init(tc::smem_u32(&d_full[b]), 1);
+            tc::mbar_init(tc::smem_u32(&d_empty[b]), 4);  // the four drain warps
+        }
+        tc::mbar_init(tc::smem_u32(&mma_fin), 1);
+        abort_flag = (*(volatile unsigned *)&ctr->status & DEV_TIMEOUT) ? 1 : 0;
+        never = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tc::smem_u32(&tmem_slot), 128);  // two 64-column accumulators
+        tc::tmem_relinquish();
+    }
+    __syncthreads();
+    // A operand: row l holds U[:, l] (the l-th column of U) split in two BF16
+    // terms, the high term in tile 0 and the low term in tile 1 (K = j); rows
+    // 64..127 are zero.  Thread (l, unit pair) reads a column of the staged U.
+    for (int e = tid; e < 128 * 8; e += RT_THREADS) {
+        const int l = e & 127, un = e >> 7;  // row, 16-byte unit (8 values of j)
+        uint32_t hw[4] = {0u, 0u, 0u, 0u}, lw[4] = {0u, 0u, 0u, 0u};
+        if (l < 64) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float u0 = Xs[(8 * un + 2 * q) * RT_XS_LD + l], u1 = Xs[(8 * un + 2 * q + 1) * RT_XS_LD + l];
+                const __nv_bfloat16 h0 = __float2bfloat16_rn(u0), h1 = __float2bfloat16_rn(u1);
+                hw[q] = pack_bf16x2(__bfloat162float(h0), __bfloat162float(h1));
+                lw[q] = pack_bf16x2(u0 - __bfloat162float(h0), u1 - __bfloat162float(h1));
+            }
+        }
+        *reinterpret_cast<uint4 *>(Aop + sw128(l, un)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4 *>(Aop + RT_A_TILE + sw128(l, un)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = tmem_slot;
+    volatile int *abortp = &abort_flag;
+    auto fail = [&]() {
+        atomicOr(&ctr->status, (unsigned)DEV_TIMEOUT);
+        abort_flag = 1;
+    };
+    auto wait = [&](uint64_t *bar, uint32_t parity) {
+        if (!*abortp && !tc::mbar_wait(tc::smem_u32(bar), parity, abortp, wait_limit)) fail();
+    };
+
+    if (warp < RT_PRODUCER_WARPS) {
+        // ============ producers: gather, centre, transposed pack; drain ============
+        const int ptid = tid;                                  // 0 .. 255
+        const int gr0 = ptid >> 3, gg = ptid & 7;              // gather units (row gr0 / gr0 + 32, group gg)
+        const T *grow0 = X + (int64_t)rows[gr0] * ld;
+        const T *grow1 = X + (int64_t)rows[gr0 + 32] * ld;
+        const bool live0 = gr0 < k, live1 = gr0 + 32 < k;
+        const int cc = ptid & 63, rg = ptid >> 6;              // centring: column cc, rows 16 rg .. 16 rg + 15
+        const float inv_k = 1.f / (float)k;
+        // transposed pack: column ta = ptid & 63, 16-byte units tu, tu + 1 (rows 8 tu ..)
+        const int ta = ptid & 63, tu = (ptid >> 6) * 2;
+        // drain: warps with lane quarter 0 or 1 (TMEM lanes = rows l 0..63), column half dh
+        const bool drainer = (warp & 3) < 2;
+        const int dq = warp & 3, dh = warp >> 2;
+        __nv_bfloat16 *yrow = Y + ((int64_t)pt * 64 + dq * 32 + lane) * ldy;
+        Unit8<T> pre0, pre1;
+        if (live0) pre0.load(grow0, gg * 8, m, vec); else pre0.zero();
+        if (live1) pre1.load(grow1, gg * 8, m, vec); else pre1.zero();
+        auto drain = [&](int c) {  // chunk c of Y, from accumulator c & 1
+            const int b = c & 1;
+            if (lane == 0) wait(&d_full[b], (uint32_t)(c >> 1) & 1u);
+            __syncwarp();
+            tc::fence_after();
+            uint32_t r32[32];
+            tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(dq * 32) << 16) + (uint32_t)(b * 64 + dh * 32), r32);
+            tc::tmem_ld_wait();
+            uint32_t pk[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) pk[e] = pack_bf16x2(__uint_as_float(r32[2 * e]), __uint_as_float(r32[2 * e + 1]));
+            uint4 *dst = reinterpret_cast<uint4 *>(yrow + (int64_t)c * RT_CH + dh * 32);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) dst[e] = make_uint4(pk[4 * e], pk[4 * e + 1], pk[4 * e + 2], pk[4 * e + 3]);
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(tc::smem_u32(&d_empty[b]));
+        };
+        for (int ci = 0; ci < nchunks; ++ci) {
+            const int b = ci & 1;
+            pre0.store(Xs + gr0 * RT_XS_LD + gg * 8, gg >= 4);
+            pre1.store(Xs + (gr0 + 32) * RT_XS_LD + gg * 8, gg >= 4);
+            if (ci + 1 < nchunks) {
+                const int64_t an = (int64_t)(ci + 1) * RT_CH + gg * 8;
+                if (live0) pre0.load(grow0, an, m, vec); else pre0.zero();
+                if (live1) pre1.load(grow1, an, m, vec); else pre1.zero();
+            }
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            float v[16], sum = 0.f;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                v[e] = Xs[(rg * 16 + e) * RT_XS_LD + cc];
+                sum += v[e];
+            }
+            Part[rg * 64 + cc] = sum;
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            const float mean = (Part[cc] + Part[64 + cc] + Part[128 + cc] + Part[192 + cc]) * inv_k;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const float x = (rg * 16 + e < k) ? v[e] - mean : 0.f;
+                Xs[(rg * 16 + e) * RT_XS_LD + cc] = x;
+            }
+            // buffer b is free once the MMAs of chunk ci - 2 are done with it
+            if (ptid == 0 && ci >= 2) wait(&b_empty[b], (uint32_t)((ci >> 1) - 1) & 1u);
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            uint8_t *Bop = Bop0 + b * RT_B_BYTES;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int un = tu + h;
+                uint32_t w4[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    w4[q] = pack_bf16x2(Xs[(8 * un + 2 * q) * RT_XS_LD + ta], Xs[(8 * un + 2 * q + 1) * RT_XS_LD + ta]);
+                *reinterpret_cast<uint4 *>(Bop + sw128(ta, un)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            if (ptid == 0) tc::mbar_arrive(tc::smem_u32(&b_full[b]));
+            // the previous chunk's accumulator, while the MMAs of this one run
+            if (drainer && ci >= 1) drain(ci - 1);
+        }
+        if (drainer) drain(nchunks - 1);
+    } else if (lane == 0) {
+        // ================= MMA thread =================
+        const uint64_t a0 = tc::sdesc_sw128(tc::smem_u32(Aop)), a1 = tc::sdesc_sw128(tc::smem_u32(Aop + RT_A_TILE));
+        bool ok = true;
+        for (int ci = 0; ci < nchunks && ok; ++ci) {
+            const int b = ci & 1;
+            if (!tc::mbar_wait(tc::smem_u32(&b_full[b]), (uint32_t)(ci >> 1) & 1u, abortp, wait_limit) ||
+                (ci >= 2 &&
+                 !tc::mbar_wait(tc::smem_u32(&d_empty[b]), (uint32_t)((ci >> 1) - 1) & 1u, abortp, wait_limit))) {
+                fail();
+                ok = false;
+                break;
+            }
+            tc::fence_after();
+            const uint64_t bd = tc::sdesc_sw128(tc::smem_u32(Bop0 + b * RT_B_BYTES));
+            const uint32_t d = tmem + (uint32_t)(b * 64);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) tc::mma_f16(d, a0 + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, kk != 0);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) tc::mma_f16(d, a1 + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, 1u);
+            tc::commit(tc::smem_u32(&b_empty[b]));
+            tc::commit(tc::smem_u32(&d_full[b]));
+        }
+        // every MMA has completed before TMEM is freed (a barrier used once)
+        tc::commit(tc::smem_u32(&mma_fin));
+        if (!tc::mbar_wait(tc::smem_u32(&mma_fin), 0u, &never, RT_WAIT)) fail();
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after();
+        tc::tmem_dealloc(tmem, 128);
+    }
+}
+
+cudaError_t launch_rotate_tc(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, const int32_t *idx,
+                             int k, int64_t np, const float *U, void *Y, int64_t ldy, long long wait_limit,
+                             DevCounters *ctr, cudaStream_t s) {
+    if (np <= 0) return cudaSuccess;
+    if (k > 64 || k < 2 || ldy < (m + RT_CH - 1) / RT_CH * RT_CH || (ldy % 8) != 0 ||
+        (reinterpret_cast<uintptr_t>(Y) & 15))
+        return cudaErrorInvalidValue;
+    if (wait_limit <= 0) wait_limit = RT_WAIT;
+    const size_t smem = rotate_tc_smem_bytes();
+    cudaError_t e;
+    if (dt == MECUCO_BF16) {
+        e = cudaFuncSetAttribute(rotate_tc_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        rotate_tc_kernel<<<(unsigned)np, RT_THREADS, smem, s>>>((const __nv_bfloat16 *)X, N, m, ld, idx, k, U,
+                                                               (__nv_bfloat16 *)Y, ldy, wait_limit, ctr);
+    } else {
+        e = cudaFuncSetAttribute(rotate_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        rotate_tc_kernel<<<(unsigned)np, RT_THREADS, smem, s>>>((const float *)X, N, m, ld, idx, k, U,
+                                                               (__nv_bfloat16 *)Y, ldy, wait_limit, ctr);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace mecuco
