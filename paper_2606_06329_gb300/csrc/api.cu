@@ -63,7 +63,6 @@ struct mecuco_ctx {
     DevCounters *ctr = nullptr;
     int32_t *m3_items[65] = {};  // per k: work items of the CUDA-core third-moment kernel
     int32_t *rowtab[65] = {};    // per k: row codes of the tensor-core moment kernel
-    int32_t *gramtab[65][2] = {};// per k, without / with the Q rows: row codes of the Gram pass
     int32_t *tttab[65] = {};     // per k: row codes of the third-moment pass (pairs only)
     int knn_splits = 0;
     int knn_pair = -1;  // -1: CTA pairs for N >= KNN_PAIR_MIN_N
@@ -353,16 +352,10 @@ mecuco_status ensure_pairs(mecuco_t h, int k) {
     return upload_table(&h->rowtab[k], host);
 }
 
-// Tables of the BF16-mixed estimator in the rotated basis: the Gram pass's G
-// (and Q) rows and the third-moment pass's pair rows.
+// Table of the BF16-mixed estimator in the rotated basis: the third-moment
+// pass's pair rows.
 mecuco_status ensure_rotated(mecuco_t h, int k) {
     mecuco_status st;
-    for (int w = 0; w < 2; ++w) {
-        if (h->gramtab[k][w]) continue;
-        std::vector<int32_t> host(128);
-        moments_tc_build_gram_rows(k, w, host.data());
-        if ((st = upload_table(&h->gramtab[k][w], host)) != MECUCO_OK) return st;
-    }
     if (!h->tttab[k]) {
         std::vector<int32_t> host((size_t)tthird_rows(k));
         tthird_build_rows(k, host.data());
@@ -449,7 +442,7 @@ mecuco_status run_curvature(mecuco_t h, char *ws, const void *X, mecuco_dtype dt
     mecuco_status st = MECUCO_OK;
     const bool tc_moments = prec == MECUCO_PREC_BF16_MIXED;
     const int64_t ym = rotated_m(h, m, prec);
-    if (!h->m3_items[k] || (tc_moments && !h->rowtab[k]) || (ym && (!h->tttab[k] || !h->gramtab[k][1])))
+    if (!h->m3_items[k] || (tc_moments && !h->rowtab[k]) || (ym && !h->tttab[k]))
         return MECUCO_ERR_INVALID_ARG;
     const int64_t nrows = re - rb;
     const int64_t chunk = est_chunk(h, nrows, k, ym);
@@ -476,7 +469,7 @@ mecuco_status run_curvature(mecuco_t h, char *ws, const void *X, mecuco_dtype dt
             const int l = h->rsvd.cols;
             if (tc_moments) {
                 LAUNCH(h, MECUCO_STAGE_MOMENTS, s,
-                       launch_moments_tc(X, dt, N, m, ld, nb, k, np, h->rowtab[k], 0, b.M, b.G, b.R,
+                       launch_moments_tc(X, dt, N, m, ld, nb, k, np, h->rowtab[k], b.M, b.G, b.R,
                                          var == MECUCO_FAST_HAAR ? b.Q : nullptr, h->tc_slots, h->wait_limit,
                                          h->ctr, s));
             } else {
@@ -503,9 +496,8 @@ mecuco_status run_curvature(mecuco_t h, char *ws, const void *X, mecuco_dtype dt
             // the estimator from the third moments of Y (no M is stored)
             float *Ud = U_out ? U_out + p0 * (int64_t)k * k : b.U;
             LAUNCH(h, MECUCO_STAGE_GRAM, s,
-                   launch_moments_tc(X, dt, N, m, ld, nb, k, np, h->gramtab[k][var == MECUCO_FAST_HAAR ? 1 : 0], 128,
-                                     nullptr, b.G, b.R, var == MECUCO_FAST_HAAR ? b.Q : nullptr, h->tc_slots,
-                                     h->wait_limit, h->ctr, s));
+                   launch_gram_tc(X, dt, N, m, ld, nb, k, np, b.G, b.R, var == MECUCO_FAST_HAAR ? b.Q : nullptr,
+                                  h->wait_limit, h->ctr, s));
             LAUNCH(h, MECUCO_STAGE_JACOBI, s,
                    launch_jacobi(b.G, k, np, fp64, h->jacobi_max_sweeps, b.sig, Ud, h->ctr, s, kJacobiPreLoose));
             if (fp64 == 1 || fp64 == 3) ++h->launches;  // the refinement is a second kernel
@@ -714,8 +706,6 @@ mecuco_status mecuco_destroy(mecuco_t h) {
         if (h->m3_items[kk]) cudaFree(h->m3_items[kk]);
         if (h->rowtab[kk]) cudaFree(h->rowtab[kk]);
         if (h->tttab[kk]) cudaFree(h->tttab[kk]);
-        for (int w = 0; w < 2; ++w)
-            if (h->gramtab[kk][w]) cudaFree(h->gramtab[kk][w]);
     }
     if (h->bws) cudaFree(h->bws);
     for (int i = 0; i < 32; ++i) {

@@ -34,6 +34,9 @@ __device__ __forceinline__ float load_elem(const __nv_bfloat16 *p) {
     return __bfloat162float(__ldg(reinterpret_cast<const __nv_bfloat16 *>(p)));
 }
 
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+
 // --- error-free transformations (Knuth TwoSum, FMA-based TwoProd) ----------
 // A value is carried as an unevaluated sum hi + lo with |lo| <= ulp(hi)/2.
 struct ff {

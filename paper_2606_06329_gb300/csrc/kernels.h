@@ -96,24 +96,25 @@ void m3_build_items(int k, int32_t *items /* m3_items(k) */);
 // BF16-mixed form: G, R, Q and the pair-major M of each patch from
 // tensor-core GEMMs over 128-row tiles of row products (BF16 operands, FP32
 // accumulation), nslots TMEM slots for the A operand; wait_limit as for
-// launch_knn_tc.  rowtab holds nrows row codes (moments_tc_build_rows:
-// nrows = moments_tc_rows(k); moments_tc_build_gram_rows: 128); idx points at
-// the chunk's first neighbour row; Q may be NULL.
+// launch_knn_tc.  rowtab holds moments_tc_rows(k) row codes built by
+// moments_tc_build_rows; idx points at the chunk's first neighbour row; Q may
+// be NULL.
 cudaError_t launch_moments_tc(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, const int32_t *idx,
-                              int k, int64_t np, const int32_t *rowtab, int nrows, float *M, float *G, float *R,
-                              float *Q, int nslots, long long wait_limit, DevCounters *ctr, cudaStream_t s);
+                              int k, int64_t np, const int32_t *rowtab, float *M, float *G, float *R, float *Q,
+                              int nslots, long long wait_limit, DevCounters *ctr, cudaStream_t s);
 int moments_tc_rows(int k);
 void moments_tc_build_rows(int k, int32_t *codes /* moments_tc_rows(k) */);
 size_t moments_tc_smem_bytes(int k);
-// Row table of the Gram pass: the G rows (and with with_q the Q rows) only, one
-// 128-row tile; M is not written.  Launch with nrows = 128.
-void moments_tc_build_gram_rows(int k, int with_q, int32_t *codes /* 128 */);
-
-// BF16-mixed estimator in the rotated basis.  launch_rotate_tc: Y = U^T X_c
+// BF16-mixed estimator in the rotated basis.  launch_gram_tc: G, R and (Q not
+// NULL) Q of each patch, as launch_patch_gram's outputs, from BF16 operands on
+// the tensor cores.  launch_rotate_tc: Y = U^T X_c
 // per point (U from launch_jacobi, k x k), BF16, point p's row l at
 // Y + (p * 64 + l) * ldy (rows k..63 zero), ldy >= m rounded up to 64, ldy % 8 == 0.
 // launch_tthird_tc: the Fast estimator from Y, sigma, U, R and Q (Haar) -
 // kappa, and lambda_out / s_out when not NULL; rowtab from tthird_build_rows.
+cudaError_t launch_gram_tc(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, const int32_t *idx,
+                           int k, int64_t np, float *G, float *R, float *Q, long long wait_limit, DevCounters *ctr,
+                           cudaStream_t s);
 cudaError_t launch_rotate_tc(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, const int32_t *idx,
                              int k, int64_t np, const float *U, void *Y, int64_t ldy, long long wait_limit,
                              DevCounters *ctr, cudaStream_t s);

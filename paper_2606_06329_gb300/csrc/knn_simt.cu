@@ -228,16 +228,15 @@ knn_rerank_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld,
 
     float err_max = -INFINITY, err_min = INFINITY, nmax = 0.f;
     bool bad = false;
-    for (int c = 0; c < L; ++c) {
+    // a complete search leaves -1 or a row of X in every slot; anything else
+    // (slots a search that timed out never wrote) is skipped, never read
+    auto cand = [&](int c) {
         int j = cidx[c];
-        // a complete search leaves -1 or a row of X in every slot; anything else
-        // (slots a search that timed out never wrote) is skipped, never read
         if (j >= N) { bad = true; j = -1; }
-        ff acc{0.f, 0.f};
+        return j;
+    };
+    auto record = [&](int c, int j, ff acc) {
         if (j >= 0) {
-            const T *xj = X + (int64_t)j * ld;
-            for (int64_t a = lane; a < m; a += 32) ff_acc_sqdiff(acc, load_elem(xq + a), load_elem(xj + a));
-            acc = ff_warp_sum(acc);
             const float e = cd[c] - acc.hi;  // overestimate of the search's distance
             err_max = fmaxf(err_max, e);
             err_min = fminf(err_min, e);
@@ -246,6 +245,55 @@ knn_rerank_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld,
             acc.hi = INFINITY;
         }
         if (lane == 0) { hi[c] = acc.hi; lo[c] = acc.lo; ci[c] = j; }
+    };
+    // Rows as 16-byte vectors when every row starts 16-byte aligned: four
+    // candidates at a time, each lane summing its share of the four rows with
+    // independent compensated accumulators, so that 4 x (m / 32 / VEC) loads
+    // are in flight per lane instead of one 2- or 4-byte load per step.  The
+    // terms are the same; only the summation order differs from the scalar form.
+    constexpr int VEC = 16 / (int)sizeof(T);
+    const bool vec = (ld % VEC == 0) && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+    int c = 0;
+    if (vec) {
+        const int64_t mv = m / VEC * VEC;  // vector part of the row; the tail is scalar
+        for (; c + 4 <= L; c += 4) {
+            int j[4];
+            const T *xr[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                j[u] = cand(c + u);
+                xr[u] = X + (int64_t)(j[u] >= 0 ? j[u] : q) * ld;  // an empty slot reads the query row, discarded
+            }
+            ff acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+            for (int64_t a = (int64_t)lane * VEC; a < mv; a += 32 * VEC) {
+                const uint4 qv = __ldg(reinterpret_cast<const uint4 *>(xq + a));
+                uint4 yv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) yv[u] = __ldg(reinterpret_cast<const uint4 *>(xr[u] + a));
+                const T *qe = reinterpret_cast<const T *>(&qv);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const T *ye = reinterpret_cast<const T *>(&yv[u]);
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) ff_acc_sqdiff(acc[u], to_f32(qe[e]), to_f32(ye[e]));
+                }
+            }
+            for (int64_t a = mv + lane; a < m; a += 32)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) ff_acc_sqdiff(acc[u], load_elem(xq + a), load_elem(xr[u] + a));
+#pragma unroll
+            for (int u = 0; u < 4; ++u) record(c + u, j[u], ff_warp_sum(acc[u]));
+        }
+    }
+    for (; c < L; ++c) {
+        const int j = cand(c);
+        ff acc{0.f, 0.f};
+        if (j >= 0) {
+            const T *xj = X + (int64_t)j * ld;
+            for (int64_t a = lane; a < m; a += 32) ff_acc_sqdiff(acc, load_elem(xq + a), load_elem(xj + a));
+            acc = ff_warp_sum(acc);
+        }
+        record(c, j, acc);
     }
     __syncwarp();
     // thresholds: a split whose list is full admitted only d~ < its max

@@ -107,15 +107,6 @@ void moments_tc_build_rows(int k, int32_t *codes) {
         }
 }
 
-void moments_tc_build_gram_rows(int k, int with_q, int32_t *codes) {
-    auto code = [](int a, int b, int kind) { return (int32_t)(a | (b << 8) | (kind << 16)); };
-    for (int n = 0; n < 128; ++n) codes[n] = code(MT_ROW_ZERO, MT_ROW_ZERO, ROW_NONE);
-    for (int a = 0; a < k; ++a) {
-        codes[a] = code(a, MT_ROW_ONES, ROW_G);
-        if (with_q) codes[64 + a] = code(a, MT_ROW_W, ROW_Q);
-    }
-}
-
 size_t moments_tc_smem_bytes(int k) {
     return 1024 + 2 * (size_t)MT_B_BYTES + 2 * (size_t)MT_XP_ROWS * MT_XP_LD * 4 + 64 * (size_t)MT_XS_LD * 4 +
            4 * 64 * 4 + (size_t)moments_tc_rows(k) * 4;
@@ -455,16 +446,15 @@ moments_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, con
 }
 
 cudaError_t launch_moments_tc(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, const int32_t *idx,
-                              int k, int64_t np, const int32_t *rowtab, int nrows, float *M, float *G, float *R,
-                              float *Q, int nslots, long long wait_limit, DevCounters *ctr, cudaStream_t s) {
+                              int k, int64_t np, const int32_t *rowtab, float *M, float *G, float *R, float *Q,
+                              int nslots, long long wait_limit, DevCounters *ctr, cudaStream_t s) {
     if (np <= 0) return cudaSuccess;
     if (wait_limit <= 0) wait_limit = MT_WAIT;
     if (k > 64 || k < 2) return cudaErrorInvalidValue;
     if (nslots < MT_GROUP || nslots > MT_MAX_SLOTS || nslots % MT_GROUP != 0 ||
         (512 - nslots * MT_SLOT_COLS) < moments_tc_n(k))
         return cudaErrorInvalidValue;
-    if (nrows <= 0) nrows = moments_tc_rows(k);
-    if (nrows > moments_tc_rows(k) || nrows % 128 != 0) return cudaErrorInvalidValue;
+    const int nrows = moments_tc_rows(k);
     const size_t smem = moments_tc_smem_bytes(k);
     cudaError_t e;
     if (dt == MECUCO_BF16) {

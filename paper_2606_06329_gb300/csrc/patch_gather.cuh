@@ -81,5 +81,32 @@ struct Unit8<float> {
     __device__ __forceinline__ void zero() { lo = hi = make_float4(0.f, 0.f, 0.f, 0.f); }
     __device__ __forceinline__ void store(float *dst, bool swap) const { store_halves(dst, lo, hi, swap); }
 };
+// Centre the staged chunk Xs (64 rows of row stride LD, rows past k zero) in
+// place: thread (column cc, rows 16 rg .. 16 rg + 15) sums its 16 values,
+// the four partial sums of a column (Part[rg * 64 + cc]) give its mean over the
+// k rows, and x = v - mean (0 past k) goes to x[] and back to Xs.  Called by
+// the 256 threads of named barrier 1 right after the chunk was staged; the
+// same operations in the same order wherever the patch is centred, so every
+// pass sees the same values.
+template <int LD>
+__device__ __forceinline__ void centre_chunk(float *Xs, float *Part, int cc, int rg, int k, float inv_k,
+                                             float (&x)[16]) {
+    asm volatile("bar.sync 1, 256;" ::: "memory");
+    float v[16], sum = 0.f;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        v[e] = Xs[(rg * 16 + e) * LD + cc];
+        sum += v[e];
+    }
+    Part[rg * 64 + cc] = sum;
+    asm volatile("bar.sync 1, 256;" ::: "memory");
+    const float mean = (Part[cc] + Part[64 + cc] + Part[128 + cc] + Part[192 + cc]) * inv_k;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        x[e] = (rg * 16 + e < k) ? v[e] - mean : 0.f;
+        Xs[(rg * 16 + e) * LD + cc] = x[e];
+    }
+}
+
 }  // namespace pg
 }  // namespace mecuco

@@ -7,9 +7,8 @@
 // Fast estimator works on Y (tthird_tc.cu).
 //
 // One CTA per patch.  8 producer warps gather the k neighbour rows of each
-// 64-column chunk, centre every column in FP32 (the same arithmetic, in the
-// same order, as the Gram pass of moments_tc.cu, so both see identical BF16
-// values) and write the chunk transposed, X_c^T (64 columns x 64 rows, BF16,
+// 64-column chunk, centre every column in FP32 (pg::centre_chunk, as the
+// Gram pass does, so both see identical BF16 values) and write the chunk transposed, X_c^T (64 columns x 64 rows, BF16,
 // K-major with the 128-byte swizzle), as the B operand.  One MMA thread
 // computes D = [U_hi^T | U_lo^T] [X_c^T | X_c^T]^T on the tensor cores: U is
 // split into two BF16 terms (U_hi = bf16(U), U_lo = bf16(U - U_hi), together
@@ -178,21 +177,8 @@ rotate_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, cons
                 if (live0) pre0.load(grow0, an, m, vec); else pre0.zero();
                 if (live1) pre1.load(grow1, an, m, vec); else pre1.zero();
             }
-            asm volatile("bar.sync 1, 256;" ::: "memory");
-            float v[16], sum = 0.f;
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                v[e] = Xs[(rg * 16 + e) * RT_XS_LD + cc];
-                sum += v[e];
-            }
-            Part[rg * 64 + cc] = sum;
-            asm volatile("bar.sync 1, 256;" ::: "memory");
-            const float mean = (Part[cc] + Part[64 + cc] + Part[128 + cc] + Part[192 + cc]) * inv_k;
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const float x = (rg * 16 + e < k) ? v[e] - mean : 0.f;
-                Xs[(rg * 16 + e) * RT_XS_LD + cc] = x;
-            }
+            float xc[16];
+            pg::centre_chunk<RT_XS_LD>(Xs, Part, cc, rg, k, inv_k, xc);
             // buffer b is free once the MMAs of chunk ci - 2 are done with it
             if (ptid == 0 && ci >= 2) wait(&b_empty[b], (uint32_t)((ci >> 1) - 1) & 1u);
             asm volatile("bar.sync 1, 256;" ::: "memory");
