@@ -124,8 +124,13 @@ typedef enum {
                                         host-call copies, batched-call lanes); a call that needs more returns
                                         MECUCO_ERR_OOM before allocating, leaving the context usable.
                                         0 (default): no cap */
-    MECUCO_OPT_PROFILE_STAGES = 12   /* bit mask of the mecuco_stage values that MECUCO_OPT_PROFILE brackets
+    MECUCO_OPT_PROFILE_STAGES = 12,  /* bit mask of the mecuco_stage values that MECUCO_OPT_PROFILE brackets
                                         with events (1 << stage); 0 (default): every stage */
+    MECUCO_OPT_TT_SLOTS = 13,        /* BF16-mixed third-moment pass: TMEM slots of its row-product operand
+                                        (2, 4, 6 or 8, default 4; as MECUCO_OPT_TC_SLOTS) */
+    MECUCO_OPT_TT_CTAS = 14          /* BF16-mixed third-moment pass: CTAs per SM, 1 (512 TMEM columns each)
+                                        or 2 (default; 256 each: fewer accumulators per pass over the patch,
+                                        two hand-over pipelines interleaved).  Results identical */
 } mecuco_option;
 
 /* Kernel stages, for mecuco_get_stage_times. */

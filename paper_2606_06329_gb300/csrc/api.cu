@@ -68,6 +68,12 @@ struct mecuco_ctx {
     int knn_pair = -1;  // -1: CTA pairs for N >= KNN_PAIR_MIN_N
     int chunk_share = 1;  // concurrent lanes sharing the chunk budget (batched calls)
     int tc_slots = 4;
+    // third-moment pass: TMEM slots of the A operand and CTAs per SM; two CTAs
+    // of 256 columns (2 tiles per pass, 9 passes at k = 64) interleave their
+    // hand-over pipelines: 177 against 251 ms for one CTA of 512 columns at
+    // 100k x 4096 (6 or 8 slots in one CTA: 275 / 261 ms; 2 slots in two: 289 ms)
+    int tt_slots = 4;
+    int tt_ctas = 2;
     // randomised low-rank SVD (mecuco_curvature_rsvd), set for the duration of a call
     struct {
         int rank = 0, cols = 0, power = 0;
@@ -506,7 +512,8 @@ mecuco_status run_curvature(mecuco_t h, char *ws, const void *X, mecuco_dtype dt
             LAUNCH(h, MECUCO_STAGE_MOMENTS, s,
                    launch_tthird_tc(b.Y, rot_ld(m), k, m, np, h->tttab[k], b.sig, Ud, b.R, Qarg, (int)var,
                                     rank_eps_gram32(m), kappa_out + p0, lambda_out ? lambda_out + p0 * k : nullptr,
-                                    s_out ? s_out + p0 * k : nullptr, h->tc_slots, h->wait_limit, h->ctr, s));
+                                    s_out ? s_out + p0 * k : nullptr, h->tt_slots, h->tt_ctas, h->wait_limit, h->ctr,
+                                    s));
         } else {
             // plain FP32: moments of the rotated patch Z = U0^T X_c (U0 = refined
             // eigenvectors of the FP32 Gram; K is invariant under the rotation and the
@@ -759,6 +766,14 @@ mecuco_status mecuco_set_option(mecuco_t h, mecuco_option opt, int64_t v) {
         case MECUCO_OPT_PROFILE_STAGES:
             if (v < 0 || v >= ((int64_t)1 << MECUCO_STAGE_COUNT)) return MECUCO_ERR_INVALID_ARG;
             h->profile_mask = v == 0 ? -1 : v;
+            break;
+        case MECUCO_OPT_TT_SLOTS:
+            if (v < 2 || v > 8 || (v & 1)) return MECUCO_ERR_INVALID_ARG;
+            h->tt_slots = (int)v;
+            break;
+        case MECUCO_OPT_TT_CTAS:
+            if (v < 1 || v > 2) return MECUCO_ERR_INVALID_ARG;
+            h->tt_ctas = (int)v;
             break;
         case MECUCO_OPT_WAIT_LIMIT:
             if (v < 0) return MECUCO_ERR_INVALID_ARG;

@@ -111,7 +111,9 @@ size_t moments_tc_smem_bytes(int k);
 // per point (U from launch_jacobi, k x k), BF16, point p's row l at
 // Y + (p * 64 + l) * ldy (rows k..63 zero), ldy >= m rounded up to 64, ldy % 8 == 0.
 // launch_tthird_tc: the Fast estimator from Y, sigma, U, R and Q (Haar) -
-// kappa, and lambda_out / s_out when not NULL; rowtab from tthird_build_rows.
+// kappa, and lambda_out / s_out when not NULL; rowtab from tthird_build_rows;
+// ctas = 1 or 2 CTAs per SM (512 or 256 TMEM columns each, nslots of them the
+// A operand's slots).
 cudaError_t launch_gram_tc(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, const int32_t *idx,
                            int k, int64_t np, float *G, float *R, float *Q, long long wait_limit, DevCounters *ctr,
                            cudaStream_t s);
@@ -122,7 +124,7 @@ int tthird_rows(int k);
 void tthird_build_rows(int k, int32_t *codes /* tthird_rows(k) */);
 cudaError_t launch_tthird_tc(const void *Y, int64_t ldy, int k, int64_t m, int64_t np, const int32_t *rowtab,
                              const float *sigma, const float *U, const float *R, const float *Q, int variant,
-                             float rank_eps, float *kappa, float *lambda_out, float *s_out, int nslots,
+                             float rank_eps, float *kappa, float *lambda_out, float *s_out, int nslots, int ctas,
                              long long wait_limit, DevCounters *ctr, cudaStream_t s);
 
 // ---- Step 3: k x k eigensolve -----------------------------------------------

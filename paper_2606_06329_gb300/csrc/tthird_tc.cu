@@ -80,11 +80,12 @@ void tthird_build_rows(int k, int32_t *codes) {
     for (; n < nrows; ++n) codes[n] = 0;
 }
 
-// At least 120 KB, so that one CTA holds an SM (each allocates all 512 TMEM
-// columns; a second CTA would only wait in its allocation).
-size_t tthird_smem_bytes(int k) {
+// ctas = CTAs per SM, each allocating 512 / ctas TMEM columns.  With one CTA
+// the request is raised to 120 KB so that no second CTA becomes resident (it
+// would only wait in its allocation).
+size_t tthird_smem_bytes(int k, int ctas) {
     const size_t need = 1024 + (size_t)TT_NS * TT_STAGE + (size_t)tthird_rows(k) * 8 + 64 * (size_t)TT_DLD * 4;
-    return need > ((size_t)120 << 10) ? need : ((size_t)120 << 10);
+    return (ctas == 1 && need < ((size_t)120 << 10)) ? ((size_t)120 << 10) : need;
 }
 
 __global__ void __launch_bounds__(TT_THREADS, 1)
@@ -92,7 +93,7 @@ tthird_tc_kernel(const __grid_constant__ CUtensorMap map_y, int k, int64_t m, co
                  int nrows, const float *__restrict__ sigma, const float *__restrict__ U,
                  const float *__restrict__ R, const float *__restrict__ Q, int variant, float rank_eps,
                  float *__restrict__ kappa, float *__restrict__ lambda_out, float *__restrict__ s_out, int nslots,
-                 long long wait_limit, DevCounters *ctr) {
+                 int tcols, long long wait_limit, DevCounters *ctr) {
     extern __shared__ __align__(1024) uint8_t tsm_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tsm_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *ring = base;                                                        // TT_NS stages
@@ -110,7 +111,7 @@ tthird_tc_kernel(const __grid_constant__ CUtensorMap map_y, int k, int64_t m, co
     const int64_t pt = blockIdx.x;
     const int ntiles = nrows / 128;
     const int Nb = tthird_n(k);
-    const int dcols = 512 - nslots * TT_SLOT_COLS;
+    const int dcols = tcols - nslots * TT_SLOT_COLS;  // accumulator columns; the A slots follow
     const int tpp = min(ntiles, dcols / Nb);
     const int npass = (ntiles + tpp - 1) / tpp;
     const int nchunks = (int)((m + TT_CH - 1) / TT_CH);
@@ -145,7 +146,7 @@ tthird_tc_kernel(const __grid_constant__ CUtensorMap map_y, int k, int64_t m, co
         tc::prefetch_tmap(&map_y);
     }
     if (warp == 0) {
-        tc::tmem_alloc(tc::smem_u32(&tmem_slot), 512);
+        tc::tmem_alloc(tc::smem_u32(&tmem_slot), (uint32_t)tcols);
         tc::tmem_relinquish();
     }
     tc::fence_before();
@@ -424,7 +425,7 @@ tthird_tc_kernel(const __grid_constant__ CUtensorMap map_y, int k, int64_t m, co
     __syncthreads();
     if (warp == 0) {
         tc::fence_after();
-        tc::tmem_dealloc(tmem, 512);
+        tc::tmem_dealloc(tmem, (uint32_t)tcols);
     }
 }
 
@@ -445,11 +446,13 @@ PFN_cuTensorMapEncodeTiled_v12000 tt_encode_fn() {
 
 cudaError_t launch_tthird_tc(const void *Y, int64_t ldy, int k, int64_t m, int64_t np, const int32_t *rowtab,
                              const float *sigma, const float *U, const float *R, const float *Q, int variant,
-                             float rank_eps, float *kappa, float *lambda_out, float *s_out, int nslots,
+                             float rank_eps, float *kappa, float *lambda_out, float *s_out, int nslots, int ctas,
                              long long wait_limit, DevCounters *ctr, cudaStream_t s) {
     if (np <= 0) return cudaSuccess;
-    if (k > 64 || k < 2 || nslots < TT_GROUP || nslots > TT_MAX_SLOTS || nslots % TT_GROUP != 0 ||
-        (512 - nslots * TT_SLOT_COLS) < tthird_n(k) || (ldy % 8) != 0 || ldy < (m + TT_CH - 1) / TT_CH * TT_CH ||
+    const int tcols = ctas == 2 ? 256 : 512;
+    if (k > 64 || k < 2 || (ctas != 1 && ctas != 2) || nslots < TT_GROUP || nslots > TT_MAX_SLOTS ||
+        nslots % TT_GROUP != 0 || (tcols - nslots * TT_SLOT_COLS) < tthird_n(k) || (ldy % 8) != 0 ||
+        ldy < (m + TT_CH - 1) / TT_CH * TT_CH ||
         (reinterpret_cast<uintptr_t>(Y) & 15) || np * 64 >= ((int64_t)1 << 31) ||
         (variant == MECUCO_FAST_HAAR && !Q))
         return cudaErrorInvalidValue;
@@ -467,12 +470,12 @@ cudaError_t launch_tthird_tc(const void *Y, int64_t ldy, int k, int64_t m, int64
            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
     const int nrows = tthird_rows(k);
-    const size_t smem = tthird_smem_bytes(k);
+    const size_t smem = tthird_smem_bytes(k, ctas);
     cudaError_t e = cudaFuncSetAttribute(tthird_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     tthird_tc_kernel<<<(unsigned)np, TT_THREADS, smem, s>>>(map, k, m, rowtab, nrows, sigma, U, R, Q, variant,
-                                                            rank_eps, kappa, lambda_out, s_out, nslots, wait_limit,
-                                                            ctr);
+                                                            rank_eps, kappa, lambda_out, s_out, nslots, tcols,
+                                                            wait_limit, ctr);
     return cudaGetLastError();
 }
 

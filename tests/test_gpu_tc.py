@@ -193,3 +193,30 @@ def test_tc_moment_slots_do_not_change_results(ctx, k, variant):
     for o in outs[1:]:
         assert torch.equal(o, outs[0])
 
+
+
+@pytest.mark.parametrize("k,variant", [(64, "literal"), (20, "haar")])
+def test_third_moment_pass_schedules_give_the_same_results(ctx, k, variant):
+    # the BF16-mixed third-moment pass with 1 or 2 CTAs per SM and 2..8 TMEM
+    # slots: the tiles, passes and hand-over change, the sums are formed in a
+    # fixed order, so kappa is bit-identical
+    from paper_2606_06329_gb300 import _native as N
+    bits = synth.curved_patches(n=2000, m=1000, n_patches=3, seed=11 + k)
+    Xd = _bf16(bits).cuda()
+    idx = ctx.mecuco_knn(Xd, k, precision="bf16_mixed")
+    outs = []
+    try:
+        for ctas, slots in ((1, 2), (1, 4), (1, 8), (2, 2), (2, 4)):
+            ctx.set_option(N.OPT_TT_CTAS, ctas)
+            ctx.set_option(N.OPT_TT_SLOTS, slots)
+            outs.append(ctx.mecuco_curvature(Xd, k, idx=idx, precision="bf16_mixed", variant=variant))
+            torch.cuda.synchronize()
+            assert ctx.mecuco_get_last_status() == 0
+        for bad in ((N.OPT_TT_CTAS, 3), (N.OPT_TT_SLOTS, 5)):
+            with pytest.raises(Exception):
+                ctx.set_option(*bad)
+    finally:
+        ctx.set_option(N.OPT_TT_CTAS, 2)
+        ctx.set_option(N.OPT_TT_SLOTS, 4)
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
