@@ -40,6 +40,8 @@ WORKLOADS = {
                               desc="32 curved 8-dim quadratic patches in R^4096 + N(0,0.005^2) noise, BF16"),
     "curved_patches_100k": dict(kind="curved_patches", N=100_000, m=4096, k=64, n_patches=32,
                                 desc="curved patches, reduced N (development size)"),
+    "curved_patches_200k": dict(kind="curved_patches", N=200_000, m=4096, k=64, n_patches=32,
+                                desc="curved patches, reduced N (one search launch, 1.6 GB: traffic captures)"),
     "sparse_clusters_70k": dict(kind="sparse_clusters", N=70_000, m=784, k=50,
                                 desc="10 sparse [0,1] Gaussian clusters, 80% zeros, FP32 (MNIST-class shape)"),
 }

@@ -501,19 +501,32 @@ mecuco_status run_curvature(mecuco_t h, char *ws, const void *X, mecuco_dtype dt
             // the eigenpairs of G, the rotated patch Y = U^T X_c, then every term of
             // the estimator from the third moments of Y (no M is stored)
             float *Ud = U_out ? U_out + p0 * (int64_t)k * k : b.U;
-            LAUNCH(h, MECUCO_STAGE_GRAM, s,
-                   launch_gram_tc(X, dt, N, m, ld, nb, k, np, b.G, b.R, var == MECUCO_FAST_HAAR ? b.Q : nullptr,
-                                  h->wait_limit, h->ctr, s));
+            PatchSeg sg{};
+            sg.X = X;
+            sg.N = N;
+            sg.m = m;
+            sg.ld = ld;
+            sg.k = k;
+            sg.idx = nb;
+            sg.rowtab = h->tttab[k];
+            sg.G = b.G;
+            sg.R = b.R;
+            sg.Q = b.Q;
+            sg.sig = b.sig;
+            sg.U = Ud;
+            sg.kappa = kappa_out + p0;
+            sg.lambda = lambda_out ? lambda_out + p0 * k : nullptr;
+            sg.s = s_out ? s_out + p0 * k : nullptr;
+            const int haar = var == MECUCO_FAST_HAAR ? 1 : 0;
+            LAUNCH(h, MECUCO_STAGE_GRAM, s, launch_gram_tc(dt, sg, nullptr, 0, np, haar, h->wait_limit, h->ctr, s));
             LAUNCH(h, MECUCO_STAGE_JACOBI, s,
-                   launch_jacobi(b.G, k, np, fp64, h->jacobi_max_sweeps, b.sig, Ud, h->ctr, s, kJacobiPreLoose));
+                   launch_jacobi_seg(sg, nullptr, 0, k, np, fp64, h->jacobi_max_sweeps, h->ctr, s, kJacobiPreLoose));
             if (fp64 == 1 || fp64 == 3) ++h->launches;  // the refinement is a second kernel
             LAUNCH(h, MECUCO_STAGE_ROTATE, s,
-                   launch_rotate_tc(X, dt, N, m, ld, nb, k, np, Ud, b.Y, rot_ld(m), h->wait_limit, h->ctr, s));
+                   launch_rotate_tc(dt, sg, nullptr, 0, np, b.Y, rot_ld(m), h->wait_limit, h->ctr, s));
             LAUNCH(h, MECUCO_STAGE_MOMENTS, s,
-                   launch_tthird_tc(b.Y, rot_ld(m), k, m, np, h->tttab[k], b.sig, Ud, b.R, Qarg, (int)var,
-                                    rank_eps_gram32(m), kappa_out + p0, lambda_out ? lambda_out + p0 * k : nullptr,
-                                    s_out ? s_out + p0 * k : nullptr, h->tt_slots, h->tt_ctas, h->wait_limit, h->ctr,
-                                    s));
+                   launch_tthird_tc(sg, nullptr, 0, k, np, b.Y, rot_ld(m), (int)var, h->tt_slots, h->tt_ctas,
+                                    h->wait_limit, h->ctr, s));
         } else {
             // plain FP32: moments of the rotated patch Z = U0^T X_c (U0 = refined
             // eigenvectors of the FP32 Gram; K is invariant under the rotation and the

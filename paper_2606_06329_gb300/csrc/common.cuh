@@ -28,6 +28,40 @@ struct DevCounters {
     unsigned pad;
 };
 
+// One run of consecutive points of one dataset within a launch over the points
+// of a chunk.  A single-dataset call passes one segment by value; a batched
+// call passes a device table of segments (one per dataset part in the chunk),
+// and each CTA finds the segment of its point.  Pointers are those of the
+// segment's first point; per-point rows follow with the segment's own k.
+struct PatchSeg {
+    const void *X;            // the dataset, row-major, leading dimension ld
+    int64_t N, m, ld;
+    int k;
+    int first;                // first point (block) of the launch in this segment
+    const int32_t *idx;       // neighbour lists (k per point)
+    const int32_t *rowtab;    // third-moment pass: row table for this k
+    float *G, *R, *Q;         // k x k, k, k x k per point
+    float *sig, *U;           // eigenpairs: k and k x k per point
+    float *kappa, *lambda, *s;// outputs: 1, k, k per point (lambda, s nullable)
+};
+
+// The segment of launch point `blk` and the point's index within it.
+__device__ __forceinline__ const PatchSeg &find_seg(const PatchSeg &one, const PatchSeg *tab, int ntab, int blk,
+                                                    int &local) {
+    if (ntab == 0) {
+        local = blk;
+        return one;
+    }
+    int lo = 0, hi = ntab - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tab[mid].first <= blk) lo = mid;
+        else hi = mid - 1;
+    }
+    local = blk - tab[lo].first;
+    return tab[lo];
+}
+
 // --- element loads ---------------------------------------------------------
 __device__ __forceinline__ float load_elem(const float *p) { return __ldg(p); }
 __device__ __forceinline__ float load_elem(const __nv_bfloat16 *p) {

@@ -43,9 +43,8 @@ size_t gram_tc_smem_bytes() { return 1024 + 2 * (size_t)GT_TILE + 64 * (size_t)G
 // two CTAs per SM (113 registers a thread): the gather needs warps in flight
 template <typename T>
 __global__ void __launch_bounds__(GT_THREADS, 2)
-gram_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, const int32_t *__restrict__ idx, int k,
-               float *__restrict__ G, float *__restrict__ R, float *__restrict__ Q, long long wait_limit,
-               DevCounters *ctr) {
+gram_tc_kernel(const __grid_constant__ PatchSeg one, const PatchSeg *__restrict__ tab, int ntab, int with_q,
+               long long wait_limit, DevCounters *ctr) {
     extern __shared__ __align__(1024) uint8_t gsm_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *Tile0 = base;                                           // 2 x 128-row tile
@@ -57,12 +56,17 @@ gram_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, const 
     __shared__ int abort_flag, never;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t pt = blockIdx.x;
+    int local;
+    const PatchSeg &seg = find_seg(one, tab, ntab, (int)blockIdx.x, local);
+    const T *X = static_cast<const T *>(seg.X);
+    const int64_t N = seg.N, m = seg.m, ld = seg.ld, pt = local;
+    const int k = seg.k;
+    const int32_t *idx = seg.idx;
+    float *G = seg.G, *R = seg.R, *Q = with_q ? seg.Q : nullptr;
     const int nchunks = (int)((m + GT_CH - 1) / GT_CH);
     const int Nb = k <= 16 ? 16 : ((k + 15) / 16) * 16;
     const uint32_t idesc = tc::idesc_bf16_f32(128, Nb);
     const bool vec = (ld % 8 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
-    const bool with_q = Q != nullptr;
 
     if (tid < 64) {
         int r = 0;
@@ -229,11 +233,10 @@ gram_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, const 
     }
 }
 
-cudaError_t launch_gram_tc(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, const int32_t *idx,
-                           int k, int64_t np, float *G, float *R, float *Q, long long wait_limit, DevCounters *ctr,
-                           cudaStream_t s) {
+cudaError_t launch_gram_tc(mecuco_dtype dt, const PatchSeg &one, const PatchSeg *tab, int ntab, int64_t np,
+                           int with_q, long long wait_limit, DevCounters *ctr, cudaStream_t s) {
     if (np <= 0) return cudaSuccess;
-    if (k > 64 || k < 2) return cudaErrorInvalidValue;
+    if (ntab == 0 && (one.k > 64 || one.k < 2)) return cudaErrorInvalidValue;
     if (wait_limit <= 0) wait_limit = GT_WAIT;
     const size_t smem = gram_tc_smem_bytes();
     cudaError_t e;
@@ -241,13 +244,11 @@ cudaError_t launch_gram_tc(const void *X, mecuco_dtype dt, int64_t N, int64_t m,
         e = cudaFuncSetAttribute(gram_tc_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
-        gram_tc_kernel<<<(unsigned)np, GT_THREADS, smem, s>>>((const __nv_bfloat16 *)X, N, m, ld, idx, k, G, R, Q,
-                                                             wait_limit, ctr);
+        gram_tc_kernel<__nv_bfloat16><<<(unsigned)np, GT_THREADS, smem, s>>>(one, tab, ntab, with_q, wait_limit, ctr);
     } else {
         e = cudaFuncSetAttribute(gram_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        gram_tc_kernel<<<(unsigned)np, GT_THREADS, smem, s>>>((const float *)X, N, m, ld, idx, k, G, R, Q,
-                                                             wait_limit, ctr);
+        gram_tc_kernel<float><<<(unsigned)np, GT_THREADS, smem, s>>>(one, tab, ntab, with_q, wait_limit, ctr);
     }
     return cudaGetLastError();
 }

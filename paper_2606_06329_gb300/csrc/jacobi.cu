@@ -55,22 +55,27 @@ struct alignas(2 * sizeof(Real) + 2 * sizeof(int) > 16 ? 32 : 16) JRot {
 
 template <typename Real>
 __global__ void __launch_bounds__(JT)
-jacobi_kernel(const float *__restrict__ G, int k, int64_t np, int max_sweeps, Real eps, float *__restrict__ sigma,
-              float *__restrict__ U, DevCounters *ctr) {
+jacobi_kernel(const __grid_constant__ PatchSeg one, const PatchSeg *__restrict__ tab, int ntab, int max_sweeps,
+              Real eps, DevCounters *ctr) {
     extern __shared__ __align__(16) unsigned char jsm[];
+    int local;
+    const PatchSeg &seg = find_seg(one, tab, ntab, (int)blockIdx.x, local);
+    const int k = seg.k;
+    const float *G = seg.G;
+    float *sigma = seg.sig, *U = seg.U;
     const int kp = (k + 1) & ~1;
     const int h = kp / 2;
     const int ld = kp + 1;
     Real *A = reinterpret_cast<Real *>(jsm);
     Real *V = A + (size_t)kp * ld;
     // [h] rotations of the round, after A and V (rounded up to the entry alignment)
-    JRot<Real> *tab = reinterpret_cast<JRot<Real> *>(
+    JRot<Real> *rtab = reinterpret_cast<JRot<Real> *>(
         (reinterpret_cast<uintptr_t>(V + (size_t)kp * ld) + alignof(JRot<Real>) - 1) & ~(uintptr_t)(alignof(JRot<Real>) - 1));
     __shared__ int s_rot;
     __shared__ int s_act;  // rotations in the current round (compacted table length)
 
     const int tid = threadIdx.x;
-    const int64_t patch = blockIdx.x;
+    const int64_t patch = local;
     const float *g = G + patch * (int64_t)k * k;
     for (int e = tid; e < kp * kp; e += JT) {
         int r = e / kp, c = e % kp;
@@ -102,7 +107,7 @@ jacobi_kernel(const float *__restrict__ G, int k, int64_t np, int max_sweeps, Re
                     const Real c = (Real)1 / sqrt((Real)1 + t * t);
                     // rotations of one round commute: keep only those that rotate, in any order
                     const int slot = atomicAdd(&s_act, 1);
-                    tab[slot] = JRot<Real>{c, t * c, p, q};
+                    rtab[slot] = JRot<Real>{c, t * c, p, q};
                 }
             }
             __syncthreads();
@@ -114,7 +119,7 @@ jacobi_kernel(const float *__restrict__ G, int k, int64_t np, int max_sweeps, Re
                 Real *row = A + line * ld;
 #pragma unroll 4
                 for (int i = i0; i < i1; ++i) {
-                    const JRot<Real> rt = tab[i];
+                    const JRot<Real> rt = rtab[i];
                     const int p = rt.p, q = rt.q;
                     const Real c = rt.c, s = rt.s;
                     const Real x = row[p], y = row[q];
@@ -128,7 +133,7 @@ jacobi_kernel(const float *__restrict__ G, int k, int64_t np, int max_sweeps, Re
                 Real *urow = V + line * ld;
 #pragma unroll 4
                 for (int i = i0; i < i1; ++i) {
-                    const JRot<Real> rt = tab[i];
+                    const JRot<Real> rt = rtab[i];
                     const int p = rt.p, q = rt.q;
                     const Real c = rt.c, s = rt.s;
                     const Real x = A[p * ld + line], y = A[q * ld + line];
@@ -141,7 +146,7 @@ jacobi_kernel(const float *__restrict__ G, int k, int64_t np, int max_sweeps, Re
             }
             __syncthreads();
             if (tid < nact) {
-                const JRot<Real> rt = tab[tid];
+                const JRot<Real> rt = rtab[tid];
                 A[rt.p * ld + rt.q] = 0;
                 A[rt.q * ld + rt.p] = 0;
             }
@@ -226,9 +231,13 @@ __device__ __forceinline__ int tri(int a, int b, int k) { return a * k - (a * (a
 constexpr int FT_REFINE = 256;
 
 __global__ void __launch_bounds__(FT_REFINE, 2)
-jacobi_refine_ff_kernel(const float *__restrict__ G, int k, int rel, float *__restrict__ sigma,
-                        float *__restrict__ U) {
+jacobi_refine_ff_kernel(const __grid_constant__ PatchSeg one, const PatchSeg *__restrict__ tab, int ntab, int rel) {
     extern __shared__ __align__(16) unsigned char fsm[];
+    int local;
+    const PatchSeg &seg = find_seg(one, tab, ntab, (int)blockIdx.x, local);
+    const int k = seg.k;
+    const float *G = seg.G;
+    float *sigma = seg.sig, *U = seg.U;
     const int ld = k + 1;
     const int ntri = k * (k + 1) / 2;
     float *A = reinterpret_cast<float *>(fsm);  // [k][ld], later E
@@ -242,7 +251,7 @@ jacobi_refine_ff_kernel(const float *__restrict__ G, int k, int rel, float *__re
     double *lam = reinterpret_cast<double *>(reinterpret_cast<uintptr_t>(Rl + ntri + 1) & ~(uintptr_t)7);  // [k]
     __shared__ double s_lmax;
     const int tid = threadIdx.x;
-    const int64_t pt = blockIdx.x;
+    const int64_t pt = local;
     const float *g = G + pt * (int64_t)k * k;
     float *u = U + pt * (int64_t)k * k;
     const int kk = k * k;
@@ -366,38 +375,46 @@ size_t jacobi_smem_bytes(int k, int fp64) {
     return (size_t)2 * kp * (kp + 1) * real + ent + (size_t)(kp / 2) * ent;
 }
 
-cudaError_t launch_jacobi(const float *G, int k, int64_t np, int fp64, int max_sweeps, float *sigma, float *U,
-                          DevCounters *ctr, cudaStream_t s, float pre_eps) {
+cudaError_t launch_jacobi_seg(const PatchSeg &one, const PatchSeg *tab, int ntab, int kmax, int64_t np, int fp64,
+                              int max_sweeps, DevCounters *ctr, cudaStream_t s, float pre_eps) {
     if (np <= 0) return cudaSuccess;
-    if (k > 64) return cudaErrorInvalidValue;
+    if (kmax > 64 || kmax < 1) return cudaErrorInvalidValue;
     cudaError_t e;
     if (fp64 == 1 || fp64 == 3) {
         // FP32 sweeps, then one refinement step (3: relative cluster test)
-        const size_t smem = jacobi_smem_bytes(k, 0);
+        const size_t smem = jacobi_smem_bytes(kmax, 0);
         e = cudaFuncSetAttribute(jacobi_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        jacobi_kernel<float><<<(unsigned)np, JT, smem, s>>>(G, k, np, max_sweeps, pre_eps, sigma, U, ctr);
+        jacobi_kernel<float><<<(unsigned)np, JT, smem, s>>>(one, tab, ntab, max_sweeps, pre_eps, ctr);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        const size_t rs = refine_ff_smem_bytes(k);
+        const size_t rs = refine_ff_smem_bytes(kmax);
         e = cudaFuncSetAttribute(jacobi_refine_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs);
         if (e != cudaSuccess) return e;
-        jacobi_refine_ff_kernel<<<(unsigned)np, FT_REFINE, rs, s>>>(G, k, fp64 == 3, sigma, U);
+        jacobi_refine_ff_kernel<<<(unsigned)np, FT_REFINE, rs, s>>>(one, tab, ntab, fp64 == 3);
         return cudaGetLastError();
     }
-    const size_t smem = jacobi_smem_bytes(k, fp64);
+    const size_t smem = jacobi_smem_bytes(kmax, fp64);
     if (fp64 == 2) {
         e = cudaFuncSetAttribute(jacobi_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        jacobi_kernel<double><<<(unsigned)np, JT, smem, s>>>(G, k, np, max_sweeps, JacobiEps<double>::rel(), sigma,
-                                                             U, ctr);
+        jacobi_kernel<double><<<(unsigned)np, JT, smem, s>>>(one, tab, ntab, max_sweeps, JacobiEps<double>::rel(), ctr);
     } else {
         e = cudaFuncSetAttribute(jacobi_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        jacobi_kernel<float><<<(unsigned)np, JT, smem, s>>>(G, k, np, max_sweeps, JacobiEps<float>::rel(), sigma, U,
-                                                            ctr);
+        jacobi_kernel<float><<<(unsigned)np, JT, smem, s>>>(one, tab, ntab, max_sweeps, JacobiEps<float>::rel(), ctr);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_jacobi(const float *G, int k, int64_t np, int fp64, int max_sweeps, float *sigma, float *U,
+                          DevCounters *ctr, cudaStream_t s, float pre_eps) {
+    PatchSeg one{};
+    one.k = k;
+    one.G = const_cast<float *>(G);
+    one.sig = sigma;
+    one.U = U;
+    return launch_jacobi_seg(one, nullptr, 0, k, np, fp64, max_sweeps, ctr, s, pre_eps);
 }
 
 }  // namespace mecuco

@@ -11,6 +11,7 @@
 namespace mecuco {
 
 struct DevCounters;
+struct PatchSeg;
 
 // Text returned by mecuco_last_error_message() for this thread.
 void set_error_text(const char *msg);
@@ -105,27 +106,26 @@ cudaError_t launch_moments_tc(const void *X, mecuco_dtype dt, int64_t N, int64_t
 int moments_tc_rows(int k);
 void moments_tc_build_rows(int k, int32_t *codes /* moments_tc_rows(k) */);
 size_t moments_tc_smem_bytes(int k);
-// BF16-mixed estimator in the rotated basis.  launch_gram_tc: G, R and (Q not
-// NULL) Q of each patch, as launch_patch_gram's outputs, from BF16 operands on
-// the tensor cores.  launch_rotate_tc: Y = U^T X_c
-// per point (U from launch_jacobi, k x k), BF16, point p's row l at
-// Y + (p * 64 + l) * ldy (rows k..63 zero), ldy >= m rounded up to 64, ldy % 8 == 0.
-// launch_tthird_tc: the Fast estimator from Y, sigma, U, R and Q (Haar) -
-// kappa, and lambda_out / s_out when not NULL; rowtab from tthird_build_rows;
-// ctas = 1 or 2 CTAs per SM (512 or 256 TMEM columns each, nslots of them the
-// A operand's slots).
-cudaError_t launch_gram_tc(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, const int32_t *idx,
-                           int k, int64_t np, float *G, float *R, float *Q, long long wait_limit, DevCounters *ctr,
-                           cudaStream_t s);
-cudaError_t launch_rotate_tc(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, const int32_t *idx,
-                             int k, int64_t np, const float *U, void *Y, int64_t ldy, long long wait_limit,
-                             DevCounters *ctr, cudaStream_t s);
-int tthird_rows(int k);
+// BF16-mixed estimator in the rotated basis, over the points of a launch
+// described by a segment table (PatchSeg, common.cuh: one segment by value for
+// a single dataset, or a device table for several).  launch_gram_tc: G, R and
+// (with_q) Q of each patch, as launch_patch_gram's outputs, from BF16 operands
+// on the tensor cores.  launch_rotate_tc: Y = U^T X_c per point (U from
+// launch_jacobi, k x k), BF16; launch point p's row l at Y + (p * 64 + l) * ldy
+// (rows k..63 zero), ldy >= every segment's m rounded up to 64, ldy % 8 == 0.
+// launch_tthird_tc: the Fast estimator from Y, sig, U, R and Q (Haar) -
+// kappa, and lambda / s when not NULL; rowtab from tthird_build_rows for the
+// segment's k; kmax bounds every segment's k; ctas = 1 or 2 CTAs per SM (512 or
+// 256 TMEM columns each, nslots of them the A operand's slots).
+cudaError_t launch_gram_tc(mecuco_dtype dt, const PatchSeg &one, const PatchSeg *tab, int ntab, int64_t np,
+                           int with_q, long long wait_limit, DevCounters *ctr, cudaStream_t s);
+cudaError_t launch_rotate_tc(mecuco_dtype dt, const PatchSeg &one, const PatchSeg *tab, int ntab, int64_t np, void *Y,
+                             int64_t ldy, long long wait_limit, DevCounters *ctr, cudaStream_t s);
+__host__ __device__ int tthird_rows(int k);
 void tthird_build_rows(int k, int32_t *codes /* tthird_rows(k) */);
-cudaError_t launch_tthird_tc(const void *Y, int64_t ldy, int k, int64_t m, int64_t np, const int32_t *rowtab,
-                             const float *sigma, const float *U, const float *R, const float *Q, int variant,
-                             float rank_eps, float *kappa, float *lambda_out, float *s_out, int nslots, int ctas,
-                             long long wait_limit, DevCounters *ctr, cudaStream_t s);
+cudaError_t launch_tthird_tc(const PatchSeg &one, const PatchSeg *tab, int ntab, int kmax, int64_t np, const void *Y,
+                             int64_t ldy, int variant, int nslots, int ctas, long long wait_limit, DevCounters *ctr,
+                             cudaStream_t s);
 
 // ---- Step 3: k x k eigensolve -----------------------------------------------
 // Parallel-order two-sided Jacobi, one CTA per patch.  G: np x k x k.
@@ -145,6 +145,10 @@ constexpr float kJacobiPreLoose = 6.103515625e-05f;        // 2^-14
 cudaError_t launch_jacobi(const float *G, int k, int64_t np, int fp64, int max_sweeps,
                           float *sigma, float *U, DevCounters *ctr, cudaStream_t s,
                           float pre_eps = kJacobiPreTight);
+// The same over a segment table (PatchSeg: G, k, sig, U of each segment);
+// kmax bounds every segment's k.
+cudaError_t launch_jacobi_seg(const PatchSeg &one, const PatchSeg *tab, int ntab, int kmax, int64_t np, int fp64,
+                              int max_sweeps, DevCounters *ctr, cudaStream_t s, float pre_eps);
 
 // ---- Step 4: k-space estimator ----------------------------------------------
 // sigma/U from launch_jacobi, M pair-major from launch_patch_m3, R and Q from

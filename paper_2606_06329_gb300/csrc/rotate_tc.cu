@@ -49,9 +49,8 @@ size_t rotate_tc_smem_bytes() {
 // two CTAs per SM (113 registers a thread): the gather needs warps in flight
 template <typename T>
 __global__ void __launch_bounds__(RT_THREADS, 2)
-rotate_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, const int32_t *__restrict__ idx, int k,
-                 const float *__restrict__ U, __nv_bfloat16 *__restrict__ Y, int64_t ldy, long long wait_limit,
-                 DevCounters *ctr) {
+rotate_tc_kernel(const __grid_constant__ PatchSeg one, const PatchSeg *__restrict__ tab, int ntab,
+                 __nv_bfloat16 *__restrict__ Y, int64_t ldy, long long wait_limit, DevCounters *ctr) {
     extern __shared__ __align__(1024) uint8_t rsm_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(rsm_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *Aop = base;                                             // 2 A tiles (U_hi^T, U_lo^T)
@@ -64,7 +63,14 @@ rotate_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, cons
     __shared__ int abort_flag, never;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t pt = blockIdx.x;
+    int local;
+    const PatchSeg &seg = find_seg(one, tab, ntab, (int)blockIdx.x, local);
+    const T *X = static_cast<const T *>(seg.X);
+    const int64_t N = seg.N, m = seg.m, ld = seg.ld, pt = local;
+    const int k = seg.k;
+    const int32_t *idx = seg.idx;
+    const float *U = seg.U;
+    const int64_t yp = blockIdx.x;  // Y is indexed by the launch's point (uniform ldy)
     const int nchunks = (int)((m + RT_CH - 1) / RT_CH);
     const uint32_t idesc = tc::idesc_bf16_f32(128, 64);
     const bool vec = (ld % 8 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
@@ -146,7 +152,7 @@ rotate_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, cons
         // drain: warps with lane quarter 0 or 1 (TMEM lanes = rows l 0..63), column half dh
         const bool drainer = (warp & 3) < 2;
         const int dq = warp & 3, dh = warp >> 2;
-        __nv_bfloat16 *yrow = Y + ((int64_t)pt * 64 + dq * 32 + lane) * ldy;
+        __nv_bfloat16 *yrow = Y + (yp * 64 + dq * 32 + lane) * ldy;
         Unit8<T> pre0, pre1;
         if (live0) pre0.load(grow0, gg * 8, m, vec); else pre0.zero();
         if (live1) pre1.load(grow1, gg * 8, m, vec); else pre1.zero();
@@ -234,11 +240,11 @@ rotate_tc_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, cons
     }
 }
 
-cudaError_t launch_rotate_tc(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, const int32_t *idx,
-                             int k, int64_t np, const float *U, void *Y, int64_t ldy, long long wait_limit,
-                             DevCounters *ctr, cudaStream_t s) {
+cudaError_t launch_rotate_tc(mecuco_dtype dt, const PatchSeg &one, const PatchSeg *tab, int ntab, int64_t np, void *Y,
+                             int64_t ldy, long long wait_limit, DevCounters *ctr, cudaStream_t s) {
     if (np <= 0) return cudaSuccess;
-    if (k > 64 || k < 2 || ldy < (m + RT_CH - 1) / RT_CH * RT_CH || (ldy % 8) != 0 ||
+    // every segment's m must fit ldy (the caller's contract for tables)
+    if ((ntab == 0 && (one.k > 64 || one.k < 2 || ldy < (one.m + RT_CH - 1) / RT_CH * RT_CH)) || (ldy % 8) != 0 ||
         (reinterpret_cast<uintptr_t>(Y) & 15))
         return cudaErrorInvalidValue;
     if (wait_limit <= 0) wait_limit = RT_WAIT;
@@ -248,13 +254,13 @@ cudaError_t launch_rotate_tc(const void *X, mecuco_dtype dt, int64_t N, int64_t 
         e = cudaFuncSetAttribute(rotate_tc_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
-        rotate_tc_kernel<<<(unsigned)np, RT_THREADS, smem, s>>>((const __nv_bfloat16 *)X, N, m, ld, idx, k, U,
-                                                               (__nv_bfloat16 *)Y, ldy, wait_limit, ctr);
+        rotate_tc_kernel<__nv_bfloat16><<<(unsigned)np, RT_THREADS, smem, s>>>(one, tab, ntab, (__nv_bfloat16 *)Y,
+                                                                              ldy, wait_limit, ctr);
     } else {
         e = cudaFuncSetAttribute(rotate_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        rotate_tc_kernel<<<(unsigned)np, RT_THREADS, smem, s>>>((const float *)X, N, m, ld, idx, k, U,
-                                                               (__nv_bfloat16 *)Y, ldy, wait_limit, ctr);
+        rotate_tc_kernel<float><<<(unsigned)np, RT_THREADS, smem, s>>>(one, tab, ntab, (__nv_bfloat16 *)Y, ldy,
+                                                                      wait_limit, ctr);
     }
     return cudaGetLastError();
 }

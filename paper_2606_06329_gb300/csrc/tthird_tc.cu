@@ -57,7 +57,7 @@ enum : int { ROW_NONE = 0, ROW_PAIR = 1 };
 __host__ __device__ inline int tthird_n(int k) { return k <= 16 ? 16 : ((k + 15) / 16) * 16; }
 }  // namespace
 
-int tthird_rows(int k) {
+__host__ __device__ int tthird_rows(int k) {
     const int kb = (k + 7) / 8;
     return (kb * (kb + 1) / 2 * 64 + 127) / 128 * 128;
 }
@@ -88,12 +88,22 @@ size_t tthird_smem_bytes(int k, int ctas) {
     return (ctas == 1 && need < ((size_t)120 << 10)) ? ((size_t)120 << 10) : need;
 }
 
-__global__ void __launch_bounds__(TT_THREADS, 1)
-tthird_tc_kernel(const __grid_constant__ CUtensorMap map_y, int k, int64_t m, const int32_t *__restrict__ rowtab,
-                 int nrows, const float *__restrict__ sigma, const float *__restrict__ U,
-                 const float *__restrict__ R, const float *__restrict__ Q, int variant, float rank_eps,
-                 float *__restrict__ kappa, float *__restrict__ lambda_out, float *__restrict__ s_out, int nslots,
-                 int tcols, long long wait_limit, DevCounters *ctr) {
+// two CTAs per SM by default (102 registers a thread at most)
+__global__ void __launch_bounds__(TT_THREADS, 2)
+tthird_tc_kernel(const __grid_constant__ CUtensorMap map_y, const __grid_constant__ PatchSeg one,
+                 const PatchSeg *__restrict__ tab, int ntab, int variant, int nslots, int tcols, long long wait_limit,
+                 DevCounters *ctr) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int local;
+    const PatchSeg &seg = find_seg(one, tab, ntab, (int)blockIdx.x, local);
+    const int64_t pt = local, m = seg.m;
+    const int k = seg.k;
+    const int nrows = tthird_rows(k);
+    const int32_t *rowtab = seg.rowtab;
+    const float *sigma = seg.sig, *U = seg.U, *R = seg.R, *Q = seg.Q;
+    float *kappa = seg.kappa, *lambda_out = seg.lambda, *s_out = seg.s;
+    // numerical-rank threshold of a Gram accumulated from BF16 products
+    const float rank_eps = 8.f * sqrtf((float)m) * 5.9604644775390625e-08f;
     extern __shared__ __align__(1024) uint8_t tsm_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tsm_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *ring = base;                                                        // TT_NS stages
@@ -107,8 +117,6 @@ tthird_tc_kernel(const __grid_constant__ CUtensorMap map_y, int k, int64_t m, co
     __shared__ double red[TT_THREADS / 32][4];
     __shared__ int s_p, abort_flag, never;
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t pt = blockIdx.x;
     const int ntiles = nrows / 128;
     const int Nb = tthird_n(k);
     const int dcols = tcols - nslots * TT_SLOT_COLS;  // accumulator columns; the A slots follow
@@ -267,7 +275,7 @@ tthird_tc_kernel(const __grid_constant__ CUtensorMap map_y, int k, int64_t m, co
                         break;
                     }
                     tc::mbar_expect_tx(full0 + 8 * st, TT_STAGE);
-                    tc::tma_load_2d(ring0 + st * TT_STAGE, &map_y, full0 + 8 * st, ci * TT_CH, (int)(pt * 64));
+                    tc::tma_load_2d(ring0 + st * TT_STAGE, &map_y, full0 + 8 * st, ci * TT_CH, (int)(blockIdx.x * 64));
                     ++issued;
                     if (++st == (uint32_t)TT_NS) { st = 0; sph ^= 1u; }
                 }
@@ -444,17 +452,16 @@ PFN_cuTensorMapEncodeTiled_v12000 tt_encode_fn() {
 }
 }  // namespace
 
-cudaError_t launch_tthird_tc(const void *Y, int64_t ldy, int k, int64_t m, int64_t np, const int32_t *rowtab,
-                             const float *sigma, const float *U, const float *R, const float *Q, int variant,
-                             float rank_eps, float *kappa, float *lambda_out, float *s_out, int nslots, int ctas,
-                             long long wait_limit, DevCounters *ctr, cudaStream_t s) {
+cudaError_t launch_tthird_tc(const PatchSeg &one, const PatchSeg *tab, int ntab, int kmax, int64_t np, const void *Y,
+                             int64_t ldy, int variant, int nslots, int ctas, long long wait_limit, DevCounters *ctr,
+                             cudaStream_t s) {
     if (np <= 0) return cudaSuccess;
     const int tcols = ctas == 2 ? 256 : 512;
-    if (k > 64 || k < 2 || (ctas != 1 && ctas != 2) || nslots < TT_GROUP || nslots > TT_MAX_SLOTS ||
-        nslots % TT_GROUP != 0 || (tcols - nslots * TT_SLOT_COLS) < tthird_n(k) || (ldy % 8) != 0 ||
-        ldy < (m + TT_CH - 1) / TT_CH * TT_CH ||
-        (reinterpret_cast<uintptr_t>(Y) & 15) || np * 64 >= ((int64_t)1 << 31) ||
-        (variant == MECUCO_FAST_HAAR && !Q))
+    if (kmax > 64 || kmax < 2 || (ctas != 1 && ctas != 2) || nslots < TT_GROUP || nslots > TT_MAX_SLOTS ||
+        nslots % TT_GROUP != 0 || (tcols - nslots * TT_SLOT_COLS) < tthird_n(kmax) || (ldy % 8) != 0 ||
+        (ntab == 0 && (one.k != kmax || ldy < (one.m + TT_CH - 1) / TT_CH * TT_CH ||
+                       (variant == MECUCO_FAST_HAAR && !one.Q))) ||
+        (reinterpret_cast<uintptr_t>(Y) & 15) || np * 64 >= ((int64_t)1 << 31))
         return cudaErrorInvalidValue;
     if (wait_limit <= 0) wait_limit = TT_WAIT;
     auto fn = tt_encode_fn();
@@ -469,13 +476,11 @@ cudaError_t launch_tthird_tc(const void *Y, int64_t ldy, int k, int64_t m, int64
            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
-    const int nrows = tthird_rows(k);
-    const size_t smem = tthird_smem_bytes(k, ctas);
+    const size_t smem = tthird_smem_bytes(kmax, ctas);
     cudaError_t e = cudaFuncSetAttribute(tthird_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    tthird_tc_kernel<<<(unsigned)np, TT_THREADS, smem, s>>>(map, k, m, rowtab, nrows, sigma, U, R, Q, variant,
-                                                            rank_eps, kappa, lambda_out, s_out, nslots, tcols,
-                                                            wait_limit, ctr);
+    tthird_tc_kernel<<<(unsigned)np, TT_THREADS, smem, s>>>(map, one, tab, ntab, variant, nslots, tcols, wait_limit,
+                                                            ctr);
     return cudaGetLastError();
 }
 
