@@ -44,6 +44,10 @@ WORKLOADS = {
                                 desc="curved patches, reduced N (one search launch, 1.6 GB: traffic captures)"),
     "sparse_clusters_70k": dict(kind="sparse_clusters", N=70_000, m=784, k=50,
                                 desc="10 sparse [0,1] Gaussian clusters, 80% zeros, FP32 (MNIST-class shape)"),
+    "batched_256": dict(kind="batched", nsets=256,
+                        desc="256 independent datasets in one batched call: N ~ U[500, 20000], m in {64, 128, 256, "
+                             "512, 1024}, k ~ U[10, 64]; seeded 2-layer tanh MLP images of d-dim Gaussian latents "
+                             "(d ~ U[2, 16]) + N(0, 0.01^2) noise, FP32"),
 }
 
 
@@ -214,6 +218,8 @@ def run_reference(args):
     if rank != 0:
         return
     w = WORKLOADS[args.workload]
+    if w["kind"] == "batched":
+        return run_reference_batched(args)
     host, kind = _make_workload(args.workload)
     vals, times = [], []
     import numpy as np
@@ -238,6 +244,49 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_reference_batched(args):
+    """The oracle on the batched workload: each step a bounded sample of rows
+    from randomly chosen datasets of the batch (brute-force FP64 kNN over the
+    dataset + the FP64 Fast estimator), host cores, rank 0."""
+    import numpy as np
+    import oracle
+    from paper_2606_06329_gb300 import synth
+    w = WORKLOADS[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    sets = synth.batched_mlp_datasets(nsets=w["nsets"], seed=1)
+    oracle.build()
+    cores = os.cpu_count() or 1
+    vals, times = [], []
+    for step in range(args.warmup + args.steps):
+        rng = np.random.default_rng(100 + step)
+        pick = rng.choice(len(sets), min(args.cpu_sets, len(sets)), replace=False)
+        t0 = time.perf_counter()
+        nrows = 0
+        for i in pick:
+            X, k = sets[i]["X"], sets[i]["k"]
+            r = np.sort(rng.choice(X.shape[0], min(args.cpu_rows_per_set, X.shape[0]), replace=False))
+            ridx, _ = oracle.knn(X, k, rows=r, nthreads=cores)
+            full = np.zeros((X.shape[0], k), dtype=np.int32)
+            full[r] = ridx
+            oracle.curvature(X, k, full, rows=r, nthreads=cores)
+            nrows += r.size
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            vals.append(nrows / dt)
+            times.append(dt * 1e3)
+    value = sum(vals) / len(vals)
+    sample = (f"{nrows} random rows of {len(pick)} random datasets of the batch per step, each a brute-force FP64 "
+              f"kNN scan of its dataset plus the FP64 Fast estimator")
+    line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"{args.workload}: {w['desc']}", "datasets": len(sets), "variant": "literal",
+                       "precision": "fp64 oracle", "device": "host cores (rank 0)"},
+            "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def aggregate_timing(elapsed_ms: float, n_per_rank: int, steps: int, dist=None, device="cpu"):
     """Whole-job timing of replicas: the slowest rank's timed region (max over
     ranks) and the points all ranks processed per second in it."""
@@ -254,33 +303,49 @@ def aggregate_timing(elapsed_ms: float, n_per_rank: int, steps: int, dist=None, 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA (2 FLOP) x 2.07 GHz
 
 
-def _stage_fracs(stages, steps, N, m, k, prec, rotations, peaks, elt=2):
+def _stage_fracs(stages, steps, shapes, prec, rotations, peaks, elt=2):
     """Per-stage achieved rate against its binding roof, from one profiled step
-    (CUDA events around every launch).  Algorithmic work per stage:
+    (CUDA events around every launch).  shapes: the (N, m, k) of every dataset
+    of the step; the algorithmic work per stage is summed over them:
       knn_search  2 N^2 m FLOP (tensor, BF16; FP32 lanes in the plain form)
-      knn_rerank  N x 128 candidate rows x m x 2 bytes read (2 lists of 64 per
-                  row from the tensor-core search at k = 64), against HBM
+      knn_rerank  N x 128 candidate rows x m x elt bytes read (2 lists of 64 per
+                  row from the tensor-core search), against HBM
       gram        the gathered patches, N k m elements, against HBM
       rotate      the gathered patches plus the rotated patches written
-                  (N x 64 rows x m BF16), against HBM
+                  (N x k rows x m BF16), against HBM
       moments     k(k+1)(k+2)/6 m multiply-adds per point (the distinct third
                   moments), x 2 FLOP (tensor, BF16)
       jacobi      18 k FLOP per plane rotation (two-sided update of A and the
-                  eigenvector update) + 8 k^3 per patch for the refinement's
-                  three products, against the FP32 lanes
+                  eigenvector update; k weighted by the rotations a k x k patch
+                  takes, ~k^2: sum N k^3 / sum N k^2) + 8 k^3 per patch for the
+                  refinement's three products, against the FP32 lanes
       estimator   k (2 k^2 p + k p (p + 1)) FLOP per point (B = M_j W and the
                   upper triangle of W^T B), p = k - 1, against the FP32 lanes"""
     bf = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
     hbm = peaks.get("hbm_gbs")
-    p = k - 1
+    tot = {key: 0.0 for key in ("knn_search", "knn_rerank", "gram", "rotate", "moments", "jacobi_ref", "estimator",
+                                "nk3", "nk2")}
+    for N, m, k in shapes:
+        N, m, k = float(N), float(m), float(k)
+        p = k - 1
+        tot["knn_search"] += 2.0 * N * N * m
+        tot["knn_rerank"] += N * 128.0 * m * elt
+        tot["gram"] += N * k * m * elt
+        tot["rotate"] += N * k * m * elt + N * k * m * 2.0
+        tot["moments"] += 2.0 * k * (k + 1) * (k + 2) / 6.0 * m * N
+        tot["jacobi_ref"] += 8.0 * k ** 3 * N
+        tot["estimator"] += k * (2.0 * k * k * p + k * p * (p + 1)) * N
+        tot["nk3"] += N * k ** 3
+        tot["nk2"] += N * k ** 2
+    kw = tot["nk3"] / tot["nk2"]
     work = {
-        "knn_search": (2.0 * N * N * m, "tensor" if prec == "bf16_mixed" else "alu"),
-        "knn_rerank": (N * 128.0 * m * 2.0, "hbm"),
-        "gram": (float(N) * k * m * elt, "hbm"),
-        "rotate": (float(N) * k * m * elt + N * 64.0 * m * 2.0, "hbm"),
-        "moments": (2.0 * k * (k + 1) * (k + 2) / 6.0 * m * N, "tensor"),
-        "jacobi": (18.0 * k * rotations + 8.0 * k ** 3 * N, "alu"),
-        "estimator": (k * (2.0 * k * k * p + k * p * (p + 1)) * N, "alu"),
+        "knn_search": (tot["knn_search"], "tensor" if prec == "bf16_mixed" else "alu"),
+        "knn_rerank": (tot["knn_rerank"], "hbm"),
+        "gram": (tot["gram"], "hbm"),
+        "rotate": (tot["rotate"], "hbm"),
+        "moments": (tot["moments"], "tensor"),
+        "jacobi": (18.0 * kw * rotations + tot["jacobi_ref"], "alu"),
+        "estimator": (tot["estimator"], "alu"),
     }
     out = {}
     for name, (ms, n) in stages.items():
@@ -296,12 +361,15 @@ def _stage_fracs(stages, steps, N, m, k, prec, rotations, peaks, elt=2):
                 ach, pk, unit = w / sec / 1e12, bf, "TFLOP/s"
             else:
                 ach, pk, unit = w / sec / 1e12, FP32_PEAK_TFLOPS, "TFLOP/s"
-            ent.update({"bound": bound, "achieved": ach, "peak": pk, "unit": unit, "frac": ach / pk})
+            ent.update({"bound": bound, "achieved": ach, "peak": pk, "unit": unit, "frac": ach / pk,
+                        "work_per_step": w})
         out[name] = ent
     return out
 
 
 def run_ours(args):
+    if WORKLOADS[args.workload]["kind"] == "batched":
+        return run_batched(args)
     import numpy as np
     import torch
     rank, world, local = _rank_env()
@@ -408,7 +476,7 @@ def run_ours(args):
                        "timing": "headline with only the distance-search launches event-bracketed; stage "
                                  "times from one further step with every launch bracketed"},
             "roofline": roof, "gpu_launches": launches, "clocks": clk, "status": status,
-            "stages": _stage_fracs(stages, 1, N, m, k, prec, stats1["jacobi_rotations"], peaks,
+            "stages": _stage_fracs(stages, 1, [(N, m, k)], prec, stats1["jacobi_rotations"], peaks,
                                    elt=Xd.element_size()),
             "knn_stats": {kk: stats[kk] for kk in ("knn_uncertified", "knn_fallback_rows", "jacobi_max_sweeps",
                                                   "jacobi_not_converged", "rank_deficient", "jacobi_rotations")}}
@@ -517,6 +585,222 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+STAGE_KERNELS = {
+    "knn_search": "knn_tc_kernel (distance GEMM + fused candidate select)",
+    "knn_rerank": "knn_rerank_kernel", "gram": "gram_tc_kernel", "rotate": "rotate_tc_kernel",
+    "moments": "tthird_tc_kernel (third moments of the rotated patch + estimator)",
+    "jacobi": "jacobi_kernel + jacobi_refine_ff_kernel", "estimator": "estimator_kernel",
+}
+
+
+def run_batched(args):
+    """The batched workload: every dataset of the batch through one
+    mecuco_curvature_batched call, captured once into a CUDA graph; a step is
+    one replay.  The configuration comes from mecuco_autotune_batched (run
+    before the warm-up, untimed)."""
+    import numpy as np
+    import torch
+    rank, world, local = _rank_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2606_06329_gb300 import api, build, synth, _native as NAT
+    build.build()
+    w = WORKLOADS[args.workload]
+    sets = synth.batched_mlp_datasets(nsets=w["nsets"], seed=1 + rank)
+    ks = [d["k"] for d in sets]
+    shapes = [(d["X"].shape[0], d["X"].shape[1], d["k"]) for d in sets]
+    npts = sum(sh[0] for sh in shapes)
+    in_bytes = sum(d["X"].nbytes for d in sets)
+    Xh = [torch.from_numpy(d["X"]).pin_memory() for d in sets]
+    Xs = [x.cuda() for x in Xh]
+    idx_out = [torch.empty((n, k), dtype=torch.int32, device="cuda") for n, _, k in shapes]
+    ctx = api.Context(local)
+    prec, var = args.precision, args.variant
+    stream = torch.cuda.current_stream()
+    tuned = ctx.mecuco_autotune_batched(Xs, ks, precision=prec, variant=var)
+
+    def call():
+        return ctx.mecuco_curvature_batched(Xs, ks, precision=prec, variant=var, idx_out=idx_out)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    # stage table: one eager call with every launch bracketed by events
+    ctx.set_option(NAT.OPT_PROFILE_STAGES, 0)
+    ctx.set_option(NAT.OPT_PROFILE, 1)
+    ctx.mecuco_get_stage_times()
+    call()
+    torch.cuda.synchronize()
+    stages = ctx.mecuco_get_stage_times()
+    stats = ctx.mecuco_get_stats()
+    ctx.set_option(NAT.OPT_PROFILE, 0)
+    launches_per_call = stats["kernel_launches"]
+    # the call captured once (tables and workspace exist after the eager calls)
+    gs = torch.cuda.Stream()
+    gs.wait_stream(stream)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(gs):
+        with torch.cuda.graph(graph, stream=gs):
+            kap_g = call()
+    stream.wait_stream(gs)
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    status = ctx.mecuco_get_last_status()
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        graph.replay()
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    elapsed_ms, value = aggregate_timing(ev0.elapsed_time(ev1), npts, args.steps, dist, device="cuda")
+    status = status or ctx.mecuco_get_last_status()
+
+    # roofline of the dominant stage's kernel: K eager calls with only its
+    # launches bracketed, right after the graph replays
+    peaks, src = _peaks()
+    elt = 4
+    fr = _stage_fracs(stages, 1, shapes, prec, stats["jacobi_rotations"], peaks, elt=elt)
+    dom = max((n for n in fr if "bound" in fr[n]), key=lambda n: fr[n]["ms_per_step"])
+    ctx.set_option(NAT.OPT_PROFILE_STAGES, 1 << NAT.STAGES.index(dom))
+    ctx.set_option(NAT.OPT_PROFILE, 1)
+    ctx.mecuco_get_stage_times()
+    for _ in range(args.steps):
+        call()
+    torch.cuda.synchronize()
+    dms, dn = ctx.mecuco_get_stage_times()[dom]
+    ctx.set_option(NAT.OPT_PROFILE, 0)
+    dwork = fr[dom]["work_per_step"]
+    dsec = dms / args.steps * 1e-3
+    ach = dwork / dsec / (1e9 if fr[dom]["bound"] == "hbm" else 1e12)
+    pk = fr[dom]["peak"]
+    roof = {"kernel": STAGE_KERNELS.get(dom, dom), "stage": dom, "bound": fr[dom]["bound"], "achieved": ach,
+            "peak": pk, "unit": fr[dom]["unit"], "frac": ach / pk, "traffic": None,
+            "peak_source": (f"{src} bf16_tflops_sustained" if fr[dom]["bound"] == "tensor" else
+                            f"{src} hbm_gbs" if fr[dom]["bound"] == "hbm" else
+                            "derived: FP32 FMA lanes 152 SMs x 128 x 2 FLOP x 2.07 GHz"),
+            "algorithmic": "the stage's work summed over the batch's datasets (see stages)",
+            "launches_timed": dn, "share_of_step": dms / args.steps / (elapsed_ms / args.steps),
+            "timing": f"{args.steps} eager calls with only this stage's launches event-bracketed, after the "
+                      f"graph replays"}
+
+    line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16-gemm/f32/f32x2-refine" if prec == "bf16_mixed" else "f32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {w['desc']}", "datasets": len(sets), "points": npts,
+                       "m_mean": float(np.mean([sh[1] for sh in shapes])),
+                       "k_mean": float(np.mean(ks)), "variant": var, "precision": prec,
+                       "l2": "inputs larger than L2 (%.1f GB in all)" % (in_bytes / 1e9),
+                       "parallelism": f"replicas x{world}", "tuned": tuned,
+                       "timing": "one step = one replay of a CUDA graph of the batched call; stage table from one "
+                                 "eager call with every launch bracketed"},
+            "roofline": roof, "gpu_launches": launches_per_call * args.steps, "launches_per_call": launches_per_call,
+            "clocks": clk, "status": status, "stages": fr,
+            "knn_stats": {kk: stats[kk] for kk in ("knn_uncertified", "knn_fallback_rows", "jacobi_max_sweeps",
+                                                  "jacobi_not_converged", "rank_deficient", "jacobi_rotations")}}
+
+    # sampled rows for the accuracy check and the oracle's timing
+    rng = np.random.default_rng(7)
+    pick = rng.choice(len(sets), min(args.cpu_sets, len(sets)), replace=False)
+    rows = {int(i): np.sort(rng.choice(shapes[i][0], min(args.cpu_rows_per_set, shapes[i][0]), replace=False))
+            for i in pick}
+    chosen = {i: (idx_out[i].cpu().numpy()[r], kap_g[i].cpu().numpy()[r]) for i, r in rows.items()}
+    plain = None
+    if rank == 0 and not args.no_plain and prec != "fp32":
+        kf = ctx.mecuco_curvature_batched(Xs, ks, precision="fp32", variant=var)
+        torch.cuda.synchronize()
+        idx_f = [torch.empty_like(t) for t in idx_out]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        kf = ctx.mecuco_curvature_batched(Xs, ks, precision="fp32", variant=var, idx_out=idx_f)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1)
+        plain = {i: (idx_f[i].cpu().numpy()[r], kf[i].cpu().numpy()[r]) for i, r in rows.items()}
+        line["plain_fp32"] = {"value": npts / (pms * 1e-3), "unit": "points/s",
+                              "sample": f"the whole batch in the plain FP32 form (stream lanes), one eager call; "
+                                        f"{pms:.0f} ms",
+                              "chosen_over_plain": value / world / (npts / (pms * 1e-3))}
+
+    if rank == 0 and not args.no_e2e:
+        kap_h = [torch.empty(n, dtype=torch.float32).pin_memory() for n, _, _ in shapes]
+
+        def e2e_step():
+            for xd, xh in zip(Xs, Xh):
+                xd.copy_(xh, non_blocking=True)
+            kk = call()
+            for a, b in zip(kap_h, kk):
+                a.copy_(b, non_blocking=True)
+            torch.cuda.synchronize()
+
+        e2e_step()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        dt = time.perf_counter() - t0
+        line["e2e"] = {"value": npts * args.e2e_steps / dt, "unit": "points/s", "h2d_bytes_per_step": int(in_bytes),
+                       "d2h_bytes_per_step": int(npts * 4), "steps": args.e2e_steps,
+                       "ms_per_step": dt / args.e2e_steps * 1e3,
+                       "path": "per step: pinned-host to device copy of every dataset, one eager batched call "
+                               "(public Python binding over the C ABI), device to pinned-host copy of every kappa"}
+
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        cores = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        ref = {}
+        for i, r in rows.items():
+            X = sets[i]["X"]
+            ridx, rd = oracle.knn(X, ks[i], rows=r, nthreads=cores)
+            full = np.zeros((X.shape[0], ks[i]), dtype=np.int32)
+            full[r] = ridx
+            ref[i] = (ridx, rd, oracle.curvature(X, ks[i], full, rows=r, nthreads=cores))
+        dt = time.perf_counter() - t0
+        nrows = sum(len(r) for r in rows.values())
+        line["cpu_baseline"] = {"value": nrows / dt, "unit": "points/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{nrows} random rows of {len(rows)} random datasets of the batch, each a "
+                                          f"brute-force FP64 kNN scan of its dataset plus the FP64 Fast estimator; "
+                                          f"{dt:.1f} s"}
+
+        def acc_of(got):
+            errs, bad = [], 0
+            for i, r in rows.items():
+                a = _accuracy(sets[i]["X"], "f32", r, got[i][0], got[i][1], *ref[i])
+                bad += a["knn_mismatch_rows"]
+                errs.append(np.abs(np.asarray(got[i][1], np.float64) - ref[i][2]) / np.abs(ref[i][2]))
+            e = np.concatenate(errs)
+            return {"kappa_max_rel": float(e.max()), "kappa_median_rel": float(np.median(e)),
+                    "knn_mismatch_rows": int(bad), "rows": int(e.size)}
+
+        acc = {"reference": "FP64 oracle: brute-force kNN over each dataset, Alg. 1 Fast branch on its lists",
+               "tie_rule": "list positions may differ only between distances equal within 1e-6 relative",
+               "chosen": acc_of(chosen)}
+        if plain is not None:
+            acc["plain_fp32"] = acc_of(plain)
+        line["accuracy"] = acc
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -529,6 +813,8 @@ def main():
     ap.add_argument("--jacobi-fp64", type=int, choices=[0, 1, 2], default=None)
     ap.add_argument("--plain-rows", type=int, default=4096)
     ap.add_argument("--cpu-rows", type=int, default=32)
+    ap.add_argument("--cpu-sets", type=int, default=16, help="batched workload: datasets sampled for the oracle")
+    ap.add_argument("--cpu-rows-per-set", type=int, default=4)
     ap.add_argument("--ref-rows", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--fp64-rows", type=int, default=16384)

@@ -128,9 +128,14 @@ typedef enum {
                                         with events (1 << stage); 0 (default): every stage */
     MECUCO_OPT_TT_SLOTS = 13,        /* BF16-mixed third-moment pass: TMEM slots of its row-product operand
                                         (2, 4, 6 or 8, default 4; as MECUCO_OPT_TC_SLOTS) */
-    MECUCO_OPT_TT_CTAS = 14          /* BF16-mixed third-moment pass: CTAs per SM, 1 (512 TMEM columns each)
+    MECUCO_OPT_TT_CTAS = 14,         /* BF16-mixed third-moment pass: CTAs per SM, 1 (512 TMEM columns each)
                                         or 2 (default; 256 each: fewer accumulators per pass over the patch,
                                         two hand-over pipelines interleaved).  Results identical */
+    MECUCO_OPT_BATCH_PERSISTENT = 15 /* 1 (default): mecuco_curvature_batched with MECUCO_PREC_BF16_MIXED runs
+                                        every dataset of the batch in one launch per stage (persistent kNN
+                                        over a device table of all datasets' work items, estimator launches
+                                        over segment tables of all datasets' points); 0: one stream lane per
+                                        dataset group, as the FP32 form always does.  Results identical */
 } mecuco_option;
 
 /* Kernel stages, for mecuco_get_stage_times. */
@@ -329,26 +334,65 @@ typedef struct {
 } mecuco_dataset;
 
 /* kNN + Fast-mode curvature (Alg. 1) of many independent datasets of uneven
- * sizes in one call, each exactly as mecuco_curvature computes it.  The
- * datasets are spread over concurrent streams ("lanes", longest first onto the
- * least-loaded lane; the caller's stream forks to them and joins them back),
- * each lane with its own slice of a batch workspace.  `sets` is a host array
- * read during the call.  A call that needs no new workspace and no new per-k
- * table (every k already seen by this context) makes no allocation and no
- * host synchronisation, so it can be captured into a CUDA graph; make one
- * uncaptured call with the same datasets first. */
+ * sizes in one call, each exactly as mecuco_curvature computes it (the same
+ * neighbour lists and curvatures, bit for bit).
+ *
+ * MECUCO_PREC_BF16_MIXED (with MECUCO_OPT_BATCH_PERSISTENT = 1, the default):
+ * one launch per stage for the whole batch.  The datasets are ordered by m,
+ * then N, descending; a device table describes each (its operand's tensor
+ * maps, its first search work item and first row) and the persistent kNN
+ * search takes the work items (query block x candidate split) of every
+ * dataset from it, one CTA (or CTA pair) per SM; row norms, BF16 copies,
+ * re-rank and fallback take every row of the batch in one launch each.  The
+ * estimator stages (Gram, eigensolve, rotation, third moments) run over
+ * segment tables that cover the points of all datasets; they are cut into as
+ * few launches as the rotated patches fit the 8 GB chunk scratch (the points
+ * of one launch share one leading dimension, that of their largest m).  The
+ * kNN tile form (single-CTA 128 x 256 or CTA-pair 256 x 256 tiles) and the
+ * third-moment pass's patches per SM and TMEM slots come from
+ * mecuco_autotune_batched when it has tuned this batch signature, else from
+ * the context's options.
+ *
+ * MECUCO_PREC_FP32 (or MECUCO_OPT_BATCH_PERSISTENT = 0): the datasets are
+ * spread over concurrent streams ("lanes", longest first onto the least-loaded
+ * lane; the caller's stream forks to them and joins them back), each lane with
+ * its own slice of a batch workspace.
+ *
+ * `sets` is a host array read during the call.  The context keeps the device
+ * tables of the last 64 distinct batches (matched byte for byte on the inputs,
+ * sizes and workspace addresses; the outputs' addresses are written into the
+ * table by a kernel at the start of every call, so calls with the same inputs
+ * reuse one table and must not run concurrently on different streams).  A call that needs no new workspace, no
+ * new per-k table (every k already seen by this context) and no new batch table
+ * makes no allocation and no host synchronisation, so it can be captured into
+ * a CUDA graph; make one uncaptured call with the same datasets first, and
+ * replay the graph only while its batch is among the 64 kept (a captured call
+ * that would need a new table fails with MECUCO_ERR_INVALID_ARG instead). */
 MECUCO_API mecuco_status mecuco_curvature_batched(mecuco_t h, const mecuco_dataset *sets, int nsets,
                                                   mecuco_dtype dt, int include_self, mecuco_variant var,
                                                   mecuco_precision prec, void *stream);
 
-/* Times mecuco_curvature_batched on these datasets with 1, 2, 4, 8, 16 and 32
- * lanes (CUDA events on `stream`, after one warm-up call), keeps the fastest
- * for this batch signature (number of sets, total N, m and k, dtype,
- * precision) in the context and returns it in *lanes_out.  Synchronous; the
- * results of the last timed call are left in the datasets' outputs. */
+/* The configuration mecuco_autotune_batched picked for a batch signature. */
+typedef struct mecuco_batch_tuning {
+    int lanes;            /* concurrent streams (lanes form); 1 for the one-launch-per-stage form */
+    int knn_pair;         /* kNN tiles: 1 = CTA pairs, 256 x 256 per two-SM MMA; 0 = 128 x 256 per CTA */
+    int tt_ctas;          /* third-moment pass: patches (CTAs) resident per SM, 1 or 2 */
+    int tt_slots;         /* third-moment pass: TMEM slots of the row-product operand */
+    float ms;             /* device time of one batched call in that configuration */
+} mecuco_batch_tuning;
+
+/* Times mecuco_curvature_batched on these datasets (CUDA events on `stream`,
+ * after one warm-up call) over a small search space and keeps the fastest
+ * configuration for this batch signature (number of sets, total N, m and k,
+ * dtype, precision) in the context.  One-launch-per-stage form: the kNN tile
+ * form (CTA pairs or single CTAs), then the third-moment pass's (CTAs per SM,
+ * TMEM slots) in {(2, 2), (2, 4), (1, 4), (1, 8)}, each stage tuned with the
+ * other at its best so far.  Lanes form: 1, 2, 4, 8, 16 and 32 lanes.
+ * Synchronous; the results of the last timed call are left in the datasets'
+ * outputs; `out` (may be NULL) receives the configuration kept. */
 MECUCO_API mecuco_status mecuco_autotune_batched(mecuco_t h, const mecuco_dataset *sets, int nsets,
                                                  mecuco_dtype dt, int include_self, mecuco_variant var,
-                                                 mecuco_precision prec, void *stream, int *lanes_out);
+                                                 mecuco_precision prec, void *stream, mecuco_batch_tuning *out);
 
 /* The same computation with HOST buffers (pageable or pinned): X_host is
  * copied to the device, the path runs, kappa (and idx if idx_host_out is not

@@ -18,7 +18,7 @@ FAST_LITERAL, FAST_HAAR = 0, 1
 PREC_FP32, PREC_BF16_MIXED = 0, 1
 (OPT_KNN_MARGIN, OPT_JACOBI_FP64, OPT_JACOBI_MAX_SWEEPS, OPT_CHUNK_POINTS, OPT_KNN_QUERY_CHUNK, OPT_PROFILE,
  OPT_KNN_SPLITS, OPT_BATCH_LANES, OPT_TC_SLOTS, OPT_KNN_PAIR, OPT_WAIT_LIMIT, OPT_WORKSPACE_LIMIT,
- OPT_PROFILE_STAGES, OPT_TT_SLOTS, OPT_TT_CTAS) = range(15)
+ OPT_PROFILE_STAGES, OPT_TT_SLOTS, OPT_TT_CTAS, OPT_BATCH_PERSISTENT) = range(16)
 STAGES = ("rownorm", "knn_search", "knn_rerank", "knn_fallback", "gram", "moments", "jacobi", "estimator", "adjoint",
           "basis", "exact", "fidelity", "rotate")
 
@@ -49,6 +49,11 @@ class mecuco_dataset(C.Structure):
                 ("idx", C.c_void_p), ("kappa", C.c_void_p)]
 
 
+class mecuco_batch_tuning(C.Structure):
+    _fields_ = [("lanes", C.c_int), ("knn_pair", C.c_int), ("tt_ctas", C.c_int), ("tt_slots", C.c_int),
+                ("ms", C.c_float)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -74,7 +79,7 @@ SIGNATURES = {
     "mecuco_minmax_normalize": (_st, [_p, _p, _i64, _p, _p]),
     "mecuco_curvature_batched": (_st, [_p, C.POINTER(mecuco_dataset), _i32, _i32, _i32, _i32, _i32, _p]),
     "mecuco_autotune_batched": (_st, [_p, C.POINTER(mecuco_dataset), _i32, _i32, _i32, _i32, _i32, _p,
-                                      C.POINTER(C.c_int)]),
+                                      C.POINTER(mecuco_batch_tuning)]),
     "mecuco_curvature_host": (_st, [_p, _p, _i32, _i64, _i64, _i64, _i32, _i32, _i32, _i32, _p, _p, _p]),
     "mecuco_knn_noalloc": (_st, [_p, _i32, _i64, _i64, _i64, _i32, _i32, _p, _p, _p]),
     "mecuco_get_last_status": (_st, [_p, _p]),

@@ -255,14 +255,16 @@ class Context:
         return kappas
 
     def mecuco_autotune_batched(self, Xs, ks, include_self: bool = False, variant: str = "literal",
-                                precision: str = "fp32") -> int:
-        """Time the batched call with 1..32 lanes; keep and return the fastest lane count."""
+                                precision: str = "fp32") -> dict:
+        """Time the batched call over its tuning space (BF16-mixed: kNN tile form and the
+        third-moment pass's CTAs per SM and TMEM slots; FP32: 1..32 lanes); keep the fastest
+        for this batch signature and return it as a dict."""
         arr, dt, _ = self._datasets(Xs, ks, None)
-        lanes = C.c_int(0)
+        out = N.mecuco_batch_tuning()
         st = self.lib.mecuco_autotune_batched(self.handle, arr, len(Xs), dt, int(bool(include_self)), _VAR[variant],
-                                              _PREC[precision], _stream(self.device), C.byref(lanes))
+                                              _PREC[precision], _stream(self.device), C.byref(out))
         N.check(st, "mecuco_autotune_batched")
-        return lanes.value
+        return {f: getattr(out, f) for f, _ in N.mecuco_batch_tuning._fields_}
 
     def mecuco_tangent_basis(self, X: torch.Tensor, k: int, idx: torch.Tensor, d_out: int, row_begin: int = 0,
                              row_end=None) -> torch.Tensor:

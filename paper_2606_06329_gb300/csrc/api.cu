@@ -86,7 +86,15 @@ struct mecuco_ctx {
     cudaStream_t lane_stream[32] = {};
     cudaEvent_t lane_event[32] = {};
     cudaEvent_t fork_event = nullptr;
-    std::map<std::tuple<int, int64_t, int64_t, int64_t, int, int>, int> tuned_lanes;  // batch signature -> lanes
+    int batch_persistent = 1;  // BF16-mixed batches: one launch per stage (0: lanes)
+    // batch signature -> tuned configuration (mecuco_autotune_batched)
+    std::map<std::tuple<int, int64_t, int64_t, int64_t, int, int>, mecuco_batch_tuning> tuned;
+    // device tables of the one-launch-per-stage batches, oldest first
+    struct BatchTables {
+        std::vector<char> host;
+        char *dev = nullptr;
+    };
+    std::vector<BatchTables> btabs;
     // options
     int64_t knn_margin = 32;
     int jacobi_fp64 = -1;
@@ -649,6 +657,277 @@ mecuco_status run_batched_lanes(mecuco_t h, const mecuco_dataset *sets, int nset
     return MECUCO_OK;
 }
 
+// ---- batched entry point, one launch per stage (BF16-mixed) ----------------
+// Every dataset's kNN work items come from one device table (KnnSet), every
+// estimator launch covers the points of all datasets through a segment table
+// (PatchSeg).  Datasets go in order of m, then N, descending, so that the
+// points of one estimator launch share the leading dimension of their rotated
+// patches with little padding.
+constexpr size_t BATCH_EST_BUDGET = (size_t)8 << 30;  // bytes of estimator chunk scratch
+constexpr int BATCH_TABLES_KEPT = 64;
+
+struct BatchChunk {
+    int64_t np;    // points (blocks) of the launches
+    int seg0, nseg;
+    int kmax;
+    int64_t ldy;   // leading dimension of the rotated patches (BF16 elements)
+    uint16_t *Y;
+};
+
+struct BatchPlan {
+    std::vector<int> order;       // table position -> dataset
+    std::vector<KnnSet> knn;      // table order (neighbour-list pointers left out)
+    std::vector<BatchChunk> chunks;
+    std::vector<PatchSeg> segs;   // output pointers left out
+    std::vector<SegRef> refs;     // dataset and first point of each segment
+    std::vector<BatchOut> outs;   // this call's outputs, table order
+    int64_t nrows = 0, nitems = 0;
+    int kcmax = 0, lmax = 0, kmax = 0;
+    bool any_copy = false;
+    size_t bytes = 0;             // workspace bytes
+};
+
+// Estimator scratch floats per point at leading dimension ldy and k.
+inline int64_t batch_point_floats(int64_t ldy, int k) { return 32 * ldy + 4LL * k * k + 3LL * k; }
+
+// Lay the batch out in the workspace at `base` (nullptr: sizes only).  The
+// neighbour lists of datasets without idx come first; the kNN scratch and the
+// estimator chunk scratch share what follows (the kNN stage is done before the
+// first estimator launch on the same stream).
+mecuco_status plan_batch(mecuco_t h, const mecuco_dataset *sets, int nsets, mecuco_dtype dt, int include_self,
+                         int pair, char *base, BatchPlan &p) {
+    p = BatchPlan();
+    p.order.resize(nsets);
+    std::iota(p.order.begin(), p.order.end(), 0);
+    std::stable_sort(p.order.begin(), p.order.end(), [&](int a, int b) {
+        if (sets[a].m != sets[b].m) return sets[a].m > sets[b].m;
+        return sets[a].N > sets[b].N;
+    });
+    Carver c(base, 0);
+    const int halves = knn_tc_halves();
+    const int qrows = knn_tc_item_rows(pair);
+    p.knn.resize(nsets);
+    p.outs.resize(nsets);
+    for (int t = 0; t < nsets; ++t) {
+        const mecuco_dataset &d = sets[p.order[t]];
+        p.outs[t].kappa = d.kappa;
+        p.outs[t].idx = d.idx ? d.idx : c.take<int32_t>((size_t)d.N * d.k);
+    }
+    const size_t after_idx = c.off;
+    for (int t = 0; t < nsets; ++t) {
+        const mecuco_dataset &d = sets[p.order[t]];
+        KnnSet &e = p.knn[t];
+        memset(&e, 0, sizeof(e));
+        e.X = d.X;
+        e.N = d.N;
+        e.m = d.m;
+        e.ld = d.ld;
+        e.k = d.k;
+        e.include_self = include_self;
+        e.kc = candidate_capacity(h, d.k);
+        e.kcl = std::min(e.kc, 64);
+        // one candidate split: the batch's query blocks fill the GPU
+        const int cap = 1024 / (halves * e.kcl);
+        e.nsplit = h->knn_splits > 0 ? std::min(h->knn_splits, cap) : 1;
+        while (e.nsplit > 1 && (d.N + e.nsplit - 1) / e.nsplit < e.kc) --e.nsplit;
+        e.lists = e.nsplit * halves;
+        const bool direct = dt == MECUCO_BF16 && d.ld % 8 == 0 && (reinterpret_cast<uintptr_t>(d.X) & 15) == 0;
+        e.ldb = direct ? d.ld : (d.m + 7) / 8 * 8;
+        e.norms = c.take<float>((size_t)d.N);
+        e.cand_d = c.take<float>((size_t)d.N * e.lists * e.kcl);
+        e.cand_i = c.take<int32_t>((size_t)d.N * e.lists * e.kcl);
+        e.flags = c.take<int32_t>((size_t)d.N);
+        e.xb = direct ? nullptr : (void *)c.take<uint16_t>((size_t)d.N * e.ldb);
+        e.item_begin = p.nitems;
+        e.row_begin = p.nrows;
+        p.nitems += (d.N + qrows - 1) / qrows * e.nsplit;
+        p.nrows += d.N;
+        p.kcmax = std::max(p.kcmax, e.kcl);
+        p.lmax = std::max(p.lmax, e.kcl * e.lists);
+        p.kmax = std::max(p.kmax, d.k);
+        p.any_copy = p.any_copy || !direct;
+        if (base && !knn_tc_make_maps(&e)) {
+            set_error_text("batched kNN: a dataset's operand cannot be described by a tensor map");
+            return MECUCO_ERR_INVALID_ARG;
+        }
+    }
+    const size_t knn_end = c.off;
+    // estimator chunks: greedy over the points in table order
+    const int64_t pt_cap = h->chunk_points > 0 ? h->chunk_points : ((int64_t)1 << 24);
+    size_t est_end = after_idx;
+    BatchChunk cur{0, 0, 0, 0, 0, nullptr};
+    auto close = [&]() {
+        if (cur.np == 0) return;
+        Carver e(base, after_idx);
+        EstBufs b;
+        est_scratch(e, cur.np, cur.kmax, &b, 0, cur.ldy);
+        est_end = std::max(est_end, e.off);
+        cur.Y = b.Y;
+        for (int i = cur.seg0; i < cur.seg0 + cur.nseg; ++i) {
+            PatchSeg &g = p.segs[i];
+            const size_t f = (size_t)g.first;
+            const size_t kk = (size_t)cur.kmax;
+            g.G = b.G + f * kk * kk;
+            g.R = b.R + f * kk;
+            g.Q = b.Q + f * kk * kk;
+            g.sig = b.sig + f * kk;
+            g.U = b.U + f * kk * kk;
+        }
+        p.chunks.push_back(cur);
+        cur = BatchChunk{0, (int)p.segs.size(), 0, 0, 0, nullptr};
+    };
+    for (int t = 0; t < nsets; ++t) {
+        const mecuco_dataset &d = sets[p.order[t]];
+        int64_t a = 0;
+        while (a < d.N) {
+            const int64_t ldy = cur.np ? cur.ldy : rot_ld(d.m);
+            const int kc = std::max(cur.kmax, d.k);
+            int64_t cap = (int64_t)(BATCH_EST_BUDGET / (sizeof(float) * (size_t)batch_point_floats(ldy, kc)));
+            cap = std::max<int64_t>(1, std::min(cap, pt_cap));
+            if (cur.np >= cap) { close(); continue; }
+            const int64_t take = std::min(d.N - a, cap - cur.np);
+            PatchSeg g{};
+            g.X = d.X;
+            g.N = d.N;
+            g.m = d.m;
+            g.ld = d.ld;
+            g.k = d.k;
+            g.first = (int)cur.np;
+            g.rowtab = h->tttab[d.k];
+            p.segs.push_back(g);
+            p.refs.push_back(SegRef{t, 0, a});
+            cur.ldy = ldy;
+            cur.kmax = kc;
+            cur.np += take;
+            ++cur.nseg;
+            a += take;
+        }
+    }
+    close();
+    p.bytes = std::max(knn_end, est_end);
+    return MECUCO_OK;
+}
+
+// The device copy of the plan's tables (KnnSet entries, the segments, their
+// references), reused when an earlier call built the same bytes: inputs,
+// workspace and sizes, not the outputs, which launch_batch_patch writes in
+// every call.
+mecuco_status batch_tables(mecuco_t h, const BatchPlan &p, cudaStream_t s, KnnSet **knn_dev, PatchSeg **seg_dev,
+                           SegRef **ref_dev) {
+    const size_t kb = align_up(sizeof(KnnSet) * p.knn.size(), 256);
+    const size_t sb = align_up(sizeof(PatchSeg) * p.segs.size(), 256);
+    std::vector<char> blob(kb + sb + sizeof(SegRef) * p.refs.size(), 0);
+    memcpy(blob.data(), p.knn.data(), sizeof(KnnSet) * p.knn.size());
+    memcpy(blob.data() + kb, p.segs.data(), sizeof(PatchSeg) * p.segs.size());
+    memcpy(blob.data() + kb + sb, p.refs.data(), sizeof(SegRef) * p.refs.size());
+    char *dev = nullptr;
+    for (size_t i = 0; i < h->btabs.size(); ++i) {
+        if (h->btabs[i].host == blob) {
+            dev = h->btabs[i].dev;
+            break;
+        }
+    }
+    if (!dev) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        CK(cudaStreamIsCapturing(s, &cs));
+        if (cs != cudaStreamCaptureStatusNone) {
+            set_error_text("batched call under stream capture needs a new device table: make one uncaptured call "
+                           "with the same datasets first");
+            return MECUCO_ERR_INVALID_ARG;
+        }
+        if ((int)h->btabs.size() >= BATCH_TABLES_KEPT) {
+            CK(cudaDeviceSynchronize());
+            cudaFree(h->btabs.front().dev);
+            h->btabs.erase(h->btabs.begin());
+        }
+        if (cudaMalloc(&dev, blob.size()) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return MECUCO_ERR_OOM;
+        }
+        cudaError_t e = cudaMemcpy(dev, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { cudaFree(dev); set_err("cudaMemcpy", e); return MECUCO_ERR_CUDA; }
+        h->btabs.push_back({std::move(blob), dev});
+    }
+    *knn_dev = reinterpret_cast<KnnSet *>(dev);
+    *seg_dev = reinterpret_cast<PatchSeg *>(dev + kb);
+    *ref_dev = reinterpret_cast<SegRef *>(dev + kb + sb);
+    return MECUCO_OK;
+}
+
+mecuco_status run_batched_persistent(mecuco_t h, const mecuco_dataset *sets, int nsets, mecuco_dtype dt,
+                                     int include_self, mecuco_variant var, cudaStream_t s,
+                                     const mecuco_batch_tuning &tn) {
+    mecuco_status st;
+    for (int i = 0; i < nsets; ++i)
+        if ((st = ensure_rotated(h, sets[i].k)) != MECUCO_OK) return st;
+    BatchPlan p;
+    if ((st = plan_batch(h, sets, nsets, dt, include_self, tn.knn_pair, nullptr, p)) != MECUCO_OK) return st;
+    if ((st = ensure(h->bws, h->bws_bytes, p.bytes, h->ws_cap)) != MECUCO_OK) return st;
+    if ((st = plan_batch(h, sets, nsets, dt, include_self, tn.knn_pair, h->bws, p)) != MECUCO_OK) return st;
+    KnnSet *kt = nullptr;
+    PatchSeg *sg = nullptr;
+    SegRef *refs = nullptr;
+    if ((st = batch_tables(h, p, s, &kt, &sg, &refs)) != MECUCO_OK) return st;
+    CK(launch_batch_patch(kt, nsets, sg, refs, (int)p.segs.size(), p.outs.data(), s));
+    h->launches += (nsets + BATCH_PATCH_SETS - 1) / BATCH_PATCH_SETS;
+    // kNN of every row of every dataset: one launch per stage
+    LAUNCH(h, MECUCO_STAGE_ROWNORM, s, launch_rownorm_batch(kt, nsets, p.nrows, dt, s));
+    if (p.any_copy) {
+        CK(launch_to_bf16_batch(kt, nsets, p.nrows, dt, s));
+        ++h->launches;
+    }
+    LAUNCH(h, MECUCO_STAGE_KNN_SEARCH, s,
+           launch_knn_tc_batch(kt, nsets, p.nitems, p.kcmax, tn.knn_pair, h->wait_limit, h->ctr, s));
+    LAUNCH(h, MECUCO_STAGE_KNN_RERANK, s, launch_knn_rerank_batch(kt, nsets, p.nrows, p.lmax, dt, h->ctr, s));
+    LAUNCH(h, MECUCO_STAGE_KNN_FALLBACK, s, launch_knn_fallback_batch(kt, nsets, p.nrows, p.kmax, dt, h->ctr, s));
+    h->knn_rows += p.nrows;
+    // estimator over the points of all datasets, chunk by chunk
+    const int fp64 = h->jacobi_fp64 >= 0 ? h->jacobi_fp64 : 1;
+    const int haar = var == MECUCO_FAST_HAAR ? 1 : 0;
+    PatchSeg none{};
+    for (const BatchChunk &ch : p.chunks) {
+        const PatchSeg *tab = sg + ch.seg0;
+        LAUNCH(h, MECUCO_STAGE_GRAM, s, launch_gram_tc(dt, none, tab, ch.nseg, ch.np, haar, h->wait_limit, h->ctr, s));
+        LAUNCH(h, MECUCO_STAGE_JACOBI, s,
+               launch_jacobi_seg(none, tab, ch.nseg, ch.kmax, ch.np, fp64, h->jacobi_max_sweeps, h->ctr, s,
+                                 kJacobiPreLoose));
+        if (fp64 == 1 || fp64 == 3) ++h->launches;
+        LAUNCH(h, MECUCO_STAGE_ROTATE, s,
+               launch_rotate_tc(dt, none, tab, ch.nseg, ch.np, ch.Y, ch.ldy, h->wait_limit, h->ctr, s));
+        LAUNCH(h, MECUCO_STAGE_MOMENTS, s,
+               launch_tthird_tc(none, tab, ch.nseg, ch.kmax, ch.np, ch.Y, ch.ldy, (int)var, tn.tt_slots, tn.tt_ctas,
+                                h->wait_limit, h->ctr, s));
+    }
+    return MECUCO_OK;
+}
+
+// The configuration a batched call runs with: the tuned one for its
+// signature, else the context's options.
+mecuco_batch_tuning batch_config(mecuco_t h, const mecuco_dataset *sets, int nsets, mecuco_dtype dt,
+                                 mecuco_precision prec) {
+    auto it = h->tuned.find(batch_signature(sets, nsets, dt, prec));
+    if (it != h->tuned.end()) return it->second;
+    mecuco_batch_tuning t{};
+    t.lanes = h->batch_lanes;
+    int64_t maxn = 0;
+    for (int i = 0; i < nsets; ++i) maxn = std::max(maxn, sets[i].N);
+    t.knn_pair = h->knn_pair > 0 || (h->knn_pair < 0 && maxn >= KNN_PAIR_MIN_N) ? 1 : 0;
+    t.tt_ctas = h->tt_ctas;
+    t.tt_slots = h->tt_slots;
+    return t;
+}
+
+bool batch_is_persistent(mecuco_t h, mecuco_precision prec) {
+    return prec == MECUCO_PREC_BF16_MIXED && h->batch_persistent;
+}
+
+mecuco_status run_batch_call(mecuco_t h, const mecuco_dataset *sets, int nsets, mecuco_dtype dt, int include_self,
+                             mecuco_variant var, mecuco_precision prec, cudaStream_t s,
+                             const mecuco_batch_tuning &tn) {
+    if (batch_is_persistent(h, prec)) return run_batched_persistent(h, sets, nsets, dt, include_self, var, s, tn);
+    return run_batched(h, sets, nsets, dt, include_self, var, prec, s, tn.lanes);
+}
+
 mecuco_status check_batch(mecuco_t h, const mecuco_dataset *sets, int nsets, mecuco_dtype dt, int include_self,
                           mecuco_variant var, mecuco_precision prec) {
     if (!h || !sets || nsets < 1) return MECUCO_ERR_INVALID_ARG;
@@ -733,6 +1012,7 @@ mecuco_status mecuco_destroy(mecuco_t h) {
         if (h->lane_event[i]) cudaEventDestroy(h->lane_event[i]);
     }
     if (h->fork_event) cudaEventDestroy(h->fork_event);
+    for (auto &bt : h->btabs) cudaFree(bt.dev);
     delete h;
     return MECUCO_OK;
 }
@@ -799,6 +1079,10 @@ mecuco_status mecuco_set_option(mecuco_t h, mecuco_option opt, int64_t v) {
         case MECUCO_OPT_BATCH_LANES:
             if (v < 1 || v > 32) return MECUCO_ERR_INVALID_ARG;
             h->batch_lanes = (int)v;
+            break;
+        case MECUCO_OPT_BATCH_PERSISTENT:
+            if (v != 0 && v != 1) return MECUCO_ERR_INVALID_ARG;
+            h->batch_persistent = (int)v;
             break;
         default: return MECUCO_ERR_INVALID_ARG;
     }
@@ -1068,46 +1352,77 @@ mecuco_status mecuco_curvature_batched(mecuco_t h, const mecuco_dataset *sets, i
     if (st != MECUCO_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = begin_call(h, s)) != MECUCO_OK) return st;
-    auto it = h->tuned_lanes.find(batch_signature(sets, nsets, dt, prec));
-    const int lanes = it != h->tuned_lanes.end() ? it->second : h->batch_lanes;
-    return run_batched(h, sets, nsets, dt, include_self, var, prec, s, lanes);
+    return run_batch_call(h, sets, nsets, dt, include_self, var, prec, s, batch_config(h, sets, nsets, dt, prec));
 }
 
 mecuco_status mecuco_autotune_batched(mecuco_t h, const mecuco_dataset *sets, int nsets, mecuco_dtype dt,
                                       int include_self, mecuco_variant var, mecuco_precision prec, void *stream,
-                                      int *lanes_out) {
+                                      mecuco_batch_tuning *out) {
     mecuco_status st = check_batch(h, sets, nsets, dt, include_self, var, prec);
     if (st != MECUCO_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    int best = 1;
-    float best_ms = 0.f;
-    const int cand[] = {32, 16, 8, 4, 2, 1};  // the largest first: it sizes the workspace once
     bool warmed = false;
-    for (int L : cand) {
-        if (L > nsets && L != 1) continue;
-        if ((st = begin_call(h, s)) != MECUCO_OK) break;
+    // one timed call (after a warm-up the first time) in configuration t
+    auto timed = [&](const mecuco_batch_tuning &t, float *ms) -> mecuco_status {
+        mecuco_status r;
+        if ((r = begin_call(h, s)) != MECUCO_OK) return r;
         if (!warmed) {
-            if ((st = run_batched(h, sets, nsets, dt, include_self, var, prec, s, L)) != MECUCO_OK) break;
+            if ((r = run_batch_call(h, sets, nsets, dt, include_self, var, prec, s, t)) != MECUCO_OK) return r;
             warmed = true;
         }
-        if (cudaEventRecord(e0, s) != cudaSuccess) { st = MECUCO_ERR_CUDA; break; }
-        if ((st = run_batched(h, sets, nsets, dt, include_self, var, prec, s, L)) != MECUCO_OK) break;
-        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
-            st = MECUCO_ERR_CUDA;
-            break;
-        }
+        if (cudaEventRecord(e0, s) != cudaSuccess) return MECUCO_ERR_CUDA;
+        if ((r = run_batch_call(h, sets, nsets, dt, include_self, var, prec, s, t)) != MECUCO_OK) return r;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return MECUCO_ERR_CUDA;
+        if (cudaEventElapsedTime(ms, e0, e1) != cudaSuccess) return MECUCO_ERR_CUDA;
+        return MECUCO_OK;
+    };
+    const auto sig = batch_signature(sets, nsets, dt, prec);
+    h->tuned.erase(sig);
+    mecuco_batch_tuning best = batch_config(h, sets, nsets, dt, prec);
+    best.ms = 0.f;
+    auto consider = [&](mecuco_batch_tuning t) -> mecuco_status {
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (best_ms == 0.f || ms < best_ms) { best_ms = ms; best = L; }
+        mecuco_status r = timed(t, &ms);
+        if (r != MECUCO_OK) return r;
+        if (best.ms == 0.f || ms < best.ms) {
+            best = t;
+            best.ms = ms;
+        }
+        return MECUCO_OK;
+    };
+    if (batch_is_persistent(h, prec)) {
+        best.lanes = 1;
+        // the kNN tile form, then the third-moment pass's patches per SM and
+        // TMEM slots, each with the other stage at its best so far
+        for (int pair : {0, 1}) {
+            mecuco_batch_tuning t = best;
+            t.knn_pair = pair;
+            if ((st = consider(t)) != MECUCO_OK) break;
+        }
+        const int tt[4][2] = {{2, 2}, {2, 4}, {1, 4}, {1, 8}};
+        for (int i = 0; i < 4 && st == MECUCO_OK; ++i) {
+            mecuco_batch_tuning t = best;
+            t.tt_ctas = tt[i][0];
+            t.tt_slots = tt[i][1];
+            if (t.tt_ctas == best.tt_ctas && t.tt_slots == best.tt_slots && best.ms > 0.f) continue;
+            st = consider(t);
+        }
+    } else {
+        for (int L : {32, 16, 8, 4, 2, 1}) {  // the largest first: it sizes the workspace once
+            if (L > nsets && L != 1) continue;
+            mecuco_batch_tuning t = best;
+            t.lanes = L;
+            if ((st = consider(t)) != MECUCO_OK) break;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != MECUCO_OK) return st;
-    h->tuned_lanes[batch_signature(sets, nsets, dt, prec)] = best;
-    if (lanes_out) *lanes_out = best;
+    h->tuned[sig] = best;
+    if (out) *out = best;
     return MECUCO_OK;
 }
 

@@ -3,6 +3,7 @@
 
 #include <math.h>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -46,6 +47,60 @@ size_t knn_tc_smem_bytes(int kc);
 // Candidate lists the tensor-core search leaves per row and split (the epilogue's
 // column halves); list h of row r, split s starts at ((r nsplit + s) halves + h) kc.
 int knn_tc_halves();
+// One dataset of a batched kNN (a device table of them, sorted by first
+// work item / first row).  The tensor maps describe the BF16 operand (xb when
+// a copy is made, else X) with TMA boxes of the search; kcl is each list's
+// capacity, lists = nsplit * knn_tc_halves() lists per row.
+struct alignas(64) KnnSet {
+    CUtensorMap map_a, map_b;
+    const void *X;     // the dataset in the call's dtype (row norms, re-rank, fallback)
+    void *xb;          // BF16 copy (FP32 inputs), or NULL when X is BF16 with ldb = ld
+    int64_t N, m, ld, ldb;
+    float *norms;      // N
+    float *cand_d;     // N x lists x kcl
+    int32_t *cand_i;
+    int32_t *flags;    // N
+    int32_t *idx;      // N x k, the neighbour lists
+    int k, kc, kcl, nsplit, lists, include_self;
+    int64_t item_begin;  // first search work item (one query block x one candidate split)
+    int64_t row_begin;   // first row in the batch's row order
+};
+// Fill the two tensor maps of a table entry (host).
+bool knn_tc_make_maps(KnnSet *d);
+// The tensor-core search over every dataset of a batch in one persistent launch:
+// nitems work items in all (the sum of each set's query blocks x splits, query
+// blocks of knn_tc_item_rows(pair) rows), kcmax the largest list capacity.
+// pair != 0: CTA pairs (256 x 256 two-SM MMAs), else one CTA per SM.
+int knn_tc_item_rows(int pair);
+cudaError_t launch_knn_tc_batch(const KnnSet *sets, int nsets, int64_t nitems, int kcmax, int pair,
+                                long long wait_limit, DevCounters *ctr, cudaStream_t s);
+// Per-call output pointers of one dataset of a batch (table order), and the
+// dataset and first point of each estimator segment.  launch_batch_patch
+// writes them into the device tables (KnnSet.idx; PatchSeg.kappa and .idx at
+// the segment's first point) through kernel parameters, BATCH_PATCH_SETS
+// datasets per launch, so a captured call carries its own outputs.
+struct BatchOut {
+    float *kappa;
+    int32_t *idx;
+};
+struct SegRef {
+    int32_t set;
+    int32_t pad;
+    int64_t a;
+};
+constexpr int BATCH_PATCH_SETS = 1024;
+cudaError_t launch_batch_patch(KnnSet *sets, int nsets, PatchSeg *segs, const SegRef *refs, int nsegs,
+                               const BatchOut *outs, cudaStream_t s);
+// Row norms, BF16 copies, exact re-rank and fallback over every row of a
+// batch (table rows sorted by row_begin, nrows rows in all); the re-rank's
+// shared memory is sized for lmax = the largest kcl * lists.
+cudaError_t launch_rownorm_batch(const KnnSet *sets, int nsets, int64_t nrows, mecuco_dtype dt, cudaStream_t s);
+cudaError_t launch_to_bf16_batch(const KnnSet *sets, int nsets, int64_t nrows, mecuco_dtype dt, cudaStream_t s);
+cudaError_t launch_knn_rerank_batch(const KnnSet *sets, int nsets, int64_t nrows, int lmax, mecuco_dtype dt,
+                                    DevCounters *ctr, cudaStream_t s);
+cudaError_t launch_knn_fallback_batch(const KnnSet *sets, int nsets, int64_t nrows, int kmax, mecuco_dtype dt,
+                                      DevCounters *ctr, cudaStream_t s);
+
 // BF16 copy of X (round to nearest even) with leading dimension ldb >= m.
 cudaError_t launch_to_bf16(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, void *Y,
                            int64_t ldb, cudaStream_t s);

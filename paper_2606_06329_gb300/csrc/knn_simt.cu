@@ -15,6 +15,17 @@
 
 namespace mecuco {
 
+// The table entry of batch row `row` (entries sorted by row_begin).
+__device__ __forceinline__ const KnnSet &find_set_row(const KnnSet *sets, int nsets, int64_t row) {
+    int lo = 0, hi = nsets - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sets[mid].row_begin <= row) lo = mid;
+        else hi = mid - 1;
+    }
+    return sets[lo];
+}
+
 template <typename T>
 __global__ void rownorm_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld,
                                float *__restrict__ out) {
@@ -39,6 +50,56 @@ cudaError_t launch_rownorm(const void *X, mecuco_dtype dt, int64_t N, int64_t m,
         rownorm_kernel<<<grid, block, 0, s>>>((const __nv_bfloat16 *)X, N, m, ld, norms);
     else
         rownorm_kernel<<<grid, block, 0, s>>>((const float *)X, N, m, ld, norms);
+    return cudaGetLastError();
+}
+
+// Row norms of every row of a batch: one warp per row, each row's dataset from
+// the table.
+template <typename T>
+__global__ void rownorm_batch_kernel(const KnnSet *__restrict__ sets, int nsets, int64_t nrows) {
+    const int64_t gr = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (gr >= nrows) return;
+    const KnnSet &d = find_set_row(sets, nsets, gr);
+    const int64_t row = gr - d.row_begin;
+    const T *x = static_cast<const T *>(d.X) + row * d.ld;
+    float acc = 0.f;
+    for (int64_t a = lane; a < d.m; a += 32) {
+        const float v = load_elem(x + a);
+        acc = fmaf(v, v, acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) d.norms[row] = acc;
+}
+
+cudaError_t launch_rownorm_batch(const KnnSet *sets, int nsets, int64_t nrows, mecuco_dtype dt, cudaStream_t s) {
+    if (nrows <= 0) return cudaSuccess;
+    dim3 block(256), grid((unsigned)((nrows + 7) / 8));
+    if (dt == MECUCO_BF16) rownorm_batch_kernel<__nv_bfloat16><<<grid, block, 0, s>>>(sets, nsets, nrows);
+    else rownorm_batch_kernel<float><<<grid, block, 0, s>>>(sets, nsets, nrows);
+    return cudaGetLastError();
+}
+
+// BF16 copies (round to nearest even, zero past m) of the rows of every
+// dataset that has one (xb): one warp per row, coalesced along the row.
+template <typename T>
+__global__ void to_bf16_batch_kernel(const KnnSet *__restrict__ sets, int nsets, int64_t nrows) {
+    const int64_t gr = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (gr >= nrows) return;
+    const KnnSet &d = find_set_row(sets, nsets, gr);
+    if (!d.xb) return;
+    const int64_t row = gr - d.row_begin;
+    const T *x = static_cast<const T *>(d.X) + row * d.ld;
+    __nv_bfloat16 *y = static_cast<__nv_bfloat16 *>(d.xb) + row * d.ldb;
+    for (int64_t a = lane; a < d.ldb; a += 32) y[a] = __float2bfloat16_rn(a < d.m ? load_elem(x + a) : 0.f);
+}
+
+cudaError_t launch_to_bf16_batch(const KnnSet *sets, int nsets, int64_t nrows, mecuco_dtype dt, cudaStream_t s) {
+    if (nrows <= 0) return cudaSuccess;
+    dim3 block(256), grid((unsigned)((nrows + 7) / 8));
+    if (dt == MECUCO_BF16) to_bf16_batch_kernel<__nv_bfloat16><<<grid, block, 0, s>>>(sets, nsets, nrows);
+    else to_bf16_batch_kernel<float><<<grid, block, 0, s>>>(sets, nsets, nrows);
     return cudaGetLastError();
 }
 
@@ -206,21 +267,49 @@ cudaError_t launch_knn_simt(const void *X, mecuco_dtype dt, int64_t N, int64_t m
 constexpr int RR_WARPS = 4;
 constexpr int RR_MAXL = 1024;
 
-template <typename T>
+template <typename T, bool BATCH>
 __global__ void __launch_bounds__(RR_WARPS * 32)
-knn_rerank_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld,
-                  const float *__restrict__ norms, int64_t q0, int64_t nq, int kc, int nsplit, int k,
-                  const float *__restrict__ cand_d, const int32_t *__restrict__ cand_i,
-                  int32_t *__restrict__ idx_out, float *__restrict__ dist_out,
-                  int32_t *__restrict__ flags, DevCounters *ctr) {
+knn_rerank_kernel(const T *__restrict__ X_, int64_t N_, int64_t m_, int64_t ld_,
+                  const float *__restrict__ norms_, int64_t q0_, int64_t nq, int kc_, int nsplit_, int k_,
+                  const float *__restrict__ cand_d_, const int32_t *__restrict__ cand_i_,
+                  int32_t *__restrict__ idx_out_, float *__restrict__ dist_out_,
+                  int32_t *__restrict__ flags_, DevCounters *ctr, const KnnSet *__restrict__ sets, int nsets,
+                  int lmax) {
     extern __shared__ float rsm[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int64_t qi = (int64_t)blockIdx.x * RR_WARPS + w;  // the launch's row (the batch's row when batched)
+    if (qi >= nq) return;
+    // the row's dataset: the arguments, or its entry of a batch's table
+    const T *X = X_;
+    int64_t N = N_, m = m_, ld = ld_, q0 = q0_;
+    const float *norms = norms_, *cand_d = cand_d_;
+    const int32_t *cand_i = cand_i_;
+    int32_t *idx_out = idx_out_, *flags = flags_;
+    float *dist_out = dist_out_;
+    int kc = kc_, nsplit = nsplit_, k = k_;
+    if constexpr (BATCH) {
+        const KnnSet &d = find_set_row(sets, nsets, qi);
+        qi -= d.row_begin;
+        X = static_cast<const T *>(d.X);
+        N = d.N;
+        m = d.m;
+        ld = d.ld;
+        q0 = 0;
+        norms = d.norms;
+        cand_d = d.cand_d;
+        cand_i = d.cand_i;
+        idx_out = d.idx;
+        flags = d.flags;
+        dist_out = nullptr;
+        kc = d.kcl;
+        nsplit = d.lists;
+        k = d.k;
+    }
     const int L = kc * nsplit;
-    float *hi = rsm + (size_t)w * L * 3;
+    const int LS = BATCH ? lmax : L;  // per-warp shared-memory stride
+    float *hi = rsm + (size_t)w * LS * 3;
     float *lo = hi + L;
     int *ci = reinterpret_cast<int *>(lo + L);
-    const int64_t qi = (int64_t)blockIdx.x * RR_WARPS + w;
-    if (qi >= nq) return;
     const int64_t q = q0 + qi;
     const float *cd = cand_d + qi * (int64_t)L;
     const int32_t *cidx = cand_i + qi * (int64_t)L;
@@ -349,19 +438,19 @@ cudaError_t launch_knn_rerank(const void *X, mecuco_dtype dt, int64_t N, int64_t
     dim3 grid((unsigned)((nq + RR_WARPS - 1) / RR_WARPS)), block(RR_WARPS * 32);
     cudaError_t e;
     if (dt == MECUCO_BF16) {
-        e = cudaFuncSetAttribute(knn_rerank_kernel<__nv_bfloat16>,
+        e = cudaFuncSetAttribute(knn_rerank_kernel<__nv_bfloat16, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        knn_rerank_kernel<<<grid, block, smem, s>>>((const __nv_bfloat16 *)X, N, m, ld, norms, q0, nq,
-                                                    kc, nsplit, k, cand_d, cand_i, idx_out, dist_out,
-                                                    flags, ctr);
+        knn_rerank_kernel<__nv_bfloat16, false><<<grid, block, smem, s>>>((const __nv_bfloat16 *)X, N, m, ld, norms,
+                                                                          q0, nq, kc, nsplit, k, cand_d, cand_i,
+                                                                          idx_out, dist_out, flags, ctr, nullptr, 0, 0);
     } else {
-        e = cudaFuncSetAttribute(knn_rerank_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(knn_rerank_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
-        knn_rerank_kernel<<<grid, block, smem, s>>>((const float *)X, N, m, ld, norms, q0, nq, kc,
-                                                    nsplit, k, cand_d, cand_i, idx_out, dist_out, flags,
-                                                    ctr);
+        knn_rerank_kernel<float, false><<<grid, block, smem, s>>>((const float *)X, N, m, ld, norms, q0, nq, kc,
+                                                                  nsplit, k, cand_d, cand_i, idx_out, dist_out, flags,
+                                                                  ctr, nullptr, 0, 0);
     }
     return cudaGetLastError();
 }
@@ -374,22 +463,45 @@ cudaError_t launch_knn_rerank(const void *X, mecuco_dtype dt, int64_t N, int64_t
 // ---------------------------------------------------------------------------
 constexpr int FB_WARPS = 8;
 
-template <typename T>
+template <typename T, bool BATCH>
 __global__ void __launch_bounds__(FB_WARPS * 32)
-knn_fallback_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, int64_t q0,
-                    int64_t nq, int k, int include_self, const int32_t *__restrict__ flags,
-                    int32_t *__restrict__ idx_out, float *__restrict__ dist_out, DevCounters *ctr) {
+knn_fallback_kernel(const T *__restrict__ X_, int64_t N_, int64_t m_, int64_t ld_, int64_t q0_,
+                    int64_t nq, int k_, int include_self_, const int32_t *__restrict__ flags_,
+                    int32_t *__restrict__ idx_out_, float *__restrict__ dist_out_, DevCounters *ctr,
+                    const KnnSet *__restrict__ sets, int nsets, int kmax) {
     extern __shared__ float fsm[];
-    float *bh = fsm;                       // [FB_WARPS][k]
-    float *bl = bh + FB_WARPS * k;         // [FB_WARPS][k]
-    int *bi = reinterpret_cast<int *>(bl + FB_WARPS * k);
+    const int KS = BATCH ? kmax : k_;      // shared-memory stride of one warp's list
+    float *bh = fsm;                       // [FB_WARPS][KS]
+    float *bl = bh + FB_WARPS * KS;        // [FB_WARPS][KS]
+    int *bi = reinterpret_cast<int *>(bl + FB_WARPS * KS);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int64_t qi = blockIdx.x; qi < nq; qi += gridDim.x) {
+    for (int64_t gi = blockIdx.x; gi < nq; gi += gridDim.x) {
+        // the row's dataset: the arguments, or its entry of a batch's table
+        const T *X = X_;
+        int64_t N = N_, m = m_, ld = ld_, q0 = q0_, qi = gi;
+        const int32_t *flags = flags_;
+        int32_t *idx_out = idx_out_;
+        float *dist_out = dist_out_;
+        int k = k_, include_self = include_self_;
+        if constexpr (BATCH) {
+            const KnnSet &d = find_set_row(sets, nsets, gi);
+            qi = gi - d.row_begin;
+            X = static_cast<const T *>(d.X);
+            N = d.N;
+            m = d.m;
+            ld = d.ld;
+            q0 = 0;
+            flags = d.flags;
+            idx_out = d.idx;
+            dist_out = nullptr;
+            k = d.k;
+            include_self = d.include_self;
+        }
         if (flags[qi] == 0) continue;  // uniform across the CTA
         const int64_t q = q0 + qi;
         const T *xq = X + q * ld;
-        float *mh = bh + w * k, *ml = bl + w * k;
-        int *mi = bi + w * k;
+        float *mh = bh + w * KS, *ml = bl + w * KS;
+        int *mi = bi + w * KS;
         if (lane == 0)
             for (int s = 0; s < k; ++s) { mh[s] = INFINITY; ml[s] = 0.f; mi[s] = 0x7fffffff; }
         __syncwarp();
@@ -411,12 +523,12 @@ knn_fallback_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, i
         }
         __syncthreads();
         // merge: rank every entry among all FB_WARPS * k entries
-        for (int e = threadIdx.x; e < FB_WARPS * k; e += blockDim.x) {
-            if (bi[e] == 0x7fffffff) continue;
+        for (int e = threadIdx.x; e < FB_WARPS * KS; e += blockDim.x) {
+            if (e % KS >= k || bi[e] == 0x7fffffff) continue;
             ff me{bh[e], bl[e]};
             int rank = 0;
-            for (int o = 0; o < FB_WARPS * k; ++o)
-                if (bi[o] != 0x7fffffff && ff_less(ff{bh[o], bl[o]}, bi[o], me, bi[e])) ++rank;
+            for (int o = 0; o < FB_WARPS * KS; ++o)
+                if (o % KS < k && bi[o] != 0x7fffffff && ff_less(ff{bh[o], bl[o]}, bi[o], me, bi[e])) ++rank;
             if (rank < k) {
                 idx_out[qi * k + rank] = bi[e];
                 if (dist_out) dist_out[qi * k + rank] = me.hi + me.lo;
@@ -434,12 +546,51 @@ cudaError_t launch_knn_fallback(const void *X, mecuco_dtype dt, int64_t N, int64
     size_t smem = (size_t)FB_WARPS * k * 3 * sizeof(float);
     unsigned grid = (unsigned)(nq < 4096 ? nq : 4096);
     if (dt == MECUCO_BF16)
-        knn_fallback_kernel<<<grid, FB_WARPS * 32, smem, s>>>((const __nv_bfloat16 *)X, N, m, ld, q0, nq,
-                                                              k, include_self, flags, idx_out, dist_out,
-                                                              ctr);
+        knn_fallback_kernel<__nv_bfloat16, false><<<grid, FB_WARPS * 32, smem, s>>>(
+            (const __nv_bfloat16 *)X, N, m, ld, q0, nq, k, include_self, flags, idx_out, dist_out, ctr, nullptr, 0, 0);
     else
-        knn_fallback_kernel<<<grid, FB_WARPS * 32, smem, s>>>((const float *)X, N, m, ld, q0, nq, k,
-                                                              include_self, flags, idx_out, dist_out, ctr);
+        knn_fallback_kernel<float, false><<<grid, FB_WARPS * 32, smem, s>>>(
+            (const float *)X, N, m, ld, q0, nq, k, include_self, flags, idx_out, dist_out, ctr, nullptr, 0, 0);
+    return cudaGetLastError();
+}
+
+// Batched forms: the rows of every dataset of a table, one launch.
+cudaError_t launch_knn_rerank_batch(const KnnSet *sets, int nsets, int64_t nrows, int lmax, mecuco_dtype dt,
+                                    DevCounters *ctr, cudaStream_t s) {
+    if (nrows <= 0) return cudaSuccess;
+    if (lmax > RR_MAXL) return cudaErrorInvalidValue;
+    size_t smem = (size_t)RR_WARPS * lmax * 3 * sizeof(float);
+    dim3 grid((unsigned)((nrows + RR_WARPS - 1) / RR_WARPS)), block(RR_WARPS * 32);
+    cudaError_t e;
+    if (dt == MECUCO_BF16) {
+        e = cudaFuncSetAttribute(knn_rerank_kernel<__nv_bfloat16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        knn_rerank_kernel<__nv_bfloat16, true><<<grid, block, smem, s>>>(nullptr, 0, 0, 0, nullptr, 0, nrows, 0, 0, 0,
+                                                                         nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                                         ctr, sets, nsets, lmax);
+    } else {
+        e = cudaFuncSetAttribute(knn_rerank_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        knn_rerank_kernel<float, true><<<grid, block, smem, s>>>(nullptr, 0, 0, 0, nullptr, 0, nrows, 0, 0, 0, nullptr,
+                                                                 nullptr, nullptr, nullptr, nullptr, ctr, sets, nsets,
+                                                                 lmax);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_knn_fallback_batch(const KnnSet *sets, int nsets, int64_t nrows, int kmax, mecuco_dtype dt,
+                                      DevCounters *ctr, cudaStream_t s) {
+    if (nrows <= 0) return cudaSuccess;
+    size_t smem = (size_t)FB_WARPS * kmax * 3 * sizeof(float);
+    unsigned grid = (unsigned)(nrows < 4096 ? nrows : 4096);
+    if (dt == MECUCO_BF16)
+        knn_fallback_kernel<__nv_bfloat16, true><<<grid, FB_WARPS * 32, smem, s>>>(
+            nullptr, 0, 0, 0, 0, nrows, 0, 0, nullptr, nullptr, nullptr, ctr, sets, nsets, kmax);
+    else
+        knn_fallback_kernel<float, true><<<grid, FB_WARPS * 32, smem, s>>>(
+            nullptr, 0, 0, 0, 0, nrows, 0, 0, nullptr, nullptr, nullptr, ctr, sets, nsets, kmax);
     return cudaGetLastError();
 }
 

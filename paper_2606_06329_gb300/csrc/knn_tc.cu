@@ -38,6 +38,7 @@
 // always use WAIT_LIMIT, since the copies and MMAs they wait for complete.
 #include <cudaTypedefs.h>
 #include <math.h>
+#include <string.h>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -134,6 +135,18 @@ struct KCfg {
 };
 static_assert(KCfg<false>::NST * KCfg<false>::STAGE == KCfg<true>::NST * KCfg<true>::STAGE, "same ring size");
 
+// Geometry of one work item: query block, candidate split and the operand's
+// description (a single launch: the kernel's arguments; a batched launch: the
+// item's dataset in the device table).
+struct ItemGeo {
+    const CUtensorMap *ma, *mb;
+    const float *norms;
+    float *cand_d;
+    int32_t *cand_i;
+    int64_t N, q0, qend, qb, cbeg, cend;
+    int ntiles, nkb, split, nsplit, kc, include_self;
+};
+
 struct TcShared {
     uint64_t full[MAX_NSTAGE];
     uint64_t empty[MAX_NSTAGE];
@@ -144,12 +157,12 @@ struct TcShared {
 };
 }  // namespace
 
-template <bool PAIR>
+template <bool PAIR, bool BATCH>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, int64_t N,
               int64_t m, const float *__restrict__ norms, int64_t q0, int64_t nq, int kc, int nsplit,
               int include_self, float *__restrict__ cand_d, int32_t *__restrict__ cand_i, long long wait_limit,
-              DevCounters *ctr) {
+              DevCounters *ctr, const KnnSet *__restrict__ sets, int nsets, int64_t nitems_all) {
     // Persistent: CTA (pair) b takes work items b, b + G, b + 2G, ... (G CTAs or
     // pairs), item = (query block item / nsplit, candidate split item % nsplit).
     // All start their items together and every item has the same number of
@@ -168,11 +181,56 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = PAIR ? tc::cluster_ctarank() : 0u;
-    const int64_t qend = q0 + nq;
-    const int64_t nitems = ((nq + C::QROWS - 1) / C::QROWS) * nsplit;
+    const int64_t nitems = BATCH ? nitems_all : ((nq + C::QROWS - 1) / C::QROWS) * nsplit;
     const int64_t first = PAIR ? blockIdx.x / 2 : blockIdx.x, stride = PAIR ? gridDim.x / 2 : gridDim.x;
-    const int64_t per = (N + nsplit - 1) / nsplit;
-    const int nkb = (int)((m + TBK - 1) / TBK);
+    // a batched launch reads each item's dataset from the table (items of a
+    // dataset are consecutive; the table is sorted by first item)
+    auto geo = [&](int64_t item) {
+        ItemGeo g;
+        int64_t li = item;
+        if constexpr (BATCH) {
+            int lo = 0, hi = nsets - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (sets[mid].item_begin <= item) lo = mid;
+                else hi = mid - 1;
+            }
+            const KnnSet &d = sets[lo];
+            li = item - d.item_begin;
+            g.ma = &d.map_a;
+            g.mb = &d.map_b;
+            g.norms = d.norms;
+            g.cand_d = d.cand_d;
+            g.cand_i = d.cand_i;
+            g.N = d.N;
+            g.q0 = 0;
+            g.qend = d.N;
+            g.nsplit = d.nsplit;
+            g.kc = d.kcl;
+            g.nkb = (int)((d.m + TBK - 1) / TBK);
+            g.include_self = d.include_self;
+        } else {
+            g.ma = &map_a;
+            g.mb = &map_b;
+            g.norms = norms;
+            g.cand_d = cand_d;
+            g.cand_i = cand_i;
+            g.N = N;
+            g.q0 = q0;
+            g.qend = q0 + nq;
+            g.nsplit = nsplit;
+            g.kc = kc;
+            g.nkb = (int)((m + TBK - 1) / TBK);
+            g.include_self = include_self;
+        }
+        const int64_t per = (g.N + g.nsplit - 1) / g.nsplit;
+        g.split = (int)(li % g.nsplit);
+        g.qb = g.q0 + (li / g.nsplit) * C::QROWS;
+        g.cbeg = (int64_t)g.split * per;
+        g.cend = min(g.N, g.cbeg + per);
+        g.ntiles = g.cend > g.cbeg ? (int)((g.cend - g.cbeg + TBN - 1) / TBN) : 0;
+        return g;
+    };
     volatile int *abort_flag = &sh->abort;
     __shared__ int never;  // a flag that stays 0: drain waits are bounded by time only
 
@@ -192,8 +250,10 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
         sh->abort = (!PAIR && (*(volatile unsigned *)&ctr->status & DEV_TIMEOUT)) ? 1 : 0;
         never = 0;
         tc::fence_mbar_init();
-        tc::prefetch_tmap(&map_a);
-        tc::prefetch_tmap(&map_b);
+        if constexpr (!BATCH) {
+            tc::prefetch_tmap(&map_a);
+            tc::prefetch_tmap(&map_b);
+        }
     }
     if (warp == 1) {
         if constexpr (PAIR) {
@@ -232,25 +292,34 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
             // pair: both CTAs' loads complete on the even CTA's barrier, which
             // expects the bytes of both
             const uint32_t pfull0 = PAIR ? tc::mapa(full0, 0) : 0u;
+            const CUtensorMap *last_map = nullptr;
             for (int64_t item = first; item < nitems && ok && !*abort_flag; item += stride) {
-            const int split = (int)(item % nsplit);
-            const int64_t qb = q0 + (item / nsplit) * C::QROWS + (int64_t)rank * TBM;
-            const int64_t cbeg = (int64_t)split * per, cend = min(N, cbeg + per);
-            const int ntiles = cend > cbeg ? (int)((cend - cbeg + TBN - 1) / TBN) : 0;
-            for (int t = 0; t < ntiles && ok && !*abort_flag; ++t) {
-                const int c0 = (int)(cbeg + (int64_t)t * TBN) + (int)rank * C::B_ROWS;
-                for (int kb = 0; kb < nkb; ++kb, ++it) {
+            const ItemGeo g = geo(item);
+            const int64_t qb = g.qb + (int64_t)rank * TBM;
+            const CUtensorMap *map_q = g.ma, *map_c = PAIR ? g.ma : g.mb;
+            if constexpr (BATCH) {
+                // the table's maps were written by a host copy: fence each dataset's
+                // pair once before its first load
+                if (map_q != last_map) {
+                    tc::fence_tmap_acquire(map_q);
+                    if (map_c != map_q) tc::fence_tmap_acquire(map_c);
+                    last_map = map_q;
+                }
+            }
+            for (int t = 0; t < g.ntiles && ok && !*abort_flag; ++t) {
+                const int c0 = (int)(g.cbeg + (int64_t)t * TBN) + (int)rank * C::B_ROWS;
+                for (int kb = 0; kb < g.nkb; ++kb, ++it) {
                     if (!tc::mbar_wait(empty0 + 8 * s, ph ^ 1u, abort_flag, wait_limit)) { ok = false; break; }
                     const uint32_t sa = st0 + s * (uint32_t)STAGE;
                     if constexpr (PAIR) {
                         if (rank == 0) tc::mbar_expect_tx(full0 + 8 * s, 2 * STAGE);
-                        tc::tma_load_2d_pair(sa, &map_a, pfull0 + 8 * s, kb * TBK, (int)qb);
-                        tc::tma_load_2d_pair(sa + A_BYTES, &map_b, pfull0 + 8 * s, kb * TBK, c0);
+                        tc::tma_load_2d_pair(sa, map_q, pfull0 + 8 * s, kb * TBK, (int)qb);
+                        tc::tma_load_2d_pair(sa + A_BYTES, map_c, pfull0 + 8 * s, kb * TBK, c0);
                     } else {
                         const uint32_t fb = full0 + 8 * s;
                         tc::mbar_expect_tx(fb, STAGE);
-                        tc::tma_load_2d(sa, &map_a, fb, kb * TBK, (int)qb);
-                        tc::tma_load_2d(sa + A_BYTES, &map_b, fb, kb * TBK, c0);
+                        tc::tma_load_2d(sa, map_q, fb, kb * TBK, (int)qb);
+                        tc::tma_load_2d(sa + A_BYTES, map_c, fb, kb * TBK, c0);
                     }
                     if (++s == (uint32_t)NST) { s = 0; ph ^= 1u; }
                 }
@@ -290,10 +359,9 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
                            empty0 = tc::smem_u32(&sh->empty[0]);
             const uint64_t ad0 = kdesc(st0), bd0 = kdesc(st0 + A_BYTES);
             for (int64_t item = first; item < nitems && ok && !*abort_flag; item += stride) {
-            const int split = (int)(item % nsplit);
-            const int64_t cbeg = (int64_t)split * per, cend = min(N, cbeg + per);
-            const int ntiles = cend > cbeg ? (int)((cend - cbeg + TBN - 1) / TBN) : 0;
-            for (int tt = 0; tt < ntiles && ok && !*abort_flag; ++tt, ++t) {
+            const ItemGeo g = geo(item);
+            const int nkb = g.nkb;
+            for (int tt = 0; tt < g.ntiles && ok && !*abort_flag; ++tt, ++t) {
                 const int acc = t & 1;
                 const uint32_t te = tc::smem_u32(&sh->tempty[acc]);
                 const uint32_t tpar = ((t >> 1) & 1) ^ 1;
@@ -353,17 +421,19 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
         const uint32_t tempty_even0 = PAIR ? tc::mapa(tc::smem_u32(&sh->tempty[0]), 0) : 0u;
         int t = 0;  // tiles drained so far by this CTA (all items)
         for (int64_t item = first; item < nitems && !*abort_flag; item += stride) {
-            const int split = (int)(item % nsplit);
-            const int64_t qb = q0 + (item / nsplit) * C::QROWS + (int64_t)rank * TBM;
-            const int64_t cbeg = (int64_t)split * per, cend = min(N, cbeg + per);
-            const int ntiles = cend > cbeg ? (int)((cend - cbeg + TBN - 1) / TBN) : 0;
+            const ItemGeo g = geo(item);
+            const int64_t qb = g.qb + (int64_t)rank * TBM;
+            const int64_t cbeg = g.cbeg, cend = g.cend, N = g.N;
+            const int ntiles = g.ntiles, kc = g.kc;
+            const int include_self = g.include_self;
+            const float *norms = g.norms;
             const int64_t gq = qb + row;
-            const bool valid_row = gq < qend;
+            const bool valid_row = gq < g.qend;
             const float qn = valid_row ? norms[gq] : 0.f;
             const int64_t out_base =
-                valid_row ? (((gq - q0) * nsplit + split) * TC_HALVES + half) * (int64_t)kc : 0;
+                valid_row ? (((gq - g.q0) * g.nsplit + g.split) * TC_HALVES + half) * (int64_t)kc : 0;
             ListState st{valid_row ? INFINITY : -INFINITY, 0};
-            int32_t *out_i = cand_i + out_base;
+            int32_t *out_i = g.cand_i + out_base;
             for (int tt = 0; tt < ntiles && !*abort_flag; ++tt, ++t) {
                 const int acc = t & 1;
                 if (!tc::mbar_wait(tc::smem_u32(&sh->tfull[acc]), (t >> 1) & 1, abort_flag, wait_limit)) {
@@ -401,9 +471,9 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
                 }
             }
             if (valid_row) {
-                for (int p = 0; p < st.cnt; ++p) cand_d[out_base + Ls[p * TBM + row]] = Ld[p * TBM + row];
+                for (int p = 0; p < st.cnt; ++p) g.cand_d[out_base + Ls[p * TBM + row]] = Ld[p * TBM + row];
                 for (int s2 = st.cnt; s2 < kc; ++s2) {
-                    cand_d[out_base + s2] = INFINITY;
+                    g.cand_d[out_base + s2] = INFINITY;
                     out_i[s2] = -1;
                 }
             }
@@ -458,6 +528,7 @@ size_t knn_tc_smem_bytes(int kc) {
 }
 
 int knn_tc_halves() { return TC_HALVES; }
+int knn_tc_item_rows(int pair) { return pair ? KCfg<true>::QROWS : KCfg<false>::QROWS; }
 
 cudaError_t launch_knn_tc(const void *Xb, int64_t N, int64_t m, int64_t ldb, const float *norms, int64_t q0,
                           int64_t nq, int kc, int nsplit, int include_self, float *cand_d, int32_t *cand_i, int pair,
@@ -476,7 +547,7 @@ cudaError_t launch_knn_tc(const void *Xb, int64_t N, int64_t m, int64_t ldb, con
     if (pair && nq >= 2 * TBM) {
         // CTA pairs (cta_group::2): 256 query rows per item; each CTA's candidate
         // half uses the 128-row box of the query map
-        e = cudaFuncSetAttribute(knn_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(knn_tc_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -491,26 +562,79 @@ cudaError_t launch_knn_tc(const void *Xb, int64_t N, int64_t m, int64_t ldb, con
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int nclusters = 0;
-        e = cudaOccupancyMaxActiveClusters(&nclusters, knn_tc_kernel<true>, &cfg);
+        e = cudaOccupancyMaxActiveClusters(&nclusters, knn_tc_kernel<true, false>, &cfg);
         if (e != cudaSuccess) return e;
         if (nclusters > 0) {
             const int64_t items = ((nq + 2 * TBM - 1) / (2 * TBM)) * nsplit;
             cfg.gridDim = dim3((unsigned)(2 * (items < nclusters ? items : nclusters)));
             // the pair form keeps the default limit: its cross-CTA arrivals are
             // not exercised with shortened waits
-            e = cudaLaunchKernelEx(&cfg, knn_tc_kernel<true>, ma, ma, N, m, norms, q0, nq, kc, nsplit, include_self,
-                                   cand_d, cand_i, WAIT_LIMIT, ctr);
+            e = cudaLaunchKernelEx(&cfg, knn_tc_kernel<true, false>, ma, ma, N, m, norms, q0, nq, kc, nsplit, include_self,
+                                   cand_d, cand_i, WAIT_LIMIT, ctr, (const KnnSet *)nullptr, 0, (int64_t)0);
             if (e != cudaSuccess) return e;
             return cudaGetLastError();
         }
         // no pair fits: single CTAs
     }
-    e = cudaFuncSetAttribute(knn_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(knn_tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t items = ((nq + TBM - 1) / TBM) * nsplit;
     dim3 grid((unsigned)(items < sms ? items : sms));  // persistent: one CTA per SM
-    knn_tc_kernel<false><<<grid, TC_THREADS, smem, s>>>(ma, mb, N, m, norms, q0, nq, kc, nsplit, include_self,
-                                                         cand_d, cand_i, wait_limit, ctr);
+    knn_tc_kernel<false, false><<<grid, TC_THREADS, smem, s>>>(ma, mb, N, m, norms, q0, nq, kc, nsplit, include_self,
+                                                                cand_d, cand_i, wait_limit, ctr, nullptr, 0, 0);
+    return cudaGetLastError();
+}
+
+bool knn_tc_make_maps(KnnSet *d) {
+    return make_map(&d->map_a, d->xb ? d->xb : d->X, d->N, d->m, d->ldb, TBM) &&
+           make_map(&d->map_b, d->xb ? d->xb : d->X, d->N, d->m, d->ldb, TBN);
+}
+
+cudaError_t launch_knn_tc_batch(const KnnSet *sets, int nsets, int64_t nitems, int kcmax, int pair,
+                                long long wait_limit, DevCounters *ctr, cudaStream_t s) {
+    if (nitems <= 0) return cudaSuccess;
+    if (kcmax > 64 || nsets < 1) return cudaErrorInvalidValue;
+    if (wait_limit <= 0) wait_limit = WAIT_LIMIT;
+    const size_t smem = knn_tc_smem_bytes(kcmax);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    CUtensorMap none;
+    memset(&none, 0, sizeof(none));
+    if (pair) {
+        // items of 256 query rows (the table's item counts must be for that size)
+        e = cudaFuncSetAttribute(knn_tc_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.blockDim = dim3(TC_THREADS);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cfg.gridDim = dim3(2);
+        int nclusters = 0;
+        e = cudaOccupancyMaxActiveClusters(&nclusters, knn_tc_kernel<true, true>, &cfg);
+        if (e != cudaSuccess) return e;
+        if (nclusters <= 0) return cudaErrorInvalidConfiguration;
+        cfg.gridDim = dim3((unsigned)(2 * (nitems < nclusters ? nitems : nclusters)));
+        e = cudaLaunchKernelEx(&cfg, knn_tc_kernel<true, true>, none, none, (int64_t)0, (int64_t)0,
+                               (const float *)nullptr, (int64_t)0, (int64_t)0, kcmax, 1, 0, (float *)nullptr,
+                               (int32_t *)nullptr, WAIT_LIMIT, ctr, sets, nsets, nitems);
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+    }
+    e = cudaFuncSetAttribute(knn_tc_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)(nitems < sms ? nitems : sms));
+    knn_tc_kernel<false, true><<<grid, TC_THREADS, smem, s>>>(none, none, 0, 0, nullptr, 0, 0, kcmax, 1, 0, nullptr,
+                                                               nullptr, wait_limit, ctr, sets, nsets, nitems);
     return cudaGetLastError();
 }
 
