@@ -131,11 +131,18 @@ typedef enum {
     MECUCO_OPT_TT_CTAS = 14,         /* BF16-mixed third-moment pass: CTAs per SM, 1 (512 TMEM columns each)
                                         or 2 (default; 256 each: fewer accumulators per pass over the patch,
                                         two hand-over pipelines interleaved).  Results identical */
-    MECUCO_OPT_BATCH_PERSISTENT = 15 /* 1 (default): mecuco_curvature_batched with MECUCO_PREC_BF16_MIXED runs
+    MECUCO_OPT_BATCH_PERSISTENT = 15,/* 1 (default): mecuco_curvature_batched with MECUCO_PREC_BF16_MIXED runs
                                         every dataset of the batch in one launch per stage (persistent kNN
                                         over a device table of all datasets' work items, estimator launches
                                         over segment tables of all datasets' points); 0: one stream lane per
                                         dataset group, as the FP32 form always does.  Results identical */
+    MECUCO_OPT_JACOBI_WARP = 16      /* FP32 Jacobi sweeps: 1, 2 (default) or 4 warps per patch in the fused
+                                        form (a round's rotations applied in one pass over 2 x 2 blocks of A
+                                        and U, two barriers per round, none with 1 warp); 0: one CTA of 128
+                                        threads per patch in three passes (row, column and eigenvector
+                                        updates, three barriers per round).  Same rotations and thresholds;
+                                        the results differ only by rounding order.  Measured on 100k patches
+                                        (k = 64): 230 ms (0), 221 (1), 192 (2), 192 (4) */
 } mecuco_option;
 
 /* Kernel stages, for mecuco_get_stage_times. */
@@ -339,7 +346,7 @@ typedef struct {
  *
  * MECUCO_PREC_BF16_MIXED (with MECUCO_OPT_BATCH_PERSISTENT = 1, the default):
  * one launch per stage for the whole batch.  The datasets are ordered by m,
- * then N, descending; a device table describes each (its operand's tensor
+ * then k, then N, descending; a device table describes each (its operand's tensor
  * maps, its first search work item and first row) and the persistent kNN
  * search takes the work items (query block x candidate split) of every
  * dataset from it, one CTA (or CTA pair) per SM; row norms, BF16 copies,

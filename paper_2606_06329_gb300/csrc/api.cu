@@ -99,6 +99,7 @@ struct mecuco_ctx {
     int64_t knn_margin = 32;
     int jacobi_fp64 = -1;
     int jacobi_max_sweeps = 40;
+    int jacobi_warp = 2;  // FP32 sweeps: warps per patch of the fused form (0: the three-pass CTA form)
     int64_t chunk_points = 0;
     int64_t knn_qchunk = 0;
     int profile = 0;
@@ -234,6 +235,7 @@ struct KnnPlan {
     bool tc;        // candidate search on the tensor cores (BF16 operands)
     bool pair;      // tensor-core search as CTA pairs sharing two-SM MMAs
     bool bf16_copy; // the tensor-core path needs a BF16 copy of X
+    bool quant;     // the search reads BF16 roundings of FP32 rows (certification bounds their error)
     int64_t ldb;    // leading dimension of the BF16 operand
 };
 
@@ -249,6 +251,7 @@ KnnPlan plan_knn(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t 
     p.pair = p.tc && (h->knn_pair > 0 || (h->knn_pair < 0 && N >= KNN_PAIR_MIN_N));
     const bool direct = dt == MECUCO_BF16 && ld % 8 == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
     p.bf16_copy = p.tc && !direct;
+    p.quant = p.tc && dt == MECUCO_F32;
     p.ldb = direct ? ld : (m + 7) / 8 * 8;
     p.qchunk = h->knn_qchunk > 0 ? h->knn_qchunk : (int64_t)1 << 18;
     if (p.qchunk > nrows) p.qchunk = nrows;
@@ -275,6 +278,7 @@ struct KnnBufs {
     float *norms, *cand_d;
     int32_t *cand_i, *flags;
     void *xb;
+    float *resid, *maxima;  // BF16 rounding residuals of FP32 rows (tensor-core search), else NULL
 };
 
 // Scratch of run_knn, carved after `start`.
@@ -284,6 +288,8 @@ void knn_scratch(Carver &c, const KnnPlan &p, int64_t N, KnnBufs *b) {
     b->cand_i = c.take<int32_t>((size_t)p.qchunk * p.lists * p.kcl);
     b->flags = c.take<int32_t>((size_t)p.qchunk);
     b->xb = p.bf16_copy ? (void *)c.take<uint16_t>((size_t)N * p.ldb) : nullptr;
+    b->resid = p.quant ? c.take<float>((size_t)N) : nullptr;
+    b->maxima = p.quant ? c.take<float>(2) : nullptr;
 }
 
 // kNN of query rows [rb, re) (outputs relative to rb); scratch at ws + start,
@@ -295,7 +301,8 @@ mecuco_status run_knn(mecuco_t h, char *ws, const void *X, mecuco_dtype dt, int6
     Carver c(ws, start);
     KnnBufs b;
     knn_scratch(c, p, N, &b);
-    LAUNCH(h, MECUCO_STAGE_ROWNORM, s, launch_rownorm(X, dt, N, m, ld, b.norms, s));
+    if (b.maxima) CK(cudaMemsetAsync(b.maxima, 0, 2 * sizeof(float), s));
+    LAUNCH(h, MECUCO_STAGE_ROWNORM, s, launch_rownorm(X, dt, N, m, ld, b.norms, s, b.resid, b.maxima));
     const void *Xb = X;
     if (p.bf16_copy) {
         CK(launch_to_bf16(X, dt, N, m, ld, b.xb, p.ldb, s));
@@ -320,7 +327,7 @@ mecuco_status run_knn(mecuco_t h, char *ws, const void *X, mecuco_dtype dt, int6
         // bounds every candidate left out
         LAUNCH(h, MECUCO_STAGE_KNN_RERANK, s,
                launch_knn_rerank(X, dt, N, m, ld, b.norms, q0, nq, p.kcl, p.lists, k, b.cand_d, b.cand_i, io, dout,
-                                 b.flags, h->ctr, s));
+                                 b.flags, h->ctr, s, b.resid, b.maxima));
         LAUNCH(h, MECUCO_STAGE_KNN_FALLBACK, s,
                launch_knn_fallback(X, dt, N, m, ld, q0, nq, k, include_self, b.flags, io, dout, h->ctr, s));
     }
@@ -496,7 +503,8 @@ mecuco_status run_curvature(mecuco_t h, char *ws, const void *X, mecuco_dtype dt
             LAUNCH(h, MECUCO_STAGE_JACOBI, s,
                    launch_rsvd_range(b.G, k, np, h->rsvd.omega, l, h->rsvd.power, b.rQ, b.rB, s));
             LAUNCH(h, MECUCO_STAGE_JACOBI, s,
-                   launch_jacobi(b.rB, l, np, 1, h->jacobi_max_sweeps, b.rsig, b.rV, h->ctr, s));
+                   launch_jacobi(b.rB, l, np, 1, h->jacobi_max_sweeps, b.rsig, b.rV, h->ctr, s,
+                                 kJacobiPreTight, h->jacobi_warp));
             ++h->launches;
             LAUNCH(h, MECUCO_STAGE_JACOBI, s,
                    launch_rsvd_compose(b.rQ, b.rsig, b.rV, k, l, h->rsvd.rank, np, b.sig, Ud, s));
@@ -528,7 +536,8 @@ mecuco_status run_curvature(mecuco_t h, char *ws, const void *X, mecuco_dtype dt
             const int haar = var == MECUCO_FAST_HAAR ? 1 : 0;
             LAUNCH(h, MECUCO_STAGE_GRAM, s, launch_gram_tc(dt, sg, nullptr, 0, np, haar, h->wait_limit, h->ctr, s));
             LAUNCH(h, MECUCO_STAGE_JACOBI, s,
-                   launch_jacobi_seg(sg, nullptr, 0, k, np, fp64, h->jacobi_max_sweeps, h->ctr, s, kJacobiPreLoose));
+                   launch_jacobi_seg(sg, nullptr, 0, k, np, fp64, h->jacobi_max_sweeps, h->ctr, s, kJacobiPreLoose,
+                                 h->jacobi_warp));
             if (fp64 == 1 || fp64 == 3) ++h->launches;  // the refinement is a second kernel
             LAUNCH(h, MECUCO_STAGE_ROTATE, s,
                    launch_rotate_tc(dt, sg, nullptr, 0, np, b.Y, rot_ld(m), h->wait_limit, h->ctr, s));
@@ -541,14 +550,17 @@ mecuco_status run_curvature(mecuco_t h, char *ws, const void *X, mecuco_dtype dt
             // nearly diagonal Gram of Z resolves small eigenvalues), then its eigenpairs
             LAUNCH(h, MECUCO_STAGE_GRAM, s,
                    launch_patch_gram(X, dt, N, m, ld, nb, k, 0, np, nullptr, b.G, b.R, nullptr, h->ctr, s));
-            LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(b.G, k, np, 1, h->jacobi_max_sweeps, b.sig, b.U0, h->ctr, s));
+            LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(b.G, k, np, 1, h->jacobi_max_sweeps, b.sig, b.U0, h->ctr, s,
+                                 kJacobiPreTight, h->jacobi_warp));
             ++h->launches;
             LAUNCH(h, MECUCO_STAGE_GRAM, s,
                    launch_patch_gram(X, dt, N, m, ld, nb, k, 0, np, b.U0, b.G, b.R, var == MECUCO_FAST_HAAR ? b.Q : nullptr,
                                      h->ctr, s));
             LAUNCH(h, MECUCO_STAGE_MOMENTS, s,
                    launch_patch_m3(X, dt, N, m, ld, nb, k, 0, np, b.U0, b.M, h->m3_items[k], h->ctr, s));
-            LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(b.G, k, np, fp64, h->jacobi_max_sweeps, b.sig, b.U, h->ctr, s));
+            LAUNCH(h, MECUCO_STAGE_JACOBI, s,
+                   launch_jacobi(b.G, k, np, fp64, h->jacobi_max_sweeps, b.sig, b.U, h->ctr, s,
+                                 kJacobiPreTight, h->jacobi_warp));
             if (fp64 == 1 || fp64 == 3) ++h->launches;
             LAUNCH(h, MECUCO_STAGE_ESTIMATOR, s,
                    launch_estimator(b.sig, b.U, b.M, b.R, Qarg, k, m, np, (int)var, rank_eps_rotated(k, m),
@@ -660,9 +672,10 @@ mecuco_status run_batched_lanes(mecuco_t h, const mecuco_dataset *sets, int nset
 // ---- batched entry point, one launch per stage (BF16-mixed) ----------------
 // Every dataset's kNN work items come from one device table (KnnSet), every
 // estimator launch covers the points of all datasets through a segment table
-// (PatchSeg).  Datasets go in order of m, then N, descending, so that the
-// points of one estimator launch share the leading dimension of their rotated
-// patches with little padding.
+// (PatchSeg).  Datasets go in order of m, then k, then N, descending, so that
+// the points of one estimator launch share the leading dimension of their
+// rotated patches with little padding, and its per-patch shared memory (sized
+// for the launch's largest k) fits most of its patches closely.
 constexpr size_t BATCH_EST_BUDGET = (size_t)8 << 30;  // bytes of estimator chunk scratch
 constexpr int BATCH_TABLES_KEPT = 64;
 
@@ -684,6 +697,7 @@ struct BatchPlan {
     int64_t nrows = 0, nitems = 0;
     int kcmax = 0, lmax = 0, kmax = 0;
     bool any_copy = false;
+    float *maxima = nullptr;      // 2 per dataset (FP32 rows), zeroed before the row norms
     size_t bytes = 0;             // workspace bytes
 };
 
@@ -701,6 +715,7 @@ mecuco_status plan_batch(mecuco_t h, const mecuco_dataset *sets, int nsets, mecu
     std::iota(p.order.begin(), p.order.end(), 0);
     std::stable_sort(p.order.begin(), p.order.end(), [&](int a, int b) {
         if (sets[a].m != sets[b].m) return sets[a].m > sets[b].m;
+        if (sets[a].k != sets[b].k) return sets[a].k > sets[b].k;
         return sets[a].N > sets[b].N;
     });
     Carver c(base, 0);
@@ -726,7 +741,10 @@ mecuco_status plan_batch(mecuco_t h, const mecuco_dataset *sets, int nsets, mecu
         e.include_self = include_self;
         e.kc = candidate_capacity(h, d.k);
         e.kcl = std::min(e.kc, 64);
-        // one candidate split: the batch's query blocks fill the GPU
+        // one candidate split: the batch's query blocks fill the GPU.  (Two
+        // splits for k > 32, where a list holds 64 < kc = 96, left 0.6% instead
+        // of 1% of the 256-dataset batch's rows uncertified, but the larger
+        // search and re-rank cost 205 ms more than the exact scans saved.)
         const int cap = 1024 / (halves * e.kcl);
         e.nsplit = h->knn_splits > 0 ? std::min(h->knn_splits, cap) : 1;
         while (e.nsplit > 1 && (d.N + e.nsplit - 1) / e.nsplit < e.kc) --e.nsplit;
@@ -738,6 +756,7 @@ mecuco_status plan_batch(mecuco_t h, const mecuco_dataset *sets, int nsets, mecu
         e.cand_i = c.take<int32_t>((size_t)d.N * e.lists * e.kcl);
         e.flags = c.take<int32_t>((size_t)d.N);
         e.xb = direct ? nullptr : (void *)c.take<uint16_t>((size_t)d.N * e.ldb);
+        e.resid = dt == MECUCO_F32 ? c.take<float>((size_t)d.N) : nullptr;
         e.item_begin = p.nitems;
         e.row_begin = p.nrows;
         p.nitems += (d.N + qrows - 1) / qrows * e.nsplit;
@@ -746,9 +765,16 @@ mecuco_status plan_batch(mecuco_t h, const mecuco_dataset *sets, int nsets, mecu
         p.lmax = std::max(p.lmax, e.kcl * e.lists);
         p.kmax = std::max(p.kmax, d.k);
         p.any_copy = p.any_copy || !direct;
-        if (base && !knn_tc_make_maps(&e)) {
-            set_error_text("batched kNN: a dataset's operand cannot be described by a tensor map");
-            return MECUCO_ERR_INVALID_ARG;
+    }
+    // the datasets' residual maxima, contiguous (one memset per call)
+    p.maxima = dt == MECUCO_F32 ? c.take<float>((size_t)2 * nsets) : nullptr;
+    for (int t = 0; t < nsets && p.maxima; ++t) p.knn[t].maxima = p.maxima + 2 * t;
+    if (base) {
+        for (int t = 0; t < nsets; ++t) {
+            if (!knn_tc_make_maps(&p.knn[t])) {
+                set_error_text("batched kNN: a dataset's operand cannot be described by a tensor map");
+                return MECUCO_ERR_INVALID_ARG;
+            }
         }
     }
     const size_t knn_end = c.off;
@@ -871,6 +897,7 @@ mecuco_status run_batched_persistent(mecuco_t h, const mecuco_dataset *sets, int
     CK(launch_batch_patch(kt, nsets, sg, refs, (int)p.segs.size(), p.outs.data(), s));
     h->launches += (nsets + BATCH_PATCH_SETS - 1) / BATCH_PATCH_SETS;
     // kNN of every row of every dataset: one launch per stage
+    if (p.maxima) CK(cudaMemsetAsync(p.maxima, 0, 2 * sizeof(float) * nsets, s));
     LAUNCH(h, MECUCO_STAGE_ROWNORM, s, launch_rownorm_batch(kt, nsets, p.nrows, dt, s));
     if (p.any_copy) {
         CK(launch_to_bf16_batch(kt, nsets, p.nrows, dt, s));
@@ -890,7 +917,7 @@ mecuco_status run_batched_persistent(mecuco_t h, const mecuco_dataset *sets, int
         LAUNCH(h, MECUCO_STAGE_GRAM, s, launch_gram_tc(dt, none, tab, ch.nseg, ch.np, haar, h->wait_limit, h->ctr, s));
         LAUNCH(h, MECUCO_STAGE_JACOBI, s,
                launch_jacobi_seg(none, tab, ch.nseg, ch.kmax, ch.np, fp64, h->jacobi_max_sweeps, h->ctr, s,
-                                 kJacobiPreLoose));
+                                 kJacobiPreLoose, h->jacobi_warp));
         if (fp64 == 1 || fp64 == 3) ++h->launches;
         LAUNCH(h, MECUCO_STAGE_ROTATE, s,
                launch_rotate_tc(dt, none, tab, ch.nseg, ch.np, ch.Y, ch.ldy, h->wait_limit, h->ctr, s));
@@ -1080,6 +1107,10 @@ mecuco_status mecuco_set_option(mecuco_t h, mecuco_option opt, int64_t v) {
             if (v < 1 || v > 32) return MECUCO_ERR_INVALID_ARG;
             h->batch_lanes = (int)v;
             break;
+        case MECUCO_OPT_JACOBI_WARP:
+            if (v != 0 && v != 1 && v != 2 && v != 4) return MECUCO_ERR_INVALID_ARG;
+            h->jacobi_warp = (int)v;
+            break;
         case MECUCO_OPT_BATCH_PERSISTENT:
             if (v != 0 && v != 1) return MECUCO_ERR_INVALID_ARG;
             h->batch_persistent = (int)v;
@@ -1215,14 +1246,17 @@ mecuco_status mecuco_curvature_backward(mecuco_t h, const void *X, mecuco_dtype 
         // which ill-conditioned patches amplify)
         LAUNCH(h, MECUCO_STAGE_GRAM, s,
                launch_patch_gram(X, dt, N, m, ld, nb, k, 0, np, nullptr, b.G, b.R, nullptr, h->ctr, s));
-        LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(b.G, k, np, 1, h->jacobi_max_sweeps, b.sig, U0, h->ctr, s));
+        LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(b.G, k, np, 1, h->jacobi_max_sweeps, b.sig, U0, h->ctr, s,
+                                 kJacobiPreTight, h->jacobi_warp));
         ++h->launches;  // the refinement kernel
         // moments of Z = U0^T X_c and the refined eigenpairs of its Gram
         LAUNCH(h, MECUCO_STAGE_GRAM, s,
                launch_patch_gram(X, dt, N, m, ld, nb, k, 0, np, U0, b.G, b.R, need_q ? b.Q : nullptr, h->ctr, s));
         LAUNCH(h, MECUCO_STAGE_MOMENTS, s,
                launch_patch_m3(X, dt, N, m, ld, nb, k, 0, np, U0, b.M, h->m3_items[k], h->ctr, s));
-        LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(b.G, k, np, rot_mode, h->jacobi_max_sweeps, b.sig, b.U, h->ctr, s));
+        LAUNCH(h, MECUCO_STAGE_JACOBI, s,
+               launch_jacobi(b.G, k, np, rot_mode, h->jacobi_max_sweeps, b.sig, b.U, h->ctr, s,
+                                 kJacobiPreTight, h->jacobi_warp));
         if (rot_mode == 1 || rot_mode == 3) ++h->launches;  // the refinement kernel
         LAUNCH(h, MECUCO_STAGE_ADJOINT, s,
                launch_adjoint(X, dt, N, m, ld, nb, k, np, (int)var, rank_eps_rotated(k, m), U0, b.sig, b.U, b.M, b.R,
@@ -1259,7 +1293,8 @@ mecuco_status mecuco_tangent_basis(mecuco_t h, const void *X, mecuco_dtype dt, i
         const int32_t *nb = idx + p0 * k;
         LAUNCH(h, MECUCO_STAGE_GRAM, s,
                launch_patch_gram(X, dt, N, m, ld, nb, k, 0, np, nullptr, G, R, nullptr, h->ctr, s));
-        LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(G, k, np, mode, h->jacobi_max_sweeps, sig, U, h->ctr, s));
+        LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(G, k, np, mode, h->jacobi_max_sweeps, sig, U, h->ctr, s,
+                                 kJacobiPreTight, h->jacobi_warp));
         if (mode == 1 || mode == 3) ++h->launches;
         LAUNCH(h, MECUCO_STAGE_BASIS, s,
                launch_tangent_basis(X, dt, N, m, ld, nb, k, np, sig, U, d_out, rank_eps_gram32(m),
@@ -1307,7 +1342,8 @@ mecuco_status mecuco_curvature_exact(mecuco_t h, const void *X, mecuco_dtype dt,
         float *vd = v_out ? v_out + p0 * m : vb;
         float *Wd = W_out ? W_out + p0 * m * m : Wb;
         LAUNCH(h, MECUCO_STAGE_EXACT, s, launch_exact_cov(X, dt, N, m, ld, nbr + p0 * k, k, np, S, h->ctr, s));
-        LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(S, mm, np, mode, h->jacobi_max_sweeps, vd, Wd, h->ctr, s));
+        LAUNCH(h, MECUCO_STAGE_JACOBI, s, launch_jacobi(S, mm, np, mode, h->jacobi_max_sweeps, vd, Wd, h->ctr, s,
+                                 kJacobiPreTight, h->jacobi_warp));
         if (mode == 1 || mode == 3) ++h->launches;
         LAUNCH(h, MECUCO_STAGE_EXACT, s, launch_exact_kappa(vd, Wd, mm, np, kappa_out + p0, s));
     }

@@ -184,6 +184,214 @@ jacobi_kernel(const __grid_constant__ PatchSeg one, const PatchSeg *__restrict__
 }
 
 // ---------------------------------------------------------------------------
+// The same parallel-order Jacobi (same pairing, thresholds, rotations and
+// sweep cap) with a round's updates fused into one pass over 2 x 2 blocks.
+// Per round, lanes i < kp/2 of warp 0 compute pair i's rotation J_i and
+// publish (c, s, p, q) in a table; then every rotating pair j is taken by one
+// of the NW warps of the patch (round-robin over the ballot of rotating pairs,
+// JW_UNROLL pairs in flight per warp), whose lane i replaces the block
+// A[{p_i,q_i}, {p_j,q_j}] by J_i^T (A_ij J_j) (J_i = I when pair i does not
+// rotate; for i = j the off-diagonal pair is set to 0) and, when pair i does
+// not rotate, also writes the transposed result into A[{p_j,q_j}, {p_i,q_i}],
+// the block whose column pair is not visited in this round; the same warp
+// applies J_j to columns p_j, q_j of U (kept transposed: rows of U^T
+// contiguous, two entries per lane, 8-byte accesses).  Every block is read and
+// written by one lane in one iteration and no iteration reads a block another
+// one writes, so a round needs two barriers (table published; updates done)
+// and none inside.  Per rotation of a full round this moves 8 words of A (plus
+// 4 transposed for pairs that do not rotate) and 8 of U, against 16 plus 3
+// table reads in the one-CTA form's three passes with three barriers.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int JW_UNROLL = 4;  // rotating pairs whose block updates are in flight together per warp
+__host__ __device__ inline size_t jw_smem_bytes(int kmax) {
+    const int kp = (kmax + 1) & ~1;
+    // A (row stride kp + 1), U^T (row stride kp), 8-byte pad, 16-byte pad, table
+    return ((size_t)kp * (kp + 1) + (size_t)kp * kp + 2 + 4) * sizeof(float) + 32 * sizeof(float4);
+}
+template <int NW>
+__device__ __forceinline__ void jw_sync() {
+    if constexpr (NW == 1) __syncwarp();
+    else __syncthreads();
+}
+}  // namespace
+
+template <int NW>
+__global__ void __launch_bounds__(NW * 32)
+jacobi_warp_kernel(const __grid_constant__ PatchSeg one, const PatchSeg *__restrict__ tab, int ntab, int max_sweeps,
+                   float eps, DevCounters *ctr) {
+    extern __shared__ __align__(16) float jw_sm[];
+    __shared__ unsigned ctl_mask;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int local;
+    const PatchSeg &seg = find_seg(one, tab, ntab, (int)blockIdx.x, local);
+    const int k = seg.k;
+    const int kp = (k + 1) & ~1;
+    const int h = kp / 2;
+    const int ld = kp + 1;
+    const int n1 = kp - 1;
+    float *A = jw_sm;
+    float *Ut = A + (size_t)kp * ld;
+    Ut += (reinterpret_cast<uintptr_t>(Ut) & 7) ? 1 : 0;  // 8-byte aligned rows (kp is even)
+    float4 *T = reinterpret_cast<float4 *>((reinterpret_cast<uintptr_t>(Ut + (size_t)kp * kp) + 15) & ~(uintptr_t)15);
+    const int64_t patch = local;
+    const float *g = seg.G + patch * (int64_t)k * k;
+    for (int e = threadIdx.x; e < kp * kp; e += NW * 32) {
+        const int r = e / kp, c = e % kp;
+        A[r * ld + c] = (r < k && c < k) ? g[r * k + c] : 0.f;
+        Ut[e] = (r == c) ? 1.f : 0.f;
+    }
+    jw_sync<NW>();
+    const unsigned FULL = 0xffffffffu;
+    int sweep = 0;
+    bool converged = false;
+    unsigned long long rotations = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        int rot = 0;
+        // circle method (warp 0): index kp - 1 fixed (lane 0's a), the others rotate
+        int a = lane == 0 ? n1 : lane % n1, b = lane == 0 ? 0 : (n1 - lane) % n1;
+        for (int round = 0; round < n1; ++round) {
+            if (warp == 0) {
+                bool act = false;
+                if (lane < h) {
+                    const int p = a < b ? a : b, q = a < b ? b : a;
+                    float c = 1.f, sn = 0.f;
+                    const float app = A[p * ld + p], aqq = A[q * ld + q], apq = A[p * ld + q];
+                    if (fabsf(apq) > eps * sqrtf(fabsf(app * aqq)) && apq != 0.f) {
+                        const float tau = (aqq - app) / (2 * apq);
+                        const float t = (tau >= 0 ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+                        c = 1.f / sqrtf(1.f + t * t);
+                        sn = t * c;
+                        act = true;
+                    }
+                    T[lane] = make_float4(c, sn, __int_as_float(p), __int_as_float(q));
+                }
+                const unsigned m = __ballot_sync(FULL, act);
+                if (lane == 0) ctl_mask = m;
+                // next round's pair
+                if (lane == 0) b = b + 1;
+                else { a = a + 1 == n1 ? 0 : a + 1; b = b + 1 == n1 ? 0 : b + 1; }
+            }
+            jw_sync<NW>();  // the round's table
+            unsigned mask = ctl_mask;
+            rot += __popc(mask);
+            if (mask != 0u && lane < h) {
+                const float4 ti = T[lane];
+                const float c = ti.x, sn = ti.y;
+                const int p = __float_as_int(ti.z), q = __float_as_int(ti.w);
+                const bool act = (mask >> lane) & 1u;
+                float *rp = A + p * ld, *rq = A + q * ld;
+                // this warp's share: every NW-th rotating pair, starting at the warp's index
+                for (int w = 0; w < warp && mask; ++w) mask &= mask - 1;
+                while (mask) {
+                    int js[JW_UNROLL];
+                    float4 tj[JW_UNROLL];
+                    float av[JW_UNROLL][4];
+                    float2 uv[JW_UNROLL], wv[JW_UNROLL];
+#pragma unroll
+                    for (int u = 0; u < JW_UNROLL; ++u) {
+                        js[u] = mask ? __ffs(mask) - 1 : -1;
+#pragma unroll
+                        for (int w = 0; w < NW; ++w) mask &= mask - 1;
+                    }
+                    // every load of the group before its first store (no element
+                    // loaded in a round is stored by another pair's update)
+#pragma unroll
+                    for (int u = 0; u < JW_UNROLL; ++u) {
+                        if (js[u] < 0) continue;
+                        tj[u] = T[js[u]];
+                        const int pj = __float_as_int(tj[u].z), qj = __float_as_int(tj[u].w);
+                        av[u][0] = rp[pj];
+                        av[u][1] = rp[qj];
+                        av[u][2] = rq[pj];
+                        av[u][3] = rq[qj];
+                        uv[u] = reinterpret_cast<const float2 *>(Ut + pj * kp)[lane];
+                        wv[u] = reinterpret_cast<const float2 *>(Ut + qj * kp)[lane];
+                    }
+#pragma unroll
+                    for (int u = 0; u < JW_UNROLL; ++u) {
+                        if (js[u] < 0) continue;
+                        const float c1 = tj[u].x, s1 = tj[u].y;
+                        const int pj = __float_as_int(tj[u].z), qj = __float_as_int(tj[u].w);
+                        // A J_j on the block's columns, then J_i^T on its rows
+                        const float t00 = c1 * av[u][0] - s1 * av[u][1], t01 = s1 * av[u][0] + c1 * av[u][1];
+                        const float t10 = c1 * av[u][2] - s1 * av[u][3], t11 = s1 * av[u][2] + c1 * av[u][3];
+                        float r00 = t00, r01 = t01, r10 = t10, r11 = t11;
+                        if (act) {
+                            r00 = c * t00 - sn * t10;
+                            r10 = sn * t00 + c * t10;
+                            r01 = c * t01 - sn * t11;
+                            r11 = sn * t01 + c * t11;
+                        }
+                        if (lane == js[u]) { r01 = 0.f; r10 = 0.f; }
+                        rp[pj] = r00;
+                        rp[qj] = r01;
+                        rq[pj] = r10;
+                        rq[qj] = r11;
+                        if (!act) {
+                            A[pj * ld + p] = r00;
+                            A[qj * ld + p] = r01;
+                            A[pj * ld + q] = r10;
+                            A[qj * ld + q] = r11;
+                        }
+                        // U J_j: rows p_j, q_j of U^T
+                        reinterpret_cast<float2 *>(Ut + pj * kp)[lane] =
+                            make_float2(c1 * uv[u].x - s1 * wv[u].x, c1 * uv[u].y - s1 * wv[u].y);
+                        reinterpret_cast<float2 *>(Ut + qj * kp)[lane] =
+                            make_float2(s1 * uv[u].x + c1 * wv[u].x, s1 * uv[u].y + c1 * wv[u].y);
+                    }
+                }
+            }
+            jw_sync<NW>();  // the round's updates
+        }
+        rotations += (unsigned long long)rot;
+        if (rot == 0) { converged = true; break; }
+    }
+    // eigenpairs (indices < k) sorted descending by rank counting
+    float *sg = seg.sig + patch * (int64_t)k;
+    float *u = seg.U + patch * (int64_t)k * k;
+    for (int i = threadIdx.x; i < k; i += NW * 32) {
+        const float di = A[i * ld + i];
+        int rank = 0;
+        for (int j = 0; j < k; ++j) {
+            const float dj = A[j * ld + j];
+            rank += (dj > di) || (dj == di && j < i);
+        }
+        sg[rank] = di;
+        for (int r = 0; r < k; ++r) u[r * k + rank] = Ut[i * kp + r];
+    }
+    if (threadIdx.x == 0) {
+        atomicMax(&ctr->jacobi_max_sweeps, (unsigned long long)(converged ? sweep : max_sweeps));
+        atomicAdd(&ctr->jacobi_rotations, rotations);
+        if (!converged) {
+            atomicAdd(&ctr->jacobi_not_converged, 1ull);
+            atomicOr(&ctr->status, (unsigned)DEV_NOT_CONVERGED);
+        }
+    }
+}
+
+namespace {
+template <int NW>
+cudaError_t launch_jw(const PatchSeg &one, const PatchSeg *tab, int ntab, int kmax, int64_t np, int max_sweeps,
+                      float eps, DevCounters *ctr, cudaStream_t s) {
+    const size_t smem = jw_smem_bytes(kmax);
+    cudaError_t e = cudaFuncSetAttribute(jacobi_warp_kernel<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    jacobi_warp_kernel<NW><<<(unsigned)np, NW * 32, smem, s>>>(one, tab, ntab, max_sweeps, eps, ctr);
+    return cudaGetLastError();
+}
+
+// warps per patch of the fused form (1, 2 or 4)
+cudaError_t launch_jacobi_warp(const PatchSeg &one, const PatchSeg *tab, int ntab, int kmax, int64_t np,
+                               int max_sweeps, float eps, DevCounters *ctr, cudaStream_t s, int nw) {
+    if (nw == 4) return launch_jw<4>(one, tab, ntab, kmax, np, max_sweeps, eps, ctr, s);
+    if (nw == 2) return launch_jw<2>(one, tab, ntab, kmax, np, max_sweeps, eps, ctr, s);
+    return launch_jw<1>(one, tab, ntab, kmax, np, max_sweeps, eps, ctr, s);
+}
+}  // namespace
+
+// ---------------------------------------------------------------------------
 // Refinement of an FP32 eigendecomposition: one step of the iterative
 // refinement for symmetric eigenproblems of Ogita & Aishima (Japan J. Indust.
 // Appl. Math. 35, 2018).  With X the k x k eigenvector estimate from the FP32
@@ -376,17 +584,23 @@ size_t jacobi_smem_bytes(int k, int fp64) {
 }
 
 cudaError_t launch_jacobi_seg(const PatchSeg &one, const PatchSeg *tab, int ntab, int kmax, int64_t np, int fp64,
-                              int max_sweeps, DevCounters *ctr, cudaStream_t s, float pre_eps) {
+                              int max_sweeps, DevCounters *ctr, cudaStream_t s, float pre_eps, int warp_form) {
     if (np <= 0) return cudaSuccess;
     if (kmax > 64 || kmax < 1) return cudaErrorInvalidValue;
     cudaError_t e;
+    // FP32 sweeps: one warp per patch, or one CTA per patch
+    auto sweeps32 = [&](float eps) -> cudaError_t {
+        if (warp_form) return launch_jacobi_warp(one, tab, ntab, kmax, np, max_sweeps, eps, ctr, s, warp_form);
+        const size_t smem = jacobi_smem_bytes(kmax, 0);
+        cudaError_t r = cudaFuncSetAttribute(jacobi_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (r != cudaSuccess) return r;
+        jacobi_kernel<float><<<(unsigned)np, JT, smem, s>>>(one, tab, ntab, max_sweeps, eps, ctr);
+        return cudaGetLastError();
+    };
     if (fp64 == 1 || fp64 == 3) {
         // FP32 sweeps, then one refinement step (3: relative cluster test)
-        const size_t smem = jacobi_smem_bytes(kmax, 0);
-        e = cudaFuncSetAttribute(jacobi_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        jacobi_kernel<float><<<(unsigned)np, JT, smem, s>>>(one, tab, ntab, max_sweeps, pre_eps, ctr);
-        e = cudaGetLastError();
+        e = sweeps32(pre_eps);
         if (e != cudaSuccess) return e;
         const size_t rs = refine_ff_smem_bytes(kmax);
         e = cudaFuncSetAttribute(jacobi_refine_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs);
@@ -394,27 +608,24 @@ cudaError_t launch_jacobi_seg(const PatchSeg &one, const PatchSeg *tab, int ntab
         jacobi_refine_ff_kernel<<<(unsigned)np, FT_REFINE, rs, s>>>(one, tab, ntab, fp64 == 3);
         return cudaGetLastError();
     }
-    const size_t smem = jacobi_smem_bytes(kmax, fp64);
     if (fp64 == 2) {
+        const size_t smem = jacobi_smem_bytes(kmax, fp64);
         e = cudaFuncSetAttribute(jacobi_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         jacobi_kernel<double><<<(unsigned)np, JT, smem, s>>>(one, tab, ntab, max_sweeps, JacobiEps<double>::rel(), ctr);
-    } else {
-        e = cudaFuncSetAttribute(jacobi_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        jacobi_kernel<float><<<(unsigned)np, JT, smem, s>>>(one, tab, ntab, max_sweeps, JacobiEps<float>::rel(), ctr);
+        return cudaGetLastError();
     }
-    return cudaGetLastError();
+    return sweeps32(JacobiEps<float>::rel());
 }
 
 cudaError_t launch_jacobi(const float *G, int k, int64_t np, int fp64, int max_sweeps, float *sigma, float *U,
-                          DevCounters *ctr, cudaStream_t s, float pre_eps) {
+                          DevCounters *ctr, cudaStream_t s, float pre_eps, int warp_form) {
     PatchSeg one{};
     one.k = k;
     one.G = const_cast<float *>(G);
     one.sig = sigma;
     one.U = U;
-    return launch_jacobi_seg(one, nullptr, 0, k, np, fp64, max_sweeps, ctr, s, pre_eps);
+    return launch_jacobi_seg(one, nullptr, 0, k, np, fp64, max_sweeps, ctr, s, pre_eps, warp_form);
 }
 
 }  // namespace mecuco

@@ -18,9 +18,12 @@ struct PatchSeg;
 void set_error_text(const char *msg);
 
 // ---- Step 1: kNN -----------------------------------------------------------
-// Squared row norms |x_i|^2 (FP32 accumulation), i in [0, N).
+// Squared row norms |x_i|^2 (compensated sum, rounded once), i in [0, N).
+// resid (FP32 rows only, else ignored): |x_i - bf16(x_i)| per row, rounded
+// up, with maxima[0..1] (zeroed by the caller) receiving the largest |x_i|^2
+// and residual norm.
 cudaError_t launch_rownorm(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
-                           float *norms, cudaStream_t s);
+                           float *norms, cudaStream_t s, float *resid = nullptr, float *maxima = nullptr);
 
 // Candidate search, plain FP32 on the CUDA cores.  Queries [q0, q0 + nq) against
 // all N rows, candidate range split in `nsplit` parts; per (query, split) the
@@ -51,7 +54,7 @@ int knn_tc_halves();
 // work item / first row).  The tensor maps describe the BF16 operand (xb when
 // a copy is made, else X) with TMA boxes of the search; kcl is each list's
 // capacity, lists = nsplit * knn_tc_halves() lists per row.
-struct alignas(64) KnnSet {
+struct KnnSet {  // aligned as CUtensorMap (the device table needs 64-byte aligned maps)
     CUtensorMap map_a, map_b;
     const void *X;     // the dataset in the call's dtype (row norms, re-rank, fallback)
     void *xb;          // BF16 copy (FP32 inputs), or NULL when X is BF16 with ldb = ld
@@ -61,6 +64,8 @@ struct alignas(64) KnnSet {
     int32_t *cand_i;
     int32_t *flags;    // N
     int32_t *idx;      // N x k, the neighbour lists
+    float *resid;      // N: |x - bf16(x)| of FP32 rows searched through a BF16 copy, else NULL
+    float *maxima;     // 2: the dataset's largest |x|^2 and residual norm (with resid)
     int k, kc, kcl, nsplit, lists, include_self;
     int64_t item_begin;  // first search work item (one query block x one candidate split)
     int64_t row_begin;   // first row in the batch's row order
@@ -109,10 +114,14 @@ cudaError_t launch_to_bf16(const void *X, mecuco_dtype dt, int64_t N, int64_t m,
 // compensated (float-float) sum of (x_a - y_a)^2, top-k by (distance, index),
 // and the certification test; uncertified rows get flags[q - q0] = 1.
 // idx_out / dist_out point at query q0's row (row q - q0 is written).
+// resid / maxima (from launch_rownorm): the search ran on BF16 roundings of
+// FP32 rows; the certification then also covers the rounding's a-priori
+// bound on every candidate's distance error.
 cudaError_t launch_knn_rerank(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
                               const float *norms, int64_t q0, int64_t nq, int kc, int nsplit, int k,
                               const float *cand_d, const int32_t *cand_i, int32_t *idx_out,
-                              float *dist_out, int32_t *flags, DevCounters *ctr, cudaStream_t s);
+                              float *dist_out, int32_t *flags, DevCounters *ctr, cudaStream_t s,
+                              const float *resid = nullptr, const float *maxima = nullptr);
 
 // Exact full scan for the flagged rows of [q0, q0 + nq) (outputs as above).
 cudaError_t launch_knn_fallback(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
@@ -197,13 +206,16 @@ cudaError_t launch_tthird_tc(const PatchSeg &one, const PatchSeg *tab, int ntab,
 // rotated Gram must come out nearly diagonal, take kJacobiPreTight.
 constexpr float kJacobiPreTight = 2.384185791015625e-07f;  // 2^-22
 constexpr float kJacobiPreLoose = 6.103515625e-05f;        // 2^-14
+// warp_form != 0: the FP32 sweeps run one warp per patch (fused 2 x 2 block
+// updates, no block barriers); 0: one CTA of 128 threads per patch.  FP64
+// sweeps (fp64 = 2) always take the CTA form.
 cudaError_t launch_jacobi(const float *G, int k, int64_t np, int fp64, int max_sweeps,
                           float *sigma, float *U, DevCounters *ctr, cudaStream_t s,
-                          float pre_eps = kJacobiPreTight);
+                          float pre_eps = kJacobiPreTight, int warp_form = 1);
 // The same over a segment table (PatchSeg: G, k, sig, U of each segment);
 // kmax bounds every segment's k.
 cudaError_t launch_jacobi_seg(const PatchSeg &one, const PatchSeg *tab, int ntab, int kmax, int64_t np, int fp64,
-                              int max_sweeps, DevCounters *ctr, cudaStream_t s, float pre_eps);
+                              int max_sweeps, DevCounters *ctr, cudaStream_t s, float pre_eps, int warp_form = 1);
 
 // ---- Step 4: k-space estimator ----------------------------------------------
 // sigma/U from launch_jacobi, M pair-major from launch_patch_m3, R and Q from

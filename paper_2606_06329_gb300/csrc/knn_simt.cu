@@ -26,30 +26,56 @@ __device__ __forceinline__ const KnnSet &find_set_row(const KnnSet *sets, int ns
     return sets[lo];
 }
 
+// One warp: |x|^2 of a row as a compensated sum (hi + lo rounded once, so
+// within a few FP32 units of the exact value) and, when resid is not NULL, the
+// norm of the row's BF16 rounding residual |x - bf16(x)| (rounded up), with
+// the dataset's largest |x|^2 and residual norm kept in maxima[0], maxima[1]
+// (non-negative floats, so their bit patterns order as integers).
 template <typename T>
-__global__ void rownorm_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld,
-                               float *__restrict__ out) {
+__device__ __forceinline__ void row_norm_warp(const T *__restrict__ x, int64_t m, int lane, float *norm_out,
+                                              float *resid_out, float *maxima) {
+    ff acc{0.f, 0.f};
+    float racc = 0.f;
+    for (int64_t a = lane; a < m; a += 32) {
+        const float v = load_elem(x + a);
+        ff_acc_sqdiff(acc, v, 0.f);
+        if (resid_out) {
+            const float r = v - __bfloat162float(__float2bfloat16_rn(v));  // exact
+            racc = fmaf(r, r, racc);
+        }
+    }
+    acc = ff_warp_sum(acc);
+    const float n = acc.hi + acc.lo;
+    if (resid_out) racc = warp_sum(racc);
+    if (lane == 0) {
+        *norm_out = n;
+        if (resid_out) {
+            // the FP32 sum of m squares is within m 2^-24 of its value: 2^-10 covers it
+            const float rr = sqrtf(racc) * (1.f + 9.765625e-04f);
+            *resid_out = rr;
+            atomicMax(reinterpret_cast<int *>(maxima), __float_as_int(n));
+            atomicMax(reinterpret_cast<int *>(maxima) + 1, __float_as_int(rr));
+        }
+    }
+}
+
+template <typename T>
+__global__ void rownorm_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, float *__restrict__ out,
+                               float *__restrict__ resid, float *__restrict__ maxima) {
     int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     int lane = threadIdx.x & 31;
     if (row >= N) return;
-    const T *x = X + row * ld;
-    float acc = 0.f;
-    for (int64_t a = lane; a < m; a += 32) {
-        float v = load_elem(x + a);
-        acc = fmaf(v, v, acc);
-    }
-    acc = warp_sum(acc);
-    if (lane == 0) out[row] = acc;
+    row_norm_warp(X + row * ld, m, lane, out + row, resid ? resid + row : nullptr, maxima);
 }
 
 cudaError_t launch_rownorm(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
-                           float *norms, cudaStream_t s) {
+                           float *norms, cudaStream_t s, float *resid, float *maxima) {
     if (N <= 0) return cudaSuccess;
     dim3 block(256), grid((unsigned)((N + 7) / 8));
     if (dt == MECUCO_BF16)
-        rownorm_kernel<<<grid, block, 0, s>>>((const __nv_bfloat16 *)X, N, m, ld, norms);
+        rownorm_kernel<<<grid, block, 0, s>>>((const __nv_bfloat16 *)X, N, m, ld, norms, nullptr, nullptr);
     else
-        rownorm_kernel<<<grid, block, 0, s>>>((const float *)X, N, m, ld, norms);
+        rownorm_kernel<<<grid, block, 0, s>>>((const float *)X, N, m, ld, norms, resid, maxima);
     return cudaGetLastError();
 }
 
@@ -62,14 +88,8 @@ __global__ void rownorm_batch_kernel(const KnnSet *__restrict__ sets, int nsets,
     if (gr >= nrows) return;
     const KnnSet &d = find_set_row(sets, nsets, gr);
     const int64_t row = gr - d.row_begin;
-    const T *x = static_cast<const T *>(d.X) + row * d.ld;
-    float acc = 0.f;
-    for (int64_t a = lane; a < d.m; a += 32) {
-        const float v = load_elem(x + a);
-        acc = fmaf(v, v, acc);
-    }
-    acc = warp_sum(acc);
-    if (lane == 0) d.norms[row] = acc;
+    row_norm_warp(static_cast<const T *>(d.X) + row * d.ld, d.m, lane, d.norms + row,
+                  d.resid ? d.resid + row : nullptr, d.maxima);
 }
 
 cudaError_t launch_rownorm_batch(const KnnSet *sets, int nsets, int64_t nrows, mecuco_dtype dt, cudaStream_t s) {
@@ -274,7 +294,7 @@ knn_rerank_kernel(const T *__restrict__ X_, int64_t N_, int64_t m_, int64_t ld_,
                   const float *__restrict__ cand_d_, const int32_t *__restrict__ cand_i_,
                   int32_t *__restrict__ idx_out_, float *__restrict__ dist_out_,
                   int32_t *__restrict__ flags_, DevCounters *ctr, const KnnSet *__restrict__ sets, int nsets,
-                  int lmax) {
+                  int lmax, const float *__restrict__ resid_, const float *__restrict__ maxima_) {
     extern __shared__ float rsm[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int64_t qi = (int64_t)blockIdx.x * RR_WARPS + w;  // the launch's row (the batch's row when batched)
@@ -286,6 +306,7 @@ knn_rerank_kernel(const T *__restrict__ X_, int64_t N_, int64_t m_, int64_t ld_,
     const int32_t *cand_i = cand_i_;
     int32_t *idx_out = idx_out_, *flags = flags_;
     float *dist_out = dist_out_;
+    const float *resid = resid_, *maxima = maxima_;
     int kc = kc_, nsplit = nsplit_, k = k_;
     if constexpr (BATCH) {
         const KnnSet &d = find_set_row(sets, nsets, qi);
@@ -304,6 +325,8 @@ knn_rerank_kernel(const T *__restrict__ X_, int64_t N_, int64_t m_, int64_t ld_,
         kc = d.kcl;
         nsplit = d.lists;
         k = d.k;
+        resid = d.resid;
+        maxima = d.maxima;
     }
     const int L = kc * nsplit;
     const int LS = BATCH ? lmax : L;  // per-warp shared-memory stride
@@ -420,7 +443,18 @@ knn_rerank_kernel(const T *__restrict__ X_, int64_t N_, int64_t m_, int64_t ld_,
     if (lane == 0 && bad) atomicOr(&ctr->status, (unsigned)DEV_INVALID);
     if (lane == 0) {
         const float spread = err_max - err_min;
-        const float e_hi = fmaxf(err_max, 0.f) + 3.f * spread + ldexpf(norms[q] + nmax, -21);
+        float e_hi = fmaxf(err_max, 0.f) + 3.f * spread + ldexpf(norms[q] + nmax, -21);
+        if (resid) {
+            // BF16 operands rounded from FP32 rows: with x = x~ + dx, y = y~ + dy,
+            // |x.y - x~.y~| <= |x~||dy| + |dx||y~| + |dx||dy| for any candidate y,
+            // bounded with the dataset's largest |y| and |dy| (a-priori, not
+            // estimated from the candidates); the tensor core's FP32
+            // accumulation, ~2^-9 of this for FP32 rows, stays with the estimate
+            const float rq = resid[q], rm = maxima[1], ym = sqrtf(maxima[0]), xq = sqrtf(norms[q]);
+            const float eq = 2.f * ((xq + rq) * rm + rq * (ym + rm) + rq * rm) * (1.f + 9.765625e-04f) +
+                             ldexpf(norms[q] + maxima[0], -21);
+            e_hi = fmaxf(e_hi, eq);
+        }
         int ok = (thr == INFINITY) || (thr - e_hi > theta);
         flags[qi] = ok ? 0 : 1;
         if (!ok) atomicAdd(&ctr->knn_uncertified, 1ull);
@@ -430,7 +464,8 @@ knn_rerank_kernel(const T *__restrict__ X_, int64_t N_, int64_t m_, int64_t ld_,
 cudaError_t launch_knn_rerank(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
                               const float *norms, int64_t q0, int64_t nq, int kc, int nsplit, int k,
                               const float *cand_d, const int32_t *cand_i, int32_t *idx_out,
-                              float *dist_out, int32_t *flags, DevCounters *ctr, cudaStream_t s) {
+                              float *dist_out, int32_t *flags, DevCounters *ctr, cudaStream_t s,
+                              const float *resid, const float *maxima) {
     if (nq <= 0) return cudaSuccess;
     int L = kc * nsplit;
     if (L > RR_MAXL) return cudaErrorInvalidValue;
@@ -443,14 +478,15 @@ cudaError_t launch_knn_rerank(const void *X, mecuco_dtype dt, int64_t N, int64_t
         if (e != cudaSuccess) return e;
         knn_rerank_kernel<__nv_bfloat16, false><<<grid, block, smem, s>>>((const __nv_bfloat16 *)X, N, m, ld, norms,
                                                                           q0, nq, kc, nsplit, k, cand_d, cand_i,
-                                                                          idx_out, dist_out, flags, ctr, nullptr, 0, 0);
+                                                                          idx_out, dist_out, flags, ctr, nullptr, 0, 0,
+                                                                          resid, maxima);
     } else {
         e = cudaFuncSetAttribute(knn_rerank_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
         knn_rerank_kernel<float, false><<<grid, block, smem, s>>>((const float *)X, N, m, ld, norms, q0, nq, kc,
                                                                   nsplit, k, cand_d, cand_i, idx_out, dist_out, flags,
-                                                                  ctr, nullptr, 0, 0);
+                                                                  ctr, nullptr, 0, 0, resid, maxima);
     }
     return cudaGetLastError();
 }
@@ -568,14 +604,14 @@ cudaError_t launch_knn_rerank_batch(const KnnSet *sets, int nsets, int64_t nrows
         if (e != cudaSuccess) return e;
         knn_rerank_kernel<__nv_bfloat16, true><<<grid, block, smem, s>>>(nullptr, 0, 0, 0, nullptr, 0, nrows, 0, 0, 0,
                                                                          nullptr, nullptr, nullptr, nullptr, nullptr,
-                                                                         ctr, sets, nsets, lmax);
+                                                                         ctr, sets, nsets, lmax, nullptr, nullptr);
     } else {
         e = cudaFuncSetAttribute(knn_rerank_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
         knn_rerank_kernel<float, true><<<grid, block, smem, s>>>(nullptr, 0, 0, 0, nullptr, 0, nrows, 0, 0, 0, nullptr,
                                                                  nullptr, nullptr, nullptr, nullptr, ctr, sets, nsets,
-                                                                 lmax);
+                                                                 lmax, nullptr, nullptr);
     }
     return cudaGetLastError();
 }
