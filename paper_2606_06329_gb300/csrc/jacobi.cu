@@ -438,7 +438,8 @@ __device__ __forceinline__ int tri(int a, int b, int k) { return a * k - (a * (a
 
 constexpr int FT_REFINE = 256;
 
-__global__ void __launch_bounds__(FT_REFINE, 2)
+template <int NT>
+__global__ void __launch_bounds__(NT, 512 / NT)
 jacobi_refine_ff_kernel(const __grid_constant__ PatchSeg one, const PatchSeg *__restrict__ tab, int ntab, int rel) {
     extern __shared__ __align__(16) unsigned char fsm[];
     int local;
@@ -463,14 +464,14 @@ jacobi_refine_ff_kernel(const __grid_constant__ PatchSeg one, const PatchSeg *__
     const float *g = G + pt * (int64_t)k * k;
     float *u = U + pt * (int64_t)k * k;
     const int kk = k * k;
-    for (int e = tid; e < kk; e += FT_REFINE) {
+    for (int e = tid; e < kk; e += NT) {
         const int r = e / k, c = e - r * k;
         A[r * ld + c] = g[e];
         X[r * ld + c] = u[e];
     }
     __syncthreads();
     // T = A X: four outputs of one row per thread pass (independent chains)
-    for (int q = tid; q * 4 < kk; q += FT_REFINE) {
+    for (int q = tid; q * 4 < kk; q += NT) {
         const int e0 = q * 4;
         float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
         int rr[4], cc[4];
@@ -493,7 +494,7 @@ jacobi_refine_ff_kernel(const __grid_constant__ PatchSeg one, const PatchSeg *__
     }
     __syncthreads();
     // S = X^T T and R = X^T X on the upper triangle, two outputs per thread pass
-    for (int q = tid; q * 2 < ntri; q += FT_REFINE) {
+    for (int q = tid; q * 2 < ntri; q += NT) {
         int ra[2], ca[2];
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
@@ -540,7 +541,7 @@ jacobi_refine_ff_kernel(const __grid_constant__ PatchSeg one, const PatchSeg *__
     __syncthreads();
     const double delta = 3.814697265625e-06 * s_lmax;  // 2^-18 max|lam|
     float *Ef = A;  // A is no longer needed
-    for (int e = tid; e < kk; e += FT_REFINE) {
+    for (int e = tid; e < kk; e += NT) {
         const int i = e / k, j = e - i * k;
         const int a = i < j ? i : j, b = i < j ? j : i;
         const double rij = Rd(a, b);
@@ -554,7 +555,7 @@ jacobi_refine_ff_kernel(const __grid_constant__ PatchSeg one, const PatchSeg *__
     __syncthreads();
     // X' = X + X E (FP32), into Th
     float *Xn = Th;
-    for (int e = tid; e < kk; e += FT_REFINE) {
+    for (int e = tid; e < kk; e += NT) {
         const int r = e / k, c = e - r * k;
         float t = 0.f;
         for (int j = 0; j < k; ++j) t = fmaf(X[r * ld + j], Ef[j * ld + c], t);
@@ -562,7 +563,7 @@ jacobi_refine_ff_kernel(const __grid_constant__ PatchSeg one, const PatchSeg *__
     }
     __syncthreads();
     float *sg = sigma + pt * (int64_t)k;
-    for (int i = tid; i < k; i += FT_REFINE) {
+    for (int i = tid; i < k; i += NT) {
         int rank = 0;
         for (int j = 0; j < k; ++j) rank += (lam[j] > lam[i]) || (lam[j] == lam[i] && j < i);
         sg[rank] = (float)lam[i];
@@ -602,11 +603,18 @@ cudaError_t launch_jacobi_seg(const PatchSeg &one, const PatchSeg *tab, int ntab
         // FP32 sweeps, then one refinement step (3: relative cluster test)
         e = sweeps32(pre_eps);
         if (e != cudaSuccess) return e;
+        // threads per patch: 64 (k <= 16), 128 (k <= 32) or 256, so that small
+        // patches are not limited to 8 per SM by idle threads
         const size_t rs = refine_ff_smem_bytes(kmax);
-        e = cudaFuncSetAttribute(jacobi_refine_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs);
-        if (e != cudaSuccess) return e;
-        jacobi_refine_ff_kernel<<<(unsigned)np, FT_REFINE, rs, s>>>(one, tab, ntab, fp64 == 3);
-        return cudaGetLastError();
+        auto refine = [&](auto kern, int nt) -> cudaError_t {
+            cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs);
+            if (r != cudaSuccess) return r;
+            kern<<<(unsigned)np, nt, rs, s>>>(one, tab, ntab, fp64 == 3);
+            return cudaGetLastError();
+        };
+        if (kmax <= 16) return refine(jacobi_refine_ff_kernel<64>, 64);
+        if (kmax <= 32) return refine(jacobi_refine_ff_kernel<128>, 128);
+        return refine(jacobi_refine_ff_kernel<FT_REFINE>, FT_REFINE);
     }
     if (fp64 == 2) {
         const size_t smem = jacobi_smem_bytes(kmax, fp64);
