@@ -136,13 +136,20 @@ typedef enum {
                                         over a device table of all datasets' work items, estimator launches
                                         over segment tables of all datasets' points); 0: one stream lane per
                                         dataset group, as the FP32 form always does.  Results identical */
-    MECUCO_OPT_JACOBI_WARP = 16      /* FP32 Jacobi sweeps: 1, 2 (default) or 4 warps per patch in the fused
+    MECUCO_OPT_JACOBI_WARP = 16,     /* FP32 Jacobi sweeps: 1, 2 (default) or 4 warps per patch in the fused
                                         form (a round's rotations applied in one pass over 2 x 2 blocks of A
                                         and U, two barriers per round, none with 1 warp); 0: one CTA of 128
                                         threads per patch in three passes (row, column and eigenvector
                                         updates, three barriers per round).  Same rotations and thresholds;
                                         the results differ only by rounding order.  Measured on 100k patches
                                         (k = 64): 230 ms (0), 221 (1), 192 (2), 192 (4) */
+    MECUCO_OPT_KNN_SPLIT_BF16 = 17   /* BF16-mixed kNN of FP32 rows: 1 (default) the tensor-core search runs on
+                                        the three-term split of each row (h = bf16(x), l = bf16(x - h); one GEMM
+                                        over [h|h|l] . [h|l|h], three times the K of one rounding) and the
+                                        certificate bounds its rounding error a priori at ~2^-16 relative;
+                                        0: one BF16 rounding, a third of the search but a ~2^-8 bound, which
+                                        sends most rows of clustered FP32 data to the exact scan.  The lists
+                                        are identical either way */
 } mecuco_option;
 
 /* Kernel stages, for mecuco_get_stage_times. */

@@ -18,7 +18,8 @@ FAST_LITERAL, FAST_HAAR = 0, 1
 PREC_FP32, PREC_BF16_MIXED = 0, 1
 (OPT_KNN_MARGIN, OPT_JACOBI_FP64, OPT_JACOBI_MAX_SWEEPS, OPT_CHUNK_POINTS, OPT_KNN_QUERY_CHUNK, OPT_PROFILE,
  OPT_KNN_SPLITS, OPT_BATCH_LANES, OPT_TC_SLOTS, OPT_KNN_PAIR, OPT_WAIT_LIMIT, OPT_WORKSPACE_LIMIT,
- OPT_PROFILE_STAGES, OPT_TT_SLOTS, OPT_TT_CTAS, OPT_BATCH_PERSISTENT, OPT_JACOBI_WARP) = range(17)
+ OPT_PROFILE_STAGES, OPT_TT_SLOTS, OPT_TT_CTAS, OPT_BATCH_PERSISTENT, OPT_JACOBI_WARP,
+ OPT_KNN_SPLIT_BF16) = range(18)
 STAGES = ("rownorm", "knn_search", "knn_rerank", "knn_fallback", "gram", "moments", "jacobi", "estimator", "adjoint",
           "basis", "exact", "fidelity", "rotate")
 

@@ -66,6 +66,7 @@ struct mecuco_ctx {
     int32_t *tttab[65] = {};     // per k: row codes of the third-moment pass (pairs only)
     int knn_splits = 0;
     int knn_pair = -1;  // -1: CTA pairs for N >= KNN_PAIR_MIN_N
+    int knn_split_bf16 = 1;  // FP32 rows: three-term BF16 split in the tensor-core search
     int chunk_share = 1;  // concurrent lanes sharing the chunk budget (batched calls)
     int tc_slots = 4;
     // third-moment pass: TMEM slots of the A operand and CTAs per SM; two CTAs
@@ -235,9 +236,13 @@ struct KnnPlan {
     bool tc;        // candidate search on the tensor cores (BF16 operands)
     bool pair;      // tensor-core search as CTA pairs sharing two-SM MMAs
     bool bf16_copy; // the tensor-core path needs a BF16 copy of X
-    bool quant;     // the search reads BF16 roundings of FP32 rows (certification bounds their error)
-    int64_t ldb;    // leading dimension of the BF16 operand
+    int quant;      // KNN_QUANT_*: how the search sees FP32 rows (the certification bounds it)
+    int64_t ldb;    // leading dimension of the BF16 operand(s)
+    int64_t mk;     // their K (m, or 3 ms for the three-term split)
 };
+
+// Segment width of the three-term split: m rounded up to whole 16-byte units.
+inline int64_t split_segment(int64_t m) { return (m + 7) / 8 * 8; }
 
 KnnPlan plan_knn(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, int64_t nrows, int k,
                  mecuco_precision prec) {
@@ -251,8 +256,13 @@ KnnPlan plan_knn(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t 
     p.pair = p.tc && (h->knn_pair > 0 || (h->knn_pair < 0 && N >= KNN_PAIR_MIN_N));
     const bool direct = dt == MECUCO_BF16 && ld % 8 == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
     p.bf16_copy = p.tc && !direct;
-    p.quant = p.tc && dt == MECUCO_F32;
-    p.ldb = direct ? ld : (m + 7) / 8 * 8;
+    // FP32 rows: the three-term split (a search three times as long in K whose
+    // rounding bound is ~2^8 smaller, so that the certificate holds where a
+    // single rounding's would send most rows to the exact scan), unless
+    // MECUCO_OPT_KNN_SPLIT_BF16 = 0
+    p.quant = !(p.tc && dt == MECUCO_F32) ? KNN_QUANT_NONE : (h->knn_split_bf16 ? KNN_QUANT_SPLIT : KNN_QUANT_SINGLE);
+    p.mk = p.quant == KNN_QUANT_SPLIT ? 3 * split_segment(m) : m;
+    p.ldb = direct ? ld : (p.mk + 7) / 8 * 8;
     p.qchunk = h->knn_qchunk > 0 ? h->knn_qchunk : (int64_t)1 << 18;
     if (p.qchunk > nrows) p.qchunk = nrows;
     // keep every SM busy (tensor-core kernel: 1 CTA/SM; CUDA-core kernel: 2):
@@ -277,8 +287,8 @@ KnnPlan plan_knn(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t 
 struct KnnBufs {
     float *norms, *cand_d;
     int32_t *cand_i, *flags;
-    void *xb;
-    float *resid, *maxima;  // BF16 rounding residuals of FP32 rows (tensor-core search), else NULL
+    void *xb, *xb2;         // BF16 operand copies (query, and candidate for the split), else NULL
+    float *resid, *maxima;  // BF16 rounding terms of FP32 rows (tensor-core search), else NULL
 };
 
 // Scratch of run_knn, carved after `start`.
@@ -288,8 +298,9 @@ void knn_scratch(Carver &c, const KnnPlan &p, int64_t N, KnnBufs *b) {
     b->cand_i = c.take<int32_t>((size_t)p.qchunk * p.lists * p.kcl);
     b->flags = c.take<int32_t>((size_t)p.qchunk);
     b->xb = p.bf16_copy ? (void *)c.take<uint16_t>((size_t)N * p.ldb) : nullptr;
-    b->resid = p.quant ? c.take<float>((size_t)N) : nullptr;
-    b->maxima = p.quant ? c.take<float>(2) : nullptr;
+    b->xb2 = p.quant == KNN_QUANT_SPLIT ? (void *)c.take<uint16_t>((size_t)N * p.ldb) : nullptr;
+    b->resid = p.quant ? c.take<float>((size_t)2 * N) : nullptr;
+    b->maxima = p.quant ? c.take<float>(3) : nullptr;
 }
 
 // kNN of query rows [rb, re) (outputs relative to rb); scratch at ws + start,
@@ -301,13 +312,18 @@ mecuco_status run_knn(mecuco_t h, char *ws, const void *X, mecuco_dtype dt, int6
     Carver c(ws, start);
     KnnBufs b;
     knn_scratch(c, p, N, &b);
-    if (b.maxima) CK(cudaMemsetAsync(b.maxima, 0, 2 * sizeof(float), s));
-    LAUNCH(h, MECUCO_STAGE_ROWNORM, s, launch_rownorm(X, dt, N, m, ld, b.norms, s, b.resid, b.maxima));
-    const void *Xb = X;
-    if (p.bf16_copy) {
+    if (b.maxima) CK(cudaMemsetAsync(b.maxima, 0, 3 * sizeof(float), s));
+    LAUNCH(h, MECUCO_STAGE_ROWNORM, s, launch_rownorm(X, dt, N, m, ld, b.norms, s, b.resid, b.maxima, p.quant));
+    const void *Xa = X, *Xb = X;
+    if (p.quant == KNN_QUANT_SPLIT) {
+        CK(launch_to_bf16_split(static_cast<const float *>(X), N, m, ld, b.xb, b.xb2, split_segment(m), p.ldb, s));
+        ++h->launches;
+        Xa = b.xb;
+        Xb = b.xb2;
+    } else if (p.bf16_copy) {
         CK(launch_to_bf16(X, dt, N, m, ld, b.xb, p.ldb, s));
         ++h->launches;
-        Xb = b.xb;
+        Xa = Xb = b.xb;
     }
     for (int64_t q0 = rb; q0 < re; q0 += p.qchunk) {
         int64_t nq = std::min(p.qchunk, re - q0);
@@ -315,7 +331,7 @@ mecuco_status run_knn(mecuco_t h, char *ws, const void *X, mecuco_dtype dt, int6
         float *dout = dist_out ? dist_out + (q0 - rb) * k : nullptr;
         if (p.tc) {
             LAUNCH(h, MECUCO_STAGE_KNN_SEARCH, s,
-                   launch_knn_tc(Xb, N, m, p.ldb, b.norms, q0, nq, p.kcl, p.nsplit, include_self, b.cand_d,
+                   launch_knn_tc(Xa, Xb, N, p.mk, p.ldb, b.norms, q0, nq, p.kcl, p.nsplit, include_self, b.cand_d,
                                  b.cand_i, p.pair ? 1 : 0, h->wait_limit, h->ctr, s));
         } else {
             LAUNCH(h, MECUCO_STAGE_KNN_SEARCH, s,
@@ -327,7 +343,7 @@ mecuco_status run_knn(mecuco_t h, char *ws, const void *X, mecuco_dtype dt, int6
         // bounds every candidate left out
         LAUNCH(h, MECUCO_STAGE_KNN_RERANK, s,
                launch_knn_rerank(X, dt, N, m, ld, b.norms, q0, nq, p.kcl, p.lists, k, b.cand_d, b.cand_i, io, dout,
-                                 b.flags, h->ctr, s, b.resid, b.maxima));
+                                 b.flags, h->ctr, s, b.resid, b.maxima, p.quant));
         LAUNCH(h, MECUCO_STAGE_KNN_FALLBACK, s,
                launch_knn_fallback(X, dt, N, m, ld, q0, nq, k, include_self, b.flags, io, dout, h->ctr, s));
     }
@@ -750,13 +766,16 @@ mecuco_status plan_batch(mecuco_t h, const mecuco_dataset *sets, int nsets, mecu
         while (e.nsplit > 1 && (d.N + e.nsplit - 1) / e.nsplit < e.kc) --e.nsplit;
         e.lists = e.nsplit * halves;
         const bool direct = dt == MECUCO_BF16 && d.ld % 8 == 0 && (reinterpret_cast<uintptr_t>(d.X) & 15) == 0;
-        e.ldb = direct ? d.ld : (d.m + 7) / 8 * 8;
+        e.quant = dt != MECUCO_F32 ? KNN_QUANT_NONE : (h->knn_split_bf16 ? KNN_QUANT_SPLIT : KNN_QUANT_SINGLE);
+        e.mk = e.quant == KNN_QUANT_SPLIT ? 3 * split_segment(d.m) : d.m;
+        e.ldb = direct ? d.ld : (e.mk + 7) / 8 * 8;
         e.norms = c.take<float>((size_t)d.N);
         e.cand_d = c.take<float>((size_t)d.N * e.lists * e.kcl);
         e.cand_i = c.take<int32_t>((size_t)d.N * e.lists * e.kcl);
         e.flags = c.take<int32_t>((size_t)d.N);
         e.xb = direct ? nullptr : (void *)c.take<uint16_t>((size_t)d.N * e.ldb);
-        e.resid = dt == MECUCO_F32 ? c.take<float>((size_t)d.N) : nullptr;
+        e.xb2 = e.quant == KNN_QUANT_SPLIT ? (void *)c.take<uint16_t>((size_t)d.N * e.ldb) : nullptr;
+        e.resid = e.quant ? c.take<float>((size_t)2 * d.N) : nullptr;
         e.item_begin = p.nitems;
         e.row_begin = p.nrows;
         p.nitems += (d.N + qrows - 1) / qrows * e.nsplit;
@@ -766,12 +785,12 @@ mecuco_status plan_batch(mecuco_t h, const mecuco_dataset *sets, int nsets, mecu
         p.kmax = std::max(p.kmax, d.k);
         p.any_copy = p.any_copy || !direct;
     }
-    // the datasets' residual maxima, contiguous (one memset per call)
-    p.maxima = dt == MECUCO_F32 ? c.take<float>((size_t)2 * nsets) : nullptr;
-    for (int t = 0; t < nsets && p.maxima; ++t) p.knn[t].maxima = p.maxima + 2 * t;
+    // the datasets' rounding maxima, contiguous (one memset per call)
+    p.maxima = dt == MECUCO_F32 ? c.take<float>((size_t)3 * nsets) : nullptr;
+    for (int t = 0; t < nsets && p.maxima; ++t) p.knn[t].maxima = p.maxima + 3 * t;
     if (base) {
         for (int t = 0; t < nsets; ++t) {
-            if (!knn_tc_make_maps(&p.knn[t])) {
+            if (!knn_tc_make_maps(&p.knn[t], pair)) {
                 set_error_text("batched kNN: a dataset's operand cannot be described by a tensor map");
                 return MECUCO_ERR_INVALID_ARG;
             }
@@ -897,7 +916,7 @@ mecuco_status run_batched_persistent(mecuco_t h, const mecuco_dataset *sets, int
     CK(launch_batch_patch(kt, nsets, sg, refs, (int)p.segs.size(), p.outs.data(), s));
     h->launches += (nsets + BATCH_PATCH_SETS - 1) / BATCH_PATCH_SETS;
     // kNN of every row of every dataset: one launch per stage
-    if (p.maxima) CK(cudaMemsetAsync(p.maxima, 0, 2 * sizeof(float) * nsets, s));
+    if (p.maxima) CK(cudaMemsetAsync(p.maxima, 0, 3 * sizeof(float) * nsets, s));
     LAUNCH(h, MECUCO_STAGE_ROWNORM, s, launch_rownorm_batch(kt, nsets, p.nrows, dt, s));
     if (p.any_copy) {
         CK(launch_to_bf16_batch(kt, nsets, p.nrows, dt, s));
@@ -1110,6 +1129,10 @@ mecuco_status mecuco_set_option(mecuco_t h, mecuco_option opt, int64_t v) {
         case MECUCO_OPT_JACOBI_WARP:
             if (v != 0 && v != 1 && v != 2 && v != 4) return MECUCO_ERR_INVALID_ARG;
             h->jacobi_warp = (int)v;
+            break;
+        case MECUCO_OPT_KNN_SPLIT_BF16:
+            if (v != 0 && v != 1) return MECUCO_ERR_INVALID_ARG;
+            h->knn_split_bf16 = (int)v;
             break;
         case MECUCO_OPT_BATCH_PERSISTENT:
             if (v != 0 && v != 1) return MECUCO_ERR_INVALID_ARG;

@@ -18,12 +18,18 @@ struct PatchSeg;
 void set_error_text(const char *msg);
 
 // ---- Step 1: kNN -----------------------------------------------------------
+// How the tensor-core search sees FP32 rows (KNN_QUANT_*): not at all (BF16
+// rows, or the CUDA-core search), as one BF16 rounding h = bf16(x), or as the
+// three-term split (h, l = bf16(x - h)) of launch_to_bf16_split.
+enum { KNN_QUANT_NONE = 0, KNN_QUANT_SINGLE = 1, KNN_QUANT_SPLIT = 2 };
 // Squared row norms |x_i|^2 (compensated sum, rounded once), i in [0, N).
-// resid (FP32 rows only, else ignored): |x_i - bf16(x_i)| per row, rounded
-// up, with maxima[0..1] (zeroed by the caller) receiving the largest |x_i|^2
-// and residual norm.
+// With quant != KNN_QUANT_NONE (FP32 rows only), resid[2 i .. 2 i + 1] gets the
+// row's rounding terms, rounded up: single rounding |x - h| and 0; split
+// |l| and |x - h - l|; maxima[0..2] (zeroed by the caller) receives the
+// dataset's largest |x|^2 and the largest of each term.
 cudaError_t launch_rownorm(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
-                           float *norms, cudaStream_t s, float *resid = nullptr, float *maxima = nullptr);
+                           float *norms, cudaStream_t s, float *resid = nullptr, float *maxima = nullptr,
+                           int quant = KNN_QUANT_NONE);
 
 // Candidate search, plain FP32 on the CUDA cores.  Queries [q0, q0 + nq) against
 // all N rows, candidate range split in `nsplit` parts; per (query, split) the
@@ -35,14 +41,16 @@ cudaError_t launch_knn_simt(const void *X, mecuco_dtype dt, int64_t N, int64_t m
 
 // Candidate search, BF16 operands on the tensor cores (tcgen05, TMEM accumulators,
 // TMA-fed shared memory): the output contract of launch_knn_simt with
-// knn_tc_halves() lists of capacity kc per row and split.  Xb is BF16 row-major
-// with ldb % 8 == 0 and a 16-byte aligned base (X itself when it is stored that
-// way, else a copy made by launch_to_bf16).  kc <= 64.
+// knn_tc_halves() lists of capacity kc per row and split.  Xa (query operand)
+// and Xb (candidate operand) are BF16 row-major with K = m columns, ldb % 8 ==
+// 0 and 16-byte aligned bases: both X itself when it is stored that way, both
+// the copy of launch_to_bf16, or the two copies of launch_to_bf16_split (then
+// m is their K = 3 ms).  kc <= 64.
 // pair != 0 (and nq >= 256): CTA pairs sharing 256 x 256 cta_group::2 MMAs;
 // the lists are the same.  wait_limit: clock cycles after which a wait of the
 // work loops gives up (MECUCO_ERR_TIMEOUT); <= 0 selects the default (~0.5 s).
 // The drains of copies and MMAs in flight always use the default.
-cudaError_t launch_knn_tc(const void *Xb, int64_t N, int64_t m, int64_t ldb, const float *norms,
+cudaError_t launch_knn_tc(const void *Xa, const void *Xb, int64_t N, int64_t m, int64_t ldb, const float *norms,
                           int64_t q0, int64_t nq, int kc, int nsplit, int include_self,
                           float *cand_d, int32_t *cand_i, int pair, long long wait_limit, DevCounters *ctr,
                           cudaStream_t s);
@@ -51,27 +59,30 @@ size_t knn_tc_smem_bytes(int kc);
 // column halves); list h of row r, split s starts at ((r nsplit + s) halves + h) kc.
 int knn_tc_halves();
 // One dataset of a batched kNN (a device table of them, sorted by first
-// work item / first row).  The tensor maps describe the BF16 operand (xb when
-// a copy is made, else X) with TMA boxes of the search; kcl is each list's
+// work item / first row).  The tensor maps describe the BF16 operands (the
+// query copy xb and candidate copy xb2 of a three-term split, one copy xb, or
+// X itself) with TMA boxes of the search, K = mk columns; kcl is each list's
 // capacity, lists = nsplit * knn_tc_halves() lists per row.
 struct KnnSet {  // aligned as CUtensorMap (the device table needs 64-byte aligned maps)
     CUtensorMap map_a, map_b;
     const void *X;     // the dataset in the call's dtype (row norms, re-rank, fallback)
-    void *xb;          // BF16 copy (FP32 inputs), or NULL when X is BF16 with ldb = ld
-    int64_t N, m, ld, ldb;
+    void *xb;          // BF16 (query) copy, or NULL when X is BF16 with ldb = ld
+    void *xb2;         // candidate copy of the three-term split, else NULL
+    int64_t N, m, ld, ldb, mk;
     float *norms;      // N
     float *cand_d;     // N x lists x kcl
     int32_t *cand_i;
     int32_t *flags;    // N
     int32_t *idx;      // N x k, the neighbour lists
-    float *resid;      // N: |x - bf16(x)| of FP32 rows searched through a BF16 copy, else NULL
-    float *maxima;     // 2: the dataset's largest |x|^2 and residual norm (with resid)
+    float *resid;      // 2 N: the rows' rounding terms (launch_rownorm), or NULL
+    float *maxima;     // 3: their maxima and the largest |x|^2 (with resid)
     int k, kc, kcl, nsplit, lists, include_self;
+    int quant;         // KNN_QUANT_*
     int64_t item_begin;  // first search work item (one query block x one candidate split)
     int64_t row_begin;   // first row in the batch's row order
 };
-// Fill the two tensor maps of a table entry (host).
-bool knn_tc_make_maps(KnnSet *d);
+// Fill the two tensor maps of a table entry for the search form (host).
+bool knn_tc_make_maps(KnnSet *d, int pair);
 // The tensor-core search over every dataset of a batch in one persistent launch:
 // nitems work items in all (the sum of each set's query blocks x splits, query
 // blocks of knn_tc_item_rows(pair) rows), kcmax the largest list capacity.
@@ -106,6 +117,11 @@ cudaError_t launch_knn_rerank_batch(const KnnSet *sets, int nsets, int64_t nrows
 cudaError_t launch_knn_fallback_batch(const KnnSet *sets, int nsets, int64_t nrows, int kmax, mecuco_dtype dt,
                                       DevCounters *ctr, cudaStream_t s);
 
+// The three-term split of FP32 rows: query copy Ya = [h | h | l], candidate
+// copy Yb = [h | l | h] in segments of ms >= m columns (ms % 8 == 0, zero past
+// m), leading dimension ldb >= 3 ms.
+cudaError_t launch_to_bf16_split(const float *X, int64_t N, int64_t m, int64_t ld, void *Ya, void *Yb, int64_t ms,
+                                 int64_t ldb, cudaStream_t s);
 // BF16 copy of X (round to nearest even) with leading dimension ldb >= m.
 cudaError_t launch_to_bf16(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, void *Y,
                            int64_t ldb, cudaStream_t s);
@@ -121,7 +137,8 @@ cudaError_t launch_knn_rerank(const void *X, mecuco_dtype dt, int64_t N, int64_t
                               const float *norms, int64_t q0, int64_t nq, int kc, int nsplit, int k,
                               const float *cand_d, const int32_t *cand_i, int32_t *idx_out,
                               float *dist_out, int32_t *flags, DevCounters *ctr, cudaStream_t s,
-                              const float *resid = nullptr, const float *maxima = nullptr);
+                              const float *resid = nullptr, const float *maxima = nullptr,
+                              int quant = KNN_QUANT_NONE);
 
 // Exact full scan for the flagged rows of [q0, q0 + nq) (outputs as above).
 cudaError_t launch_knn_fallback(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,

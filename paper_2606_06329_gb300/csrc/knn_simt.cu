@@ -27,55 +27,70 @@ __device__ __forceinline__ const KnnSet &find_set_row(const KnnSet *sets, int ns
 }
 
 // One warp: |x|^2 of a row as a compensated sum (hi + lo rounded once, so
-// within a few FP32 units of the exact value) and, when resid is not NULL, the
-// norm of the row's BF16 rounding residual |x - bf16(x)| (rounded up), with
-// the dataset's largest |x|^2 and residual norm kept in maxima[0], maxima[1]
-// (non-negative floats, so their bit patterns order as integers).
+// within a few FP32 units of the exact value) and, for quant != NONE, the
+// norms of the row's BF16 rounding terms (rounded up) into resid[0..1]:
+// single rounding h = bf16(x): |x - h| and 0; three-term split, l = bf16(x - h):
+// |l| and |x - h - l| (both differences exact in FP32).  The dataset's largest
+// |x|^2 and terms go to maxima[0..2] (non-negative floats, so their bit
+// patterns order as integers).
 template <typename T>
 __device__ __forceinline__ void row_norm_warp(const T *__restrict__ x, int64_t m, int lane, float *norm_out,
-                                              float *resid_out, float *maxima) {
+                                              float *resid_out, float *maxima, int quant) {
     ff acc{0.f, 0.f};
-    float racc = 0.f;
+    float a1 = 0.f, a2 = 0.f;
     for (int64_t a = lane; a < m; a += 32) {
         const float v = load_elem(x + a);
         ff_acc_sqdiff(acc, v, 0.f);
-        if (resid_out) {
-            const float r = v - __bfloat162float(__float2bfloat16_rn(v));  // exact
-            racc = fmaf(r, r, racc);
+        if (quant != KNN_QUANT_NONE) {
+            const float r = v - __bfloat162float(__float2bfloat16_rn(v));
+            if (quant == KNN_QUANT_SINGLE) {
+                a1 = fmaf(r, r, a1);
+            } else {
+                const float l = __bfloat162float(__float2bfloat16_rn(r));
+                const float r2 = r - l;
+                a1 = fmaf(l, l, a1);
+                a2 = fmaf(r2, r2, a2);
+            }
         }
     }
     acc = ff_warp_sum(acc);
     const float n = acc.hi + acc.lo;
-    if (resid_out) racc = warp_sum(racc);
+    if (quant != KNN_QUANT_NONE) {
+        a1 = warp_sum(a1);
+        a2 = warp_sum(a2);
+    }
     if (lane == 0) {
         *norm_out = n;
-        if (resid_out) {
-            // the FP32 sum of m squares is within m 2^-24 of its value: 2^-10 covers it
-            const float rr = sqrtf(racc) * (1.f + 9.765625e-04f);
-            *resid_out = rr;
+        if (quant != KNN_QUANT_NONE) {
+            // the FP32 sums of m squares are within m 2^-24 of their values: 2^-10 covers it
+            const float t1 = sqrtf(a1) * (1.f + 9.765625e-04f), t2 = sqrtf(a2) * (1.f + 9.765625e-04f);
+            resid_out[0] = t1;
+            resid_out[1] = t2;
             atomicMax(reinterpret_cast<int *>(maxima), __float_as_int(n));
-            atomicMax(reinterpret_cast<int *>(maxima) + 1, __float_as_int(rr));
+            atomicMax(reinterpret_cast<int *>(maxima) + 1, __float_as_int(t1));
+            atomicMax(reinterpret_cast<int *>(maxima) + 2, __float_as_int(t2));
         }
     }
 }
 
 template <typename T>
 __global__ void rownorm_kernel(const T *__restrict__ X, int64_t N, int64_t m, int64_t ld, float *__restrict__ out,
-                               float *__restrict__ resid, float *__restrict__ maxima) {
+                               float *__restrict__ resid, float *__restrict__ maxima, int quant) {
     int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     int lane = threadIdx.x & 31;
     if (row >= N) return;
-    row_norm_warp(X + row * ld, m, lane, out + row, resid ? resid + row : nullptr, maxima);
+    row_norm_warp(X + row * ld, m, lane, out + row, quant ? resid + 2 * row : nullptr, maxima, quant);
 }
 
 cudaError_t launch_rownorm(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld,
-                           float *norms, cudaStream_t s, float *resid, float *maxima) {
+                           float *norms, cudaStream_t s, float *resid, float *maxima, int quant) {
     if (N <= 0) return cudaSuccess;
+    if (dt == MECUCO_BF16 || !resid || !maxima) quant = KNN_QUANT_NONE;
     dim3 block(256), grid((unsigned)((N + 7) / 8));
     if (dt == MECUCO_BF16)
-        rownorm_kernel<<<grid, block, 0, s>>>((const __nv_bfloat16 *)X, N, m, ld, norms, nullptr, nullptr);
+        rownorm_kernel<<<grid, block, 0, s>>>((const __nv_bfloat16 *)X, N, m, ld, norms, nullptr, nullptr, quant);
     else
-        rownorm_kernel<<<grid, block, 0, s>>>((const float *)X, N, m, ld, norms, resid, maxima);
+        rownorm_kernel<<<grid, block, 0, s>>>((const float *)X, N, m, ld, norms, resid, maxima, quant);
     return cudaGetLastError();
 }
 
@@ -89,7 +104,7 @@ __global__ void rownorm_batch_kernel(const KnnSet *__restrict__ sets, int nsets,
     const KnnSet &d = find_set_row(sets, nsets, gr);
     const int64_t row = gr - d.row_begin;
     row_norm_warp(static_cast<const T *>(d.X) + row * d.ld, d.m, lane, d.norms + row,
-                  d.resid ? d.resid + row : nullptr, d.maxima);
+                  d.quant ? d.resid + 2 * row : nullptr, d.maxima, d.quant);
 }
 
 cudaError_t launch_rownorm_batch(const KnnSet *sets, int nsets, int64_t nrows, mecuco_dtype dt, cudaStream_t s) {
@@ -112,7 +127,21 @@ __global__ void to_bf16_batch_kernel(const KnnSet *__restrict__ sets, int nsets,
     const int64_t row = gr - d.row_begin;
     const T *x = static_cast<const T *>(d.X) + row * d.ld;
     __nv_bfloat16 *y = static_cast<__nv_bfloat16 *>(d.xb) + row * d.ldb;
-    for (int64_t a = lane; a < d.ldb; a += 32) y[a] = __float2bfloat16_rn(a < d.m ? load_elem(x + a) : 0.f);
+    if (!d.xb2) {
+        for (int64_t a = lane; a < d.ldb; a += 32) y[a] = __float2bfloat16_rn(a < d.m ? load_elem(x + a) : 0.f);
+        return;
+    }
+    // three-term split (as launch_to_bf16_split): query [h | h | l], candidate [h | l | h]
+    __nv_bfloat16 *yb = static_cast<__nv_bfloat16 *>(d.xb2) + row * d.ldb;
+    const int64_t ms = d.mk / 3;
+    for (int64_t a = lane; a < d.ldb; a += 32) {
+        const int64_t seg = a / ms, c = a - seg * ms;
+        const float v = (seg < 3 && c < d.m) ? load_elem(x + c) : 0.f;
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+        y[a] = seg == 2 ? l : h;
+        yb[a] = seg == 1 ? l : h;
+    }
 }
 
 cudaError_t launch_to_bf16_batch(const KnnSet *sets, int nsets, int64_t nrows, mecuco_dtype dt, cudaStream_t s) {
@@ -294,7 +323,7 @@ knn_rerank_kernel(const T *__restrict__ X_, int64_t N_, int64_t m_, int64_t ld_,
                   const float *__restrict__ cand_d_, const int32_t *__restrict__ cand_i_,
                   int32_t *__restrict__ idx_out_, float *__restrict__ dist_out_,
                   int32_t *__restrict__ flags_, DevCounters *ctr, const KnnSet *__restrict__ sets, int nsets,
-                  int lmax, const float *__restrict__ resid_, const float *__restrict__ maxima_) {
+                  int lmax, const float *__restrict__ resid_, const float *__restrict__ maxima_, int quant_) {
     extern __shared__ float rsm[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int64_t qi = (int64_t)blockIdx.x * RR_WARPS + w;  // the launch's row (the batch's row when batched)
@@ -307,6 +336,7 @@ knn_rerank_kernel(const T *__restrict__ X_, int64_t N_, int64_t m_, int64_t ld_,
     int32_t *idx_out = idx_out_, *flags = flags_;
     float *dist_out = dist_out_;
     const float *resid = resid_, *maxima = maxima_;
+    int quant = quant_;
     int kc = kc_, nsplit = nsplit_, k = k_;
     if constexpr (BATCH) {
         const KnnSet &d = find_set_row(sets, nsets, qi);
@@ -327,6 +357,7 @@ knn_rerank_kernel(const T *__restrict__ X_, int64_t N_, int64_t m_, int64_t ld_,
         k = d.k;
         resid = d.resid;
         maxima = d.maxima;
+        quant = d.quant;
     }
     const int L = kc * nsplit;
     const int LS = BATCH ? lmax : L;  // per-warp shared-memory stride
@@ -444,15 +475,18 @@ knn_rerank_kernel(const T *__restrict__ X_, int64_t N_, int64_t m_, int64_t ld_,
     if (lane == 0) {
         const float spread = err_max - err_min;
         float e_hi = fmaxf(err_max, 0.f) + 3.f * spread + ldexpf(norms[q] + nmax, -21);
-        if (resid) {
-            // BF16 operands rounded from FP32 rows: with x = x~ + dx, y = y~ + dy,
-            // |x.y - x~.y~| <= |x~||dy| + |dx||y~| + |dx||dy| for any candidate y,
-            // bounded with the dataset's largest |y| and |dy| (a-priori, not
-            // estimated from the candidates); the tensor core's FP32
-            // accumulation, ~2^-9 of this for FP32 rows, stays with the estimate
-            const float rq = resid[q], rm = maxima[1], ym = sqrtf(maxima[0]), xq = sqrtf(norms[q]);
-            const float eq = 2.f * ((xq + rq) * rm + rq * (ym + rm) + rq * rm) * (1.f + 9.765625e-04f) +
-                             ldexpf(norms[q] + maxima[0], -21);
+        if (quant != KNN_QUANT_NONE) {
+            // BF16 operands from FP32 rows: an a-priori bound (not estimated from
+            // the candidates) on |x.y - (the search's product)| for any
+            // candidate y, with the dataset's largest |y| and rounding terms.
+            //   single (x = h + d):      |h||d_y| + |d||h_y| + |d||d_y|
+            //   split (x = h + l + r):   |l||l_y| + |h + l||r_y| + |r||h_y + l_y| + |r||r_y|
+            // The tensor core's FP32 accumulation stays with the estimate.
+            const float t1 = resid[2 * q], t2 = resid[2 * q + 1], xq = sqrtf(norms[q]);
+            const float ym = sqrtf(maxima[0]), m1 = maxima[1], m2 = maxima[2];
+            const float b = quant == KNN_QUANT_SINGLE ? (xq + t1) * m1 + t1 * (ym + m1) + t1 * m1
+                                                      : t1 * m1 + (xq + t2) * m2 + t2 * (ym + m2) + t2 * m2;
+            const float eq = 2.f * b * (1.f + 9.765625e-04f) + ldexpf(norms[q] + maxima[0], -21);
             e_hi = fmaxf(e_hi, eq);
         }
         int ok = (thr == INFINITY) || (thr - e_hi > theta);
@@ -465,7 +499,8 @@ cudaError_t launch_knn_rerank(const void *X, mecuco_dtype dt, int64_t N, int64_t
                               const float *norms, int64_t q0, int64_t nq, int kc, int nsplit, int k,
                               const float *cand_d, const int32_t *cand_i, int32_t *idx_out,
                               float *dist_out, int32_t *flags, DevCounters *ctr, cudaStream_t s,
-                              const float *resid, const float *maxima) {
+                              const float *resid, const float *maxima, int quant) {
+    if (!resid || !maxima) quant = KNN_QUANT_NONE;
     if (nq <= 0) return cudaSuccess;
     int L = kc * nsplit;
     if (L > RR_MAXL) return cudaErrorInvalidValue;
@@ -479,14 +514,14 @@ cudaError_t launch_knn_rerank(const void *X, mecuco_dtype dt, int64_t N, int64_t
         knn_rerank_kernel<__nv_bfloat16, false><<<grid, block, smem, s>>>((const __nv_bfloat16 *)X, N, m, ld, norms,
                                                                           q0, nq, kc, nsplit, k, cand_d, cand_i,
                                                                           idx_out, dist_out, flags, ctr, nullptr, 0, 0,
-                                                                          resid, maxima);
+                                                                          resid, maxima, quant);
     } else {
         e = cudaFuncSetAttribute(knn_rerank_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
         knn_rerank_kernel<float, false><<<grid, block, smem, s>>>((const float *)X, N, m, ld, norms, q0, nq, kc,
                                                                   nsplit, k, cand_d, cand_i, idx_out, dist_out, flags,
-                                                                  ctr, nullptr, 0, 0, resid, maxima);
+                                                                  ctr, nullptr, 0, 0, resid, maxima, quant);
     }
     return cudaGetLastError();
 }
@@ -604,14 +639,14 @@ cudaError_t launch_knn_rerank_batch(const KnnSet *sets, int nsets, int64_t nrows
         if (e != cudaSuccess) return e;
         knn_rerank_kernel<__nv_bfloat16, true><<<grid, block, smem, s>>>(nullptr, 0, 0, 0, nullptr, 0, nrows, 0, 0, 0,
                                                                          nullptr, nullptr, nullptr, nullptr, nullptr,
-                                                                         ctr, sets, nsets, lmax, nullptr, nullptr);
+                                                                         ctr, sets, nsets, lmax, nullptr, nullptr, 0);
     } else {
         e = cudaFuncSetAttribute(knn_rerank_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
         knn_rerank_kernel<float, true><<<grid, block, smem, s>>>(nullptr, 0, 0, 0, nullptr, 0, nrows, 0, 0, 0, nullptr,
                                                                  nullptr, nullptr, nullptr, nullptr, ctr, sets, nsets,
-                                                                 lmax, nullptr, nullptr);
+                                                                 lmax, nullptr, nullptr, 0);
     }
     return cudaGetLastError();
 }

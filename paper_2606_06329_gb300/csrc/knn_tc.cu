@@ -210,7 +210,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
             g.qend = d.N;
             g.nsplit = d.nsplit;
             g.kc = d.kcl;
-            g.nkb = (int)((d.m + TBK - 1) / TBK);
+            g.nkb = (int)((d.mk + TBK - 1) / TBK);
             g.include_self = d.include_self;
         } else {
             g.ma = &map_a;
@@ -299,7 +299,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
             for (int64_t item = first; item < nitems && ok && !*abort_flag; item += stride) {
             const ItemGeo g = geo(item);
             const int64_t qb = g.qb + (int64_t)rank * TBM;
-            const CUtensorMap *map_q = g.ma, *map_c = PAIR ? g.ma : g.mb;
+            const CUtensorMap *map_q = g.ma, *map_c = g.mb;
             if constexpr (BATCH) {
                 // the table's maps were written by a host copy: fence each dataset's
                 // pair once before its first load
@@ -581,14 +581,18 @@ size_t knn_tc_smem_bytes(int kc) {
 int knn_tc_halves() { return TC_HALVES; }
 int knn_tc_item_rows(int pair) { return pair ? KCfg<true>::QROWS : KCfg<false>::QROWS; }
 
-cudaError_t launch_knn_tc(const void *Xb, int64_t N, int64_t m, int64_t ldb, const float *norms, int64_t q0,
-                          int64_t nq, int kc, int nsplit, int include_self, float *cand_d, int32_t *cand_i, int pair,
-                          long long wait_limit, DevCounters *ctr, cudaStream_t s) {
+cudaError_t launch_knn_tc(const void *Xa, const void *Xb, int64_t N, int64_t m, int64_t ldb, const float *norms,
+                          int64_t q0, int64_t nq, int kc, int nsplit, int include_self, float *cand_d, int32_t *cand_i,
+                          int pair, long long wait_limit, DevCounters *ctr, cudaStream_t s) {
     if (nq <= 0) return cudaSuccess;
     if (wait_limit <= 0) wait_limit = WAIT_LIMIT;
-    if ((reinterpret_cast<uintptr_t>(Xb) & 15) || (ldb % 8) != 0 || kc > 64) return cudaErrorInvalidValue;
-    CUtensorMap ma, mb;
-    if (!make_map(&ma, Xb, N, m, ldb, TBM) || !make_map(&mb, Xb, N, m, ldb, TBN)) return cudaErrorInvalidValue;
+    if ((reinterpret_cast<uintptr_t>(Xa) & 15) || (reinterpret_cast<uintptr_t>(Xb) & 15) || (ldb % 8) != 0 || kc > 64)
+        return cudaErrorInvalidValue;
+    // queries from Xa (128-row boxes); candidates from Xb, in 256-row boxes for
+    // single CTAs and 128-row halves for CTA pairs
+    CUtensorMap ma, mb, mb2;
+    if (!make_map(&ma, Xa, N, m, ldb, TBM) || !make_map(&mb, Xb, N, m, ldb, TBN) || !make_map(&mb2, Xb, N, m, ldb, TBM))
+        return cudaErrorInvalidValue;
     const size_t smem = knn_tc_smem_bytes(kc);
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -625,7 +629,7 @@ cudaError_t launch_knn_tc(const void *Xb, int64_t N, int64_t m, int64_t ldb, con
             cfg.gridDim = dim3((unsigned)(2 * (items < nclusters ? items : nclusters)));
             // the pair form keeps the default limit: its cross-CTA arrivals are
             // not exercised with shortened waits
-            e = cudaLaunchKernelEx(&cfg, kern, ma, ma, N, m, norms, q0, nq, kc, nsplit, include_self, cand_d, cand_i,
+            e = cudaLaunchKernelEx(&cfg, kern, ma, mb2, N, m, norms, q0, nq, kc, nsplit, include_self, cand_d, cand_i,
                                    WAIT_LIMIT, ctr, (const KnnSet *)nullptr, 0, (int64_t)0);
             if (e != cudaSuccess) return e;
             return cudaGetLastError();
@@ -642,9 +646,11 @@ cudaError_t launch_knn_tc(const void *Xb, int64_t N, int64_t m, int64_t ldb, con
     return cudaGetLastError();
 }
 
-bool knn_tc_make_maps(KnnSet *d) {
-    return make_map(&d->map_a, d->xb ? d->xb : d->X, d->N, d->m, d->ldb, TBM) &&
-           make_map(&d->map_b, d->xb ? d->xb : d->X, d->N, d->m, d->ldb, TBN);
+bool knn_tc_make_maps(KnnSet *d, int pair) {
+    const void *qa = d->xb ? d->xb : d->X;
+    const void *cb = d->xb2 ? d->xb2 : qa;
+    return make_map(&d->map_a, qa, d->N, d->mk, d->ldb, TBM) &&
+           make_map(&d->map_b, cb, d->N, d->mk, d->ldb, pair ? TBM : TBN);
 }
 
 cudaError_t launch_knn_tc_batch(const KnnSet *sets, int nsets, int64_t nitems, int kcmax, int pair,
@@ -701,6 +707,33 @@ __global__ void to_bf16_kernel(const float *__restrict__ X, int64_t N, int64_t m
     const int64_t row = blockIdx.x;
     for (int64_t a = threadIdx.x; a < ldb; a += blockDim.x)
         Y[row * ldb + a] = __float2bfloat16_rn(a < m ? X[row * ld + a] : 0.f);
+}
+
+// The three-term split of FP32 rows for the search: with h = bf16(x) and
+// l = bf16(x - h), the query copy holds [h | h | l] and the candidate copy
+// [h | l | h] along K (segments of ms columns, zero past m), so that one GEMM
+// over K = 3 ms gives h.h' + h.l' + l.h', the FP32 product up to l.l' and the
+// remainders past two terms.
+__global__ void to_bf16_split_kernel(const float *__restrict__ X, int64_t m, int64_t ld, __nv_bfloat16 *__restrict__ Ya,
+                                     __nv_bfloat16 *__restrict__ Yb, int64_t ms, int64_t ldb) {
+    const int64_t row = blockIdx.x;
+    const float *x = X + row * ld;
+    __nv_bfloat16 *ya = Ya + row * ldb, *yb = Yb + row * ldb;
+    for (int64_t a = threadIdx.x; a < ldb; a += blockDim.x) {
+        const int64_t seg = a / ms, c = a - seg * ms;
+        const float v = (seg < 3 && c < m) ? x[c] : 0.f;
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+        ya[a] = seg == 2 ? l : h;
+        yb[a] = seg == 1 ? l : h;
+    }
+}
+
+cudaError_t launch_to_bf16_split(const float *X, int64_t N, int64_t m, int64_t ld, void *Ya, void *Yb, int64_t ms,
+                                 int64_t ldb, cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    to_bf16_split_kernel<<<(unsigned)N, 256, 0, s>>>(X, m, ld, (__nv_bfloat16 *)Ya, (__nv_bfloat16 *)Yb, ms, ldb);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_to_bf16(const void *X, mecuco_dtype dt, int64_t N, int64_t m, int64_t ld, void *Y, int64_t ldb,

@@ -55,11 +55,21 @@ def test_tc_knn_fp32_input_small_m(ctx, orc):
     _check(ctx, orc, torch.from_numpy(X), X.astype(np.float64), 10)
 
 
-def test_tc_knn_sparse_clusters(ctx, orc):
+@pytest.mark.parametrize("split", [1, 0])
+def test_tc_knn_sparse_clusters(ctx, orc, split):
+    """FP32 rows through the tensor-core search, as the three-term BF16 split
+    (default) and as one rounding: the lists are the oracle's either way.  One
+    rounding perturbs d~ by ~1e-2 here and its a-priori bound leaves rows
+    uncertified (the exact scan re-solves them); the split's bound is ~2^8
+    smaller and certifies all but a few."""
+    from paper_2606_06329_gb300 import _native as N
     X = synth.sparse_clusters(n=6000, m=784, seed=2)
-    # BF16 rounding of FP32 inputs perturbs d~ by ~1e-2 here: the margin may
-    # leave a few rows uncertified, which the exact fallback then re-solves
-    _check(ctx, orc, torch.from_numpy(X), X.astype(np.float64), 50, max_uncert=60)
+    ctx.set_option(N.OPT_KNN_SPLIT_BF16, split)
+    try:
+        _check(ctx, orc, torch.from_numpy(X), X.astype(np.float64), 50, max_uncert=6 if split else 6000)
+        print(f"split={split}: uncertified {ctx.mecuco_get_stats()['knn_uncertified']} of 6000")
+    finally:
+        ctx.set_option(N.OPT_KNN_SPLIT_BF16, 1)
 
 
 @pytest.mark.parametrize("n,m,k", [(1037, 200, 16), (700, 4096, 32), (3000, 256, 64)])
