@@ -264,6 +264,13 @@ KnnPlan plan_knn(mecuco_t h, const void *X, mecuco_dtype dt, int64_t N, int64_t 
     p.mk = p.quant == KNN_QUANT_SPLIT ? 3 * split_segment(m) : m;
     p.ldb = direct ? ld : (p.mk + 7) / 8 * 8;
     p.qchunk = h->knn_qchunk > 0 ? h->knn_qchunk : (int64_t)1 << 18;
+    if (p.tc && h->knn_qchunk <= 0) {
+        // whole waves of the persistent search per launch: a multiple of the
+        // query rows one wave of CTAs (pairs) covers, so that only the last
+        // launch ends on a partial wave (1M points: 52 instead of 53 waves)
+        const int64_t wave = p.pair ? (int64_t)(h->num_sms / 2) * 256 : (int64_t)h->num_sms * 128;
+        if (p.qchunk > wave) p.qchunk = p.qchunk / wave * wave;
+    }
     if (p.qchunk > nrows) p.qchunk = nrows;
     // keep every SM busy (tensor-core kernel: 1 CTA/SM; CUDA-core kernel: 2):
     // split the candidate range when there are few query blocks (the re-rank
