@@ -27,12 +27,14 @@
  *   orc_grad_fd        FP64 central finite differences of sum_i K_i with the
  *                      neighbour lists frozen (reference gradient).
  *
- * Readings of the paper taken here (each is listed with its reason in the
- * design notes): a point is not its own neighbour unless include_self; ties
- * in distance go to the lower index; the truncation rank is
- * p = min(k-1, m, numerical rank) with numerical rank
- * #{ s_l^2 > k*m*2^-52 * s_1^2 }; with no null space (q = m - p = 0) the
- * null-space term is 0.
+ * Readings of the paper taken here, where it is silent: a point is not its
+ * own neighbour unless include_self (a kNN graph has no self loops); ties in
+ * distance go to the lower index (a deterministic order the GPU can match);
+ * the truncation rank is p = min(k-1, m, numerical rank) with numerical rank
+ * #{ s_l^2 > k*m*2^-52 * s_1^2 } (Alg. 1 fixes p = k - 1, which a
+ * rank-deficient patch cannot support: its extra singular values are FP64
+ * rounding noise); with no null space (q = m - p = 0) the null-space term is
+ * 0 (Alg. 1 would divide by m - p = 0; Fast then equals Exact).
  *
  * Parity pins: see the tests (special cases, invariants, Haar Monte Carlo,
  * library SVD cross-checks, closed-form golden patches, finite differences).

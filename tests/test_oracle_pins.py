@@ -244,7 +244,9 @@ def test_haar_expectation_monte_carlo(orc):
     haar = orc.fast_patch(Xc, variant=orc.HAAR)["kappa"]
     literal = orc.fast_patch(Xc, variant=orc.LITERAL)["kappa"]
     assert abs(haar - mean) < 4 * se, (haar, mean, se)
-    # the printed algorithm is not the Haar expectation (see design notes)
+    # the algorithm as printed (middle term |X_c V_r|_F^2, denominator m - p)
+    # is not the Haar expectation, whose middle term is
+    # sum_{j,a} X_c[j,a]^2 (1 - d_P[a]) and whose denominator is m - p + 2
     assert abs(literal - mean) > 20 * se
 
 
