@@ -200,3 +200,30 @@ def test_batched_256_uneven_datasets(ctx, orc, precision):
         ref = ctx.mecuco_curvature(Xs[i], ks[i], idx=ref_idx, precision=precision)
         assert torch.equal(idx_out[i], ref_idx)
         assert torch.equal(kap[i], ref)
+
+
+@pytest.mark.parametrize("dtype,include_self", [("f32", False), ("bf16", False), ("f32", True)])
+def test_one_launch_per_stage_edge_datasets(ctx, dtype, include_self):
+    """Corners of the batch tables: datasets smaller than one search tile
+    (N down to 3), k at its largest for N (N - 1, or N with the query itself),
+    m = 1, odd m, m just past a 64-column chunk, and rows whose leading
+    dimension exceeds m (views); every dataset must come out as a single call
+    gives it, bit for bit."""
+    rng = np.random.default_rng(17)
+    shapes = [(3, 5, 2), (40, 1, 5), (257, 3, 64), (300, 65, 20), (129, 33, 64), (1000, 130, 17), (64, 8, 63)]
+    Xs, ks = [], []
+    for n, m, k in shapes:
+        if include_self and k == n - 1:
+            k = n
+        k = min(k, n if include_self else n - 1, 64)
+        base = rng.standard_normal((n, m + 3)).astype(np.float32)
+        X = torch.from_numpy(base).cuda()[:, :m]  # leading dimension m + 3
+        if dtype == "bf16":
+            X = X.to(torch.bfloat16)
+        Xs.append(X)
+        ks.append(k)
+    idx_out = [torch.empty((X.shape[0], k), dtype=torch.int32, device="cuda") for X, k in zip(Xs, ks)]
+    kb = ctx.mecuco_curvature_batched(Xs, ks, precision="bf16_mixed", include_self=include_self, idx_out=idx_out)
+    torch.cuda.synchronize()
+    assert ctx.mecuco_get_last_status() == 0
+    _check_against_single_calls(ctx, Xs, ks, kb, idx_out, "bf16_mixed", include_self)
