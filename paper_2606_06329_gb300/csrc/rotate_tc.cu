@@ -6,10 +6,14 @@
 // X_c = U Y exactly for the full orthogonal U.  The third-moment pass of the
 // Fast estimator works on Y (tthird_tc.cu).
 //
-// One CTA per patch.  8 producer warps gather the k neighbour rows of each
-// 64-column chunk, centre every column in FP32 (pg::centre_chunk, as the
-// Gram pass does, so both see identical BF16 values) and write the chunk transposed, X_c^T (64 columns x 64 rows, BF16,
-// K-major with the 128-byte swizzle), as the B operand.  One MMA thread
+// One CTA per patch.  The 256 producer threads gather the k neighbour rows of
+// each 64-column chunk into a ring of raw stages with cp.async (four chunks in
+// flight for BF16 rows, one for FP32 rows; the first ones while U is staged).
+// Producer warp u then owns columns 8u .. 8u + 7 of the chunk, lane l rows l
+// and l + 32: it centres them in FP32 (pg::centre_lane, as the Gram pass
+// does, so both see identical BF16 values) and writes them transposed into
+// X_c^T (64 columns x 64 rows, BF16, K-major with the 128-byte swizzle), the
+// B operand; a chunk costs the CTA one barrier.  One MMA thread
 // computes D = [U_hi^T | U_lo^T] [X_c^T | X_c^T]^T on the tensor cores: U is
 // split into two BF16 terms (U_hi = bf16(U), U_lo = bf16(U - U_hi), together
 // U to ~2^-17 relative) placed side by side along K, so one FP32 accumulator
@@ -35,18 +39,25 @@ constexpr int RT_CH = 64;                                  // columns per chunk
 constexpr int RT_XS_LD = 68;                               // FP32 staging row stride (floats)
 constexpr int RT_A_TILE = 128 * 128;                       // one A tile: 128 rows x 64 K (BF16), 16 KB
 constexpr int RT_B_BYTES = 64 * 128;                       // X_c^T chunk: 64 rows x 64 K (BF16), 8 KB
+constexpr int RT_U_BYTES = 64 * RT_XS_LD * 4;              // U staged in FP32 (A operand set-up)
 constexpr long long RT_WAIT = 1000000000LL;
-using pg::load_halves;
+// gather ring depth: 5 x 8 KB stages of BF16 rows, 2 x 16 KB of FP32 rows
+// (two CTAs per SM)
+template <typename T>
+__host__ __device__ constexpr int rt_stages() {
+    return sizeof(T) == 2 ? 5 : 2;
+}
 using pg::pack_bf16x2;
 using pg::sw128;
-using pg::Unit8;
 }  // namespace
 
+template <typename T>
 size_t rotate_tc_smem_bytes() {
-    return 1024 + 2 * (size_t)RT_A_TILE + 2 * (size_t)RT_B_BYTES + 64 * (size_t)RT_XS_LD * 4 + 4 * 64 * 4;
+    return 1024 + 2 * (size_t)RT_A_TILE + 2 * (size_t)RT_B_BYTES + (size_t)RT_U_BYTES +
+           (size_t)rt_stages<T>() * pg::raw_stage_bytes<T>();
 }
 
-// two CTAs per SM (113 registers a thread): the gather needs warps in flight
+// two CTAs per SM (~108 KB of shared memory each)
 template <typename T>
 __global__ void __launch_bounds__(RT_THREADS, 2)
 rotate_tc_kernel(const __grid_constant__ PatchSeg one, const PatchSeg *__restrict__ tab, int ntab,
@@ -55,11 +66,11 @@ rotate_tc_kernel(const __grid_constant__ PatchSeg one, const PatchSeg *__restric
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(rsm_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *Aop = base;                                             // 2 A tiles (U_hi^T, U_lo^T)
     uint8_t *Bop0 = base + 2 * RT_A_TILE;                            // 2 x B operand
-    float *Xs = reinterpret_cast<float *>(Bop0 + 2 * RT_B_BYTES);    // [64][68] FP32 staging
-    float *Part = Xs + 64 * RT_XS_LD;                                // [4][64] column partials
+    float *Xs = reinterpret_cast<float *>(Bop0 + 2 * RT_B_BYTES);    // [64][68] U in FP32
+    uint8_t *Raw = reinterpret_cast<uint8_t *>(Xs) + RT_U_BYTES;     // gather ring
+    constexpr int S = rt_stages<T>(), RB = pg::raw_stage_bytes<T>();
     __shared__ uint64_t b_full[2], b_empty[2], d_full[2], d_empty[2], mma_fin;
     __shared__ uint32_t tmem_slot;
-    __shared__ int rows[64];
     __shared__ int abort_flag, never;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -75,23 +86,40 @@ rotate_tc_kernel(const __grid_constant__ PatchSeg one, const PatchSeg *__restric
     const uint32_t idesc = tc::idesc_bf16_f32(128, 64);
     const bool vec = (ld % 8 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
 
-    if (tid < 64) {
-        int r = 0;
-        if (tid < k) {
-            r = idx[pt * k + tid];
-            if (r < 0 || (int64_t)r >= N) { atomicOr(&ctr->status, (unsigned)DEV_INVALID); r = 0; }
-        }
-        rows[tid] = r;
+    if (tid < k) {
+        const int r = idx[pt * k + tid];
+        if (r < 0 || (int64_t)r >= N) atomicOr(&ctr->status, (unsigned)DEV_INVALID);
     }
+    // gather units of producer thread tid: rows gr0 and gr0 + 32, 8-column unit gg
+    // (an invalid index reads row 0); the first S - 1 chunks go in flight now
+    const int gr0 = (tid & 255) >> 3, gg = tid & 7;
+    const bool glive0 = gr0 < k, glive1 = gr0 + 32 < k;
+    auto nbr = [&](bool live, int j) -> const T * {
+        int r = live ? idx[pt * k + j] : 0;
+        if (r < 0 || (int64_t)r >= N) r = 0;
+        return X + (int64_t)r * ld;
+    };
+    const T *grow0 = nbr(glive0, gr0), *grow1 = nbr(glive1, gr0 + 32);
+    auto issue = [&](int j) {  // chunk j into stage j % S (an empty group past the last chunk)
+        if (j < nchunks) {
+            uint8_t *st = Raw + (j % S) * RB;
+            const int64_t a = (int64_t)j * RT_CH + gg * 8;
+            pg::raw_issue(st, gr0, gg, grow0, glive0, a, m, vec);
+            pg::raw_issue(st, gr0 + 32, gg, grow1, glive1, a, m, vec);
+        }
+        pg::cp_async_commit();
+    };
+    if (warp < RT_PRODUCER_WARPS)
+        for (int j = 0; j < S - 1; ++j) issue(j);
     // U (row j, column l) staged as Xs[j][l], zero outside k x k
-    const float *u = U + pt * (int64_t)k * k;
+    const float *Up = U + pt * (int64_t)k * k;
     for (int e = tid; e < 64 * 64; e += RT_THREADS) {
         const int j = e >> 6, l = e & 63;
-        Xs[j * RT_XS_LD + l] = (j < k && l < k) ? u[j * k + l] : 0.f;
+        Xs[j * RT_XS_LD + l] = (j < k && l < k) ? Up[j * k + l] : 0.f;
     }
     if (tid == 0) {
         for (int b = 0; b < 2; ++b) {
-            tc::mbar_init(tc::smem_u32(&b_full[b]), 1);
+            tc::mbar_init(tc::smem_u32(&b_full[b]), RT_PRODUCER_WARPS);
             tc::mbar_init(tc::smem_u32(&b_empty[b]), 1);
             tc::mbar_init(tc::smem_u32(&d_full[b]), 1);
             tc::mbar_init(tc::smem_u32(&d_empty[b]), 4);  // the four drain warps
@@ -140,22 +168,12 @@ rotate_tc_kernel(const __grid_constant__ PatchSeg one, const PatchSeg *__restric
 
     if (warp < RT_PRODUCER_WARPS) {
         // ============ producers: gather, centre, transposed pack; drain ============
-        const int ptid = tid;                                  // 0 .. 255
-        const int gr0 = ptid >> 3, gg = ptid & 7;              // gather units (row gr0 / gr0 + 32, group gg)
-        const T *grow0 = X + (int64_t)rows[gr0] * ld;
-        const T *grow1 = X + (int64_t)rows[gr0 + 32] * ld;
-        const bool live0 = gr0 < k, live1 = gr0 + 32 < k;
-        const int cc = ptid & 63, rg = ptid >> 6;              // centring: column cc, rows 16 rg .. 16 rg + 15
+        const int u = warp;  // columns 8u .. 8u + 7 of every chunk; rows lane, lane + 32
         const float inv_k = 1.f / (float)k;
-        // transposed pack: column ta = ptid & 63, 16-byte units tu, tu + 1 (rows 8 tu ..)
-        const int ta = ptid & 63, tu = (ptid >> 6) * 2;
         // drain: warps with lane quarter 0 or 1 (TMEM lanes = rows l 0..63), column half dh
         const bool drainer = (warp & 3) < 2;
         const int dq = warp & 3, dh = warp >> 2;
         __nv_bfloat16 *yrow = Y + (yp * 64 + dq * 32 + lane) * ldy;
-        Unit8<T> pre0, pre1;
-        if (live0) pre0.load(grow0, gg * 8, m, vec); else pre0.zero();
-        if (live1) pre1.load(grow1, gg * 8, m, vec); else pre1.zero();
         auto drain = [&](int c) {  // chunk c of Y, from accumulator c & 1
             const int b = c & 1;
             if (lane == 0) wait(&d_full[b], (uint32_t)(c >> 1) & 1u);
@@ -174,33 +192,33 @@ rotate_tc_kernel(const __grid_constant__ PatchSeg one, const PatchSeg *__restric
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(tc::smem_u32(&d_empty[b]));
         };
+        // this lane's K positions (rows j = lane, lane + 32) in a row of X_c^T
+        const uint32_t kb0 = (uint32_t)((lane & 7) * 2);
+        const int ku0 = lane >> 3, ku1 = 4 + (lane >> 3);
         for (int ci = 0; ci < nchunks; ++ci) {
             const int b = ci & 1;
-            pre0.store(Xs + gr0 * RT_XS_LD + gg * 8, gg >= 4);
-            pre1.store(Xs + (gr0 + 32) * RT_XS_LD + gg * 8, gg >= 4);
-            if (ci + 1 < nchunks) {
-                const int64_t an = (int64_t)(ci + 1) * RT_CH + gg * 8;
-                if (live0) pre0.load(grow0, an, m, vec); else pre0.zero();
-                if (live1) pre1.load(grow1, an, m, vec); else pre1.zero();
-            }
-            float xc[16];
-            pg::centre_chunk<RT_XS_LD>(Xs, Part, cc, rg, k, inv_k, xc);
-            // buffer b is free once the MMAs of chunk ci - 2 are done with it
-            if (ptid == 0 && ci >= 2) wait(&b_empty[b], (uint32_t)((ci >> 1) - 1) & 1u);
+            pg::cp_async_wait<S - 2>();  // this thread's copies of chunk ci have landed
+            // every producer's copies of chunk ci are visible, and every read
+            // of stage (ci - 1) % S is done, so it takes chunk ci + S - 1
             asm volatile("bar.sync 1, 256;" ::: "memory");
+            issue(ci + S - 1);
+            float x0[8], x1[8];
+            pg::centre_lane<T>(Raw + (ci % S) * RB, lane, u, k, inv_k, x0, x1);
+            // buffer b is free once the MMAs of chunk ci - 2 are done with it
+            if (ci >= 2) {
+                if (lane == 0) wait(&b_empty[b], (uint32_t)((ci >> 1) - 1) & 1u);
+                __syncwarp();
+            }
             uint8_t *Bop = Bop0 + b * RT_B_BYTES;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int un = tu + h;
-                uint32_t w4[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    w4[q] = pack_bf16x2(Xs[(8 * un + 2 * q) * RT_XS_LD + ta], Xs[(8 * un + 2 * q + 1) * RT_XS_LD + ta]);
-                *reinterpret_cast<uint4 *>(Bop + sw128(ta, un)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+            for (int e = 0; e < 8; ++e) {
+                const int c = 8 * u + e;  // row of X_c^T
+                *reinterpret_cast<__nv_bfloat16 *>(Bop + sw128(c, ku0) + kb0) = __float2bfloat16_rn(x0[e]);
+                *reinterpret_cast<__nv_bfloat16 *>(Bop + sw128(c, ku1) + kb0) = __float2bfloat16_rn(x1[e]);
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("bar.sync 1, 256;" ::: "memory");
-            if (ptid == 0) tc::mbar_arrive(tc::smem_u32(&b_full[b]));
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(tc::smem_u32(&b_full[b]));
             // the previous chunk's accumulator, while the MMAs of this one run
             if (drainer && ci >= 1) drain(ci - 1);
         }
@@ -248,15 +266,16 @@ cudaError_t launch_rotate_tc(mecuco_dtype dt, const PatchSeg &one, const PatchSe
         (reinterpret_cast<uintptr_t>(Y) & 15))
         return cudaErrorInvalidValue;
     if (wait_limit <= 0) wait_limit = RT_WAIT;
-    const size_t smem = rotate_tc_smem_bytes();
     cudaError_t e;
     if (dt == MECUCO_BF16) {
+        const size_t smem = rotate_tc_smem_bytes<__nv_bfloat16>();
         e = cudaFuncSetAttribute(rotate_tc_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
         rotate_tc_kernel<__nv_bfloat16><<<(unsigned)np, RT_THREADS, smem, s>>>(one, tab, ntab, (__nv_bfloat16 *)Y,
                                                                               ldy, wait_limit, ctr);
     } else {
+        const size_t smem = rotate_tc_smem_bytes<float>();
         e = cudaFuncSetAttribute(rotate_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         rotate_tc_kernel<float><<<(unsigned)np, RT_THREADS, smem, s>>>(one, tab, ntab, (__nv_bfloat16 *)Y, ldy,
