@@ -18,8 +18,9 @@
 // split into two BF16 terms (U_hi = bf16(U), U_lo = bf16(U - U_hi), together
 // U to ~2^-17 relative) placed side by side along K, so one FP32 accumulator
 // sums both products; BF16 x BF16 products are exact in FP32.  Rows 64..127 of
-// the MMA's A operand are zero.  Four producer warps drain the accumulator
-// (TMEM lanes 0..63 = rows l of Y), round to BF16 and store the chunk of Y.
+// the MMA's A operand repeat rows 0..63, so TMEM lanes 64..127 hold a second
+// copy of the chunk of Y and all eight producer warps (each confined to its
+// TMEM lane quarter) drain 16 columns of it: round to BF16 and store.
 // Accumulators and B operands are double-buffered; every wait is bounded
 // (MECUCO_ERR_TIMEOUT, no trap) and the MMA thread waits for its last MMAs
 // before tensor memory is freed.
@@ -122,7 +123,7 @@ rotate_tc_kernel(const __grid_constant__ PatchSeg one, const PatchSeg *__restric
             tc::mbar_init(tc::smem_u32(&b_full[b]), RT_PRODUCER_WARPS);
             tc::mbar_init(tc::smem_u32(&b_empty[b]), 1);
             tc::mbar_init(tc::smem_u32(&d_full[b]), 1);
-            tc::mbar_init(tc::smem_u32(&d_empty[b]), 4);  // the four drain warps
+            tc::mbar_init(tc::smem_u32(&d_empty[b]), RT_PRODUCER_WARPS);
         }
         tc::mbar_init(tc::smem_u32(&mma_fin), 1);
         abort_flag = (*(volatile unsigned *)&ctr->status & DEV_TIMEOUT) ? 1 : 0;
@@ -134,20 +135,19 @@ rotate_tc_kernel(const __grid_constant__ PatchSeg one, const PatchSeg *__restric
         tc::tmem_relinquish();
     }
     __syncthreads();
-    // A operand: row l holds U[:, l] (the l-th column of U) split in two BF16
-    // terms, the high term in tile 0 and the low term in tile 1 (K = j); rows
-    // 64..127 are zero.  Thread (l, unit pair) reads a column of the staged U.
+    // A operand: rows l and 64 + l hold U[:, l] (the l-th column of U) split in
+    // two BF16 terms, the high term in tile 0 and the low term in tile 1
+    // (K = j).  Thread (row, unit) reads a column of the staged U.
     for (int e = tid; e < 128 * 8; e += RT_THREADS) {
         const int l = e & 127, un = e >> 7;  // row, 16-byte unit (8 values of j)
-        uint32_t hw[4] = {0u, 0u, 0u, 0u}, lw[4] = {0u, 0u, 0u, 0u};
-        if (l < 64) {
+        const int lc = l & 63;               // column of U
+        uint32_t hw[4], lw[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float u0 = Xs[(8 * un + 2 * q) * RT_XS_LD + l], u1 = Xs[(8 * un + 2 * q + 1) * RT_XS_LD + l];
-                const __nv_bfloat16 h0 = __float2bfloat16_rn(u0), h1 = __float2bfloat16_rn(u1);
-                hw[q] = pack_bf16x2(__bfloat162float(h0), __bfloat162float(h1));
-                lw[q] = pack_bf16x2(u0 - __bfloat162float(h0), u1 - __bfloat162float(h1));
-            }
+        for (int q = 0; q < 4; ++q) {
+            const float u0 = Xs[(8 * un + 2 * q) * RT_XS_LD + lc], u1 = Xs[(8 * un + 2 * q + 1) * RT_XS_LD + lc];
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(u0), h1 = __float2bfloat16_rn(u1);
+            hw[q] = pack_bf16x2(__bfloat162float(h0), __bfloat162float(h1));
+            lw[q] = pack_bf16x2(u0 - __bfloat162float(h0), u1 - __bfloat162float(h1));
         }
         *reinterpret_cast<uint4 *>(Aop + sw128(l, un)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
         *reinterpret_cast<uint4 *>(Aop + RT_A_TILE + sw128(l, un)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
@@ -170,24 +170,24 @@ rotate_tc_kernel(const __grid_constant__ PatchSeg one, const PatchSeg *__restric
         // ============ producers: gather, centre, transposed pack; drain ============
         const int u = warp;  // columns 8u .. 8u + 7 of every chunk; rows lane, lane + 32
         const float inv_k = 1.f / (float)k;
-        // drain: warps with lane quarter 0 or 1 (TMEM lanes = rows l 0..63), column half dh
-        const bool drainer = (warp & 3) < 2;
-        const int dq = warp & 3, dh = warp >> 2;
-        __nv_bfloat16 *yrow = Y + (yp * 64 + dq * 32 + lane) * ldy;
+        // drain: warp w reads TMEM lane quarter dq = w & 3 (rows l = 32 (dq & 1)
+        // + lane of Y; quarters 2 and 3 hold the copy), columns [16 ds, +16)
+        const int dq = warp & 3, ds = 2 * (warp >> 2) + (dq >> 1);
+        __nv_bfloat16 *yrow = Y + (yp * 64 + (dq & 1) * 32 + lane) * ldy;
         auto drain = [&](int c) {  // chunk c of Y, from accumulator c & 1
             const int b = c & 1;
             if (lane == 0) wait(&d_full[b], (uint32_t)(c >> 1) & 1u);
             __syncwarp();
             tc::fence_after();
-            uint32_t r32[32];
-            tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(dq * 32) << 16) + (uint32_t)(b * 64 + dh * 32), r32);
+            uint32_t r16[16];
+            tc::tmem_ld_32x32b_x16(tmem + ((uint32_t)(dq * 32) << 16) + (uint32_t)(b * 64 + ds * 16), r16);
             tc::tmem_ld_wait();
-            uint32_t pk[16];
+            uint32_t pk[8];
 #pragma unroll
-            for (int e = 0; e < 16; ++e) pk[e] = pack_bf16x2(__uint_as_float(r32[2 * e]), __uint_as_float(r32[2 * e + 1]));
-            uint4 *dst = reinterpret_cast<uint4 *>(yrow + (int64_t)c * RT_CH + dh * 32);
+            for (int e = 0; e < 8; ++e) pk[e] = pack_bf16x2(__uint_as_float(r16[2 * e]), __uint_as_float(r16[2 * e + 1]));
+            uint4 *dst = reinterpret_cast<uint4 *>(yrow + (int64_t)c * RT_CH + ds * 16);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) dst[e] = make_uint4(pk[4 * e], pk[4 * e + 1], pk[4 * e + 2], pk[4 * e + 3]);
+            for (int e = 0; e < 2; ++e) dst[e] = make_uint4(pk[4 * e], pk[4 * e + 1], pk[4 * e + 2], pk[4 * e + 3]);
             tc::fence_before();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(tc::smem_u32(&d_empty[b]));
@@ -220,9 +220,9 @@ rotate_tc_kernel(const __grid_constant__ PatchSeg one, const PatchSeg *__restric
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(tc::smem_u32(&b_full[b]));
             // the previous chunk's accumulator, while the MMAs of this one run
-            if (drainer && ci >= 1) drain(ci - 1);
+            if (ci >= 1) drain(ci - 1);
         }
-        if (drainer) drain(nchunks - 1);
+        drain(nchunks - 1);
     } else if (lane == 0) {
         // ================= MMA thread =================
         const uint64_t a0 = tc::sdesc_sw128(tc::smem_u32(Aop)), a1 = tc::sdesc_sw128(tc::smem_u32(Aop + RT_A_TILE));
