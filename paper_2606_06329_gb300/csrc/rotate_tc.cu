@@ -19,8 +19,9 @@
 // U to ~2^-17 relative) placed side by side along K, so one FP32 accumulator
 // sums both products; BF16 x BF16 products are exact in FP32.  Rows 64..127 of
 // the MMA's A operand repeat rows 0..63, so TMEM lanes 64..127 hold a second
-// copy of the chunk of Y and all eight producer warps (each confined to its
-// TMEM lane quarter) drain 16 columns of it: round to BF16 and store.
+// copy of the chunk of Y: two drain warps, confined to TMEM lane quarters 1
+// and 2, read rows 32..63 and (the copy of) rows 0..31, round to BF16 and
+// store the chunk of Y while the producers already centre the next ones.
 // Accumulators and B operands are double-buffered; every wait is bounded
 // (MECUCO_ERR_TIMEOUT, no trap) and the MMA thread waits for its last MMAs
 // before tensor memory is freed.
@@ -35,7 +36,9 @@ namespace mecuco {
 
 namespace {
 constexpr int RT_PRODUCER_WARPS = 8;
-constexpr int RT_THREADS = (RT_PRODUCER_WARPS + 1) * 32;  // + the MMA warp
+constexpr int RT_MMA_WARP = RT_PRODUCER_WARPS;             // warp 8; warps 9, 10 drain
+constexpr int RT_DRAIN_WARPS = 2;
+constexpr int RT_THREADS = (RT_PRODUCER_WARPS + 1 + RT_DRAIN_WARPS) * 32;
 constexpr int RT_CH = 64;                                  // columns per chunk
 constexpr int RT_XS_LD = 68;                               // FP32 staging row stride (floats)
 constexpr int RT_A_TILE = 128 * 128;                       // one A tile: 128 rows x 64 K (BF16), 16 KB
@@ -58,7 +61,7 @@ size_t rotate_tc_smem_bytes() {
            (size_t)rt_stages<T>() * pg::raw_stage_bytes<T>();
 }
 
-// two CTAs per SM (~108 KB of shared memory each)
+// two CTAs per SM (~108 KB of shared memory each, 76 registers a thread)
 template <typename T>
 __global__ void __launch_bounds__(RT_THREADS, 2)
 rotate_tc_kernel(const __grid_constant__ PatchSeg one, const PatchSeg *__restrict__ tab, int ntab,
@@ -123,7 +126,7 @@ rotate_tc_kernel(const __grid_constant__ PatchSeg one, const PatchSeg *__restric
             tc::mbar_init(tc::smem_u32(&b_full[b]), RT_PRODUCER_WARPS);
             tc::mbar_init(tc::smem_u32(&b_empty[b]), 1);
             tc::mbar_init(tc::smem_u32(&d_full[b]), 1);
-            tc::mbar_init(tc::smem_u32(&d_empty[b]), RT_PRODUCER_WARPS);
+            tc::mbar_init(tc::smem_u32(&d_empty[b]), RT_DRAIN_WARPS);
         }
         tc::mbar_init(tc::smem_u32(&mma_fin), 1);
         abort_flag = (*(volatile unsigned *)&ctr->status & DEV_TIMEOUT) ? 1 : 0;
@@ -167,31 +170,9 @@ rotate_tc_kernel(const __grid_constant__ PatchSeg one, const PatchSeg *__restric
     };
 
     if (warp < RT_PRODUCER_WARPS) {
-        // ============ producers: gather, centre, transposed pack; drain ============
+        // ============ producers: gather, centre, transposed pack ============
         const int u = warp;  // columns 8u .. 8u + 7 of every chunk; rows lane, lane + 32
         const float inv_k = 1.f / (float)k;
-        // drain: warp w reads TMEM lane quarter dq = w & 3 (rows l = 32 (dq & 1)
-        // + lane of Y; quarters 2 and 3 hold the copy), columns [16 ds, +16)
-        const int dq = warp & 3, ds = 2 * (warp >> 2) + (dq >> 1);
-        __nv_bfloat16 *yrow = Y + (yp * 64 + (dq & 1) * 32 + lane) * ldy;
-        auto drain = [&](int c) {  // chunk c of Y, from accumulator c & 1
-            const int b = c & 1;
-            if (lane == 0) wait(&d_full[b], (uint32_t)(c >> 1) & 1u);
-            __syncwarp();
-            tc::fence_after();
-            uint32_t r16[16];
-            tc::tmem_ld_32x32b_x16(tmem + ((uint32_t)(dq * 32) << 16) + (uint32_t)(b * 64 + ds * 16), r16);
-            tc::tmem_ld_wait();
-            uint32_t pk[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) pk[e] = pack_bf16x2(__uint_as_float(r16[2 * e]), __uint_as_float(r16[2 * e + 1]));
-            uint4 *dst = reinterpret_cast<uint4 *>(yrow + (int64_t)c * RT_CH + ds * 16);
-#pragma unroll
-            for (int e = 0; e < 2; ++e) dst[e] = make_uint4(pk[4 * e], pk[4 * e + 1], pk[4 * e + 2], pk[4 * e + 3]);
-            tc::fence_before();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(tc::smem_u32(&d_empty[b]));
-        };
         // this lane's K positions (rows j = lane, lane + 32) in a row of X_c^T
         const uint32_t kb0 = (uint32_t)((lane & 7) * 2);
         const int ku0 = lane >> 3, ku1 = 4 + (lane >> 3);
@@ -219,10 +200,33 @@ rotate_tc_kernel(const __grid_constant__ PatchSeg one, const PatchSeg *__restric
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(tc::smem_u32(&b_full[b]));
-            // the previous chunk's accumulator, while the MMAs of this one run
-            if (ci >= 1) drain(ci - 1);
         }
-        drain(nchunks - 1);
+    } else if (warp > RT_MMA_WARP) {
+        // ============ drain: TMEM lane quarter dq, rows 32 (dq & 1) + lane of Y ============
+        const int dq = warp & 3;  // 1 (rows 32..63) or 2 (the copy of rows 0..31)
+        __nv_bfloat16 *yrow = Y + (yp * 64 + (dq & 1) * 32 + lane) * ldy;
+        for (int c = 0; c < nchunks; ++c) {
+            const int b = c & 1;
+            if (lane == 0) wait(&d_full[b], (uint32_t)(c >> 1) & 1u);
+            __syncwarp();
+            tc::fence_after();
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uint32_t r32[32];
+                tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(dq * 32) << 16) + (uint32_t)(b * 64 + h * 32), r32);
+                tc::tmem_ld_wait();
+                uint32_t pk[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e)
+                    pk[e] = pack_bf16x2(__uint_as_float(r32[2 * e]), __uint_as_float(r32[2 * e + 1]));
+                uint4 *dst = reinterpret_cast<uint4 *>(yrow + (int64_t)c * RT_CH + h * 32);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) dst[e] = make_uint4(pk[4 * e], pk[4 * e + 1], pk[4 * e + 2], pk[4 * e + 3]);
+            }
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(tc::smem_u32(&d_empty[b]));
+        }
     } else if (lane == 0) {
         // ================= MMA thread =================
         const uint64_t a0 = tc::sdesc_sw128(tc::smem_u32(Aop)), a1 = tc::sdesc_sw128(tc::smem_u32(Aop + RT_A_TILE));
